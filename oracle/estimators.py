@@ -1,0 +1,134 @@
+"""Oracle: stochastic trace estimators of the paper (test infrastructure only).
+
+All estimators target tr[B D^{-1}(t, t)] per timeslice t, with B = 1 or
+gamma5 (x) 1 (Sec. 4, Eq. 21, O(t) = tr[Gamma5(t) D^{-1}(t, t)]), and return
+the per-sample values X_i(t) so that the mean and the sample variance can be
+formed.  A per-sample value is the quadratic form of the paper restricted to
+the dofs of timeslice t:  X(t) = sum_{j in t} conj(v_j) (B D^{-1} v)_j.
+
+  hutchinson   Eq. 3 with Rademacher vectors (Sec. 1); optional time dilution
+               (v restricted to one timeslice per solve).
+  probing      Eq. 14 with the probing vectors of Eq. 13 (Rademacher entries on
+               one colour of the torus colouring, Eq. 15), times spin-colour
+               dilution (Sec. 3: 12 components for full dilution).  The
+               printed Eq. 14 lacks the dagger on the left vector; it is read
+               as v^dagger (equal to v^T for real v).
+  mlmc2        the two-level multigrid MLMC estimator (Eqs. 9-12 with L = 2):
+               X_1 = eta^dag B (D^{-1} - P D_c^{-1} P^dag) eta  on fine noise,
+               X_2 = (P xi)^dag B (P D_c^{-1} xi)             on coarse noise,
+               the second being tr(B P D_c^{-1} P^dag) = tr(P^dag B P D_c^{-1}).
+
+`solve(v)` is any callable returning D^{-1} v for a flat length-12V vector.
+"""
+import numpy as np
+
+from .noise import rademacher, COARSE_STREAM
+from .wilson import gamma5_full, timeslice_of_dof
+
+
+def contract(v, y, dims, gamma5):
+    """X(t) = sum_{j in timeslice t} conj(v_j) (B y)_j, complex array (T,)."""
+    X, Y, Z, T = dims
+    V = X * Y * Z * T
+    by = y * gamma5_full(V) if gamma5 else y
+    prod = np.conj(v) * by
+    return prod.reshape(T, -1).sum(axis=1)
+
+
+def hutchinson(solve, dims, seed, N, gamma5, time_dilution=False, sample0=0):
+    """Per-sample X_i(t), shape (N, T)."""
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    ts = timeslice_of_dof(dims)
+    out = np.zeros((N, T), np.complex128)
+    for i in range(N):
+        eta = rademacher(seed, sample0 + i, n).astype(np.complex128)
+        if time_dilution:
+            for t in range(T):
+                v = np.where(ts == t, eta, 0)
+                out[i] += contract(v, solve(v), dims, gamma5)
+        else:
+            out[i] = contract(eta, solve(eta), dims, gamma5)
+    return out
+
+
+def probing_masks(col, nc, dilution):
+    """Boolean masks (nc*dilution, 12V) of the probing x dilution vectors:
+    colour c of the site (col: per-site colours) and, for dilution 12, the
+    spin-colour component k = 3*spin + colour of the dof."""
+    V = col.shape[0]
+    site_col = np.repeat(col, 12)
+    comp = np.tile(np.arange(12), V)
+    masks = []
+    for c in range(nc):
+        for k in range(dilution):
+            m = site_col == c
+            if dilution == 12:
+                m = m & (comp == k)
+            masks.append(m)
+    return np.array(masks)
+
+
+def probing(solve, dims, seed, N, gamma5, col, nc, dilution, sample0=0):
+    """Per-sample X_i(t) = sum over colours and dilution components, (N, T)."""
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    masks = probing_masks(col, nc, dilution)
+    out = np.zeros((N, T), np.complex128)
+    for i in range(N):
+        eta = rademacher(seed, sample0 + i, n).astype(np.complex128)
+        for m in masks:
+            v = np.where(m, eta, 0)
+            out[i] += contract(v, solve(v), dims, gamma5)
+    return out
+
+
+def mlmc2(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, sample0=0):
+    """Per-sample level values (X1 (N1, T), X2 (N2, T)) of the 2-level estimator."""
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    ncd = P.shape[1]
+    X1 = np.zeros((N1, T), np.complex128)
+    for i in range(N1):
+        eta = rademacher(seed, sample0 + i, n).astype(np.complex128)
+        z = solve(eta)
+        w = P @ solve_coarse(P.conj().T @ eta)
+        X1[i] = contract(eta, z - w, dims, gamma5)
+    X2 = np.zeros((N2, T), np.complex128)
+    for i in range(N2):
+        xi = rademacher(seed, (sample0 + i) | COARSE_STREAM, ncd).astype(np.complex128)
+        X2[i] = contract(P @ xi, P @ solve_coarse(xi), dims, gamma5)
+    return X1, X2
+
+
+def mean_and_variance(samples):
+    """Mean over samples and the sample variance s^2 = sum |X_i - mean|^2/(N-1)
+    (complex modulus), for each column and for the total over columns.
+    Returns (mean (T,), var (T,), mean_total, var_total)."""
+    s = np.asarray(samples)
+    N = s.shape[0]
+    tot = s.sum(axis=1)
+    mean = s.mean(axis=0)
+    mt = tot.mean()
+    if N < 2:
+        return mean, np.full(s.shape[1], np.nan), mt, np.nan
+    var = (np.abs(s - mean) ** 2).sum(axis=0) / (N - 1)
+    vt = (np.abs(tot - mt) ** 2).sum() / (N - 1)
+    return mean, var, mt, vt
+
+
+def hutchinson_variance(A):
+    """Eq. 4: V[eta^T A eta] = 1/2 || offdiag(A + A^T) ||_F^2 (Rademacher eta)."""
+    S = A + A.T
+    S = S - np.diag(np.diag(S))
+    return 0.5 * np.sum(np.abs(S) ** 2)
+
+
+def probing_variance(A, groups):
+    """Variance of sum_g v_g^T A v_g when v_g is eta restricted to the dofs of
+    group g (colour x dilution component): only pairs i != j in the same group
+    contribute, V = 1/2 sum_{i != j, g_i = g_j} |A_ij + A_ji|^2."""
+    S = A + A.T
+    same = groups[:, None] == groups[None, :]
+    np.fill_diagonal(same, False)
+    return 0.5 * np.sum(np.abs(S[same]) ** 2)

@@ -1,0 +1,82 @@
+"""Oracle: aggregation-based two-level hierarchy (test infrastructure only).
+
+Sec. 2: R = P^dagger with P^dagger P = I, and the Galerkin coarse operator
+D_c = P^dagger D P (Eq. 7).  The paper delegates the construction to the
+DD-alpha-AMG setup; reading taken here (the usual aggregation scheme):
+  * the fine lattice is cut into aggregates of agg[mu] sites per direction
+    (4^4 in the large workloads);
+  * every test vector is restricted to each aggregate and to each chirality
+    half (gamma5 = +1: spins 0, 1; gamma5 = -1: spins 2, 3);
+  * the restricted vectors of one (aggregate, half) are orthonormalised by
+    modified Gram-Schmidt in test-vector order.
+Coarse dof index = 2*nv*X_c + nv*h + k (coarse site X_c lexicographic, x fastest;
+half h; test vector k).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+
+def coarse_dims(dims, agg):
+    for L, a in zip(dims, agg):
+        if L % a:
+            raise ValueError('aggregate size must divide the lattice extent')
+    return tuple(L // a for L, a in zip(dims, agg))
+
+
+def aggregate_rows(dims, agg):
+    """For each (coarse site, half): the sorted fine dof indices it owns.
+    Returns an int array (Vc, 2, m) with m = 6 * prod(agg)."""
+    X, Y, Z, T = dims
+    cd = coarse_dims(dims, agg)
+    Vc = int(np.prod(cd))
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X), indexing='ij')
+    site = (x + X * (y + Y * (z + Z * t))).reshape(-1)
+    csite = ((x // agg[0]) + cd[0] * ((y // agg[1]) + cd[1] * ((z // agg[2]) + cd[2] * (t // agg[3])))).reshape(-1)
+    rows = []
+    for c in range(Vc):
+        sites = np.sort(site[csite == c])
+        per = []
+        for h in range(2):
+            d = (12 * sites[:, None] + 3 * (2 * h) + np.arange(6)[None, :]).reshape(-1)
+            per.append(np.sort(d))
+        rows.append(per)
+    return np.array(rows)
+
+
+def mgs(A):
+    """Modified Gram-Schmidt on the columns of A (in column order)."""
+    Q = np.array(A, dtype=np.complex128, copy=True)
+    for k in range(Q.shape[1]):
+        for j in range(k):
+            Q[:, k] -= np.vdot(Q[:, j], Q[:, k]) * Q[:, j]
+        Q[:, k] /= np.linalg.norm(Q[:, k])
+    return Q
+
+
+def prolongator(tv, dims, agg):
+    """P as scipy CSR (12V x 2 nv Vc) from test vectors tv (nv, T, Z, Y, X, 4, 3)."""
+    nv = tv.shape[0]
+    flat = tv.reshape(nv, -1)
+    rows = aggregate_rows(dims, agg)
+    Vc = rows.shape[0]
+    n = flat.shape[1]
+    R, C, Vals = [], [], []
+    for c in range(Vc):
+        for h in range(2):
+            r = rows[c, h]
+            Q = mgs(flat[:, r].T)                # (m, nv)
+            for k in range(nv):
+                R.append(r); C.append(np.full(r.shape, 2 * nv * c + nv * h + k)); Vals.append(Q[:, k])
+    return sp.csr_matrix((np.concatenate(Vals), (np.concatenate(R), np.concatenate(C))),
+                         shape=(n, 2 * nv * Vc))
+
+
+def coarse_operator(Dmat, P):
+    """Eq. 7: D_c = P^dagger D P (sparse)."""
+    Ph = P.conj().T.tocsr()
+    return (Ph @ (Dmat @ P)).tocsr()
+
+
+def gamma5_coarse(nv, Vc):
+    """gamma5 on the coarse space: +1 on half 0, -1 on half 1 of every coarse site."""
+    return np.tile(np.concatenate([np.ones(nv), -np.ones(nv)]), Vc)
