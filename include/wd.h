@@ -1,0 +1,192 @@
+/*
+ * wd.h -- C ABI of libwd, a B300 (sm_103a) engine for the data-parallel hot
+ * path of stochastic trace estimation with the Wilson-Dirac operator:
+ * many-right-hand-side Krylov solves with D, torus-colouring probing with
+ * spin-colour dilution, and two-level multigrid multilevel Monte Carlo.
+ *
+ * Paper: "Variance reduction with probing and Multilevel Monte Carlo in
+ * Lattice QCD" (Frommer, Jimenez-Merchan, Lang, Papace, Ramirez-Hidalgo).
+ * Equations are cited in order of appearance: Eq. 1 noise moments,
+ * Eq. 3 Hutchinson estimator, Eq. 4 its variance, Eq. 7 Galerkin coarse
+ * operator, Eqs. 9-12 level splitting and the multigrid MLMC estimator,
+ * Eqs. 13-14 probing vectors and estimator, Eq. 15 torus colouring,
+ * Eq. 21 the disconnected loop O(t).
+ *
+ * Conventions shared by every entry point
+ *   dims[4] = {X, Y, Z, T}; every extent must be even (even-odd ordering).
+ *   Site index = x + X*(y + Y*(z + Z*t)).
+ *   Gauge field (host, caller owned, read once): complex128 interleaved
+ *     [4][T][Z][Y][X][3][3], entry [mu][t][z][y][x][a][b] = U_mu(x)_{ab},
+ *     mu = 0..3 <-> x, y, z, t.
+ *   Spinor fields (caller owned, DEVICE memory unless stated): complex
+ *     interleaved [nrhs][T][Z][Y][X][4][3] (spin before colour),
+ *     complex128 for WD_FP64 and complex64 for WD_MIXED_FP32 where a
+ *     precision selects the element type; complex128 everywhere else.
+ *   Operator (reading of Sec. 1, which fixes only "12x12 blocks on a
+ *     nearest-neighbour torus"): Wilson hopping form
+ *       D psi(x) = psi(x) - kappa sum_mu [(1-g_mu) U_mu(x) psi(x+mu)
+ *                                        + (1+g_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *     with Hermitian chiral gammas (g5 = diag(1,1,-1,-1)) and a factor bc[mu]
+ *     on hops that wrap around the lattice in direction mu.
+ *   All work is queued on the CUDA stream given to wd_create; entry points
+ *   that return host results synchronise that stream before returning.
+ *   Every entry point returns a wd_status; on failure wd_last_error() gives
+ *   a message (thread-local, valid until the next call on that thread).
+ *   No entry point is safe to call concurrently on the same context.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_ctx wd_ctx;
+
+typedef enum {
+    WD_OK = 0,
+    WD_EINVAL = -1,      /* bad argument (null pointer, odd extent, nrhs < 0, ...) */
+    WD_ENOMEM = -2,      /* device or host allocation failed */
+    WD_ECUDA = -3,       /* a CUDA call failed (message has the CUDA error string) */
+    WD_ENOCONV = -4,     /* a solve hit max_iter; outputs hold the best iterate */
+    WD_EBREAKDOWN = -5,  /* Krylov breakdown (rho, omega ~ 0 or non-finite) */
+    WD_ETIMEOUT = -6,    /* a bounded device wait ran out */
+    WD_ENOTSUP = -7      /* feature not available for these arguments */
+} wd_status;
+
+typedef enum {
+    WD_FP64 = 0,         /* FP64 storage and arithmetic throughout */
+    WD_MIXED_FP32 = 1,   /* FP32 inner Krylov solve inside FP64 defect correction */
+    WD_MIXED_BF16 = 2    /* BF16 storage, FP32 arithmetic inner solve, FP64 outer */
+} wd_prec;
+
+/* trace_estimate methods */
+enum { WD_HUTCH = 0, WD_PROBE = 1, WD_MLMC2 = 2 };
+/* trace_estimate operators B in tr[B D^{-1}(t,t)] */
+enum { WD_TR_DINV = 0, WD_TR_G5_DINV = 1 };
+/* dilution flags: low byte = spin-colour dilution (1 or 12); OR in
+   WD_DIL_TIME to also dilute in time (one timeslice per right-hand side) */
+enum { WD_DIL_TIME = 0x100 };
+
+/* Create a context: uploads the gauge field (a1), folds the boundary factors
+ * into the wrap-around links and builds FP64/FP32/BF16 even-odd copies.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The context owns
+ * every device buffer it allocates; `gauge` is not retained. */
+int wd_create(wd_ctx **out, const int dims[4], const double *gauge, double kappa,
+              const int bc[4], void *stream);
+int wd_destroy(wd_ctx *ctx);
+
+/* y = D x (dagger = 0) or D^dag x (dagger = 1) on nrhs fields (Sec. 1).
+ * in/out: device, complex128 for WD_FP64, complex64 for WD_MIXED_FP32
+ * (then the stencil runs in FP32); WD_MIXED_BF16 takes complex64 fields,
+ * rounds them and the links to BF16 and accumulates in FP32. */
+int wd_apply(wd_ctx *ctx, const void *in, void *out, int nrhs, int prec, int dagger);
+
+/* x = D^{-1} b for nrhs right-hand sides (the D^{-1} eta products of Sec. 1),
+ * even-odd preconditioned BiCGStab.  rhs, x: device complex128.  prec selects
+ * the inner arithmetic; for the mixed modes the outer loop is FP64 defect
+ * correction, so tol (relative FP64 residual ||b - D x|| / ||b|| per RHS) can be
+ * 1e-10 or below.  iters_out[nrhs] (host, nullable): inner iterations summed
+ * over outer steps; true_resid_out[nrhs] (host, nullable): final FP64 relative
+ * residual.  Returns WD_ENOCONV if some RHS missed tol within max_iter inner
+ * iterations (x still holds the best iterate). */
+int wd_solve(wd_ctx *ctx, const double *rhs, double *x, int nrhs, double tol, int prec,
+             int max_iter, int *iters_out, double *true_resid_out);
+
+/* Torus colouring (Sec. 3, Eq. 15): smallest n_c and the lexicographically
+ * first sigma such that c(x) = sum_j sigma_j x_j mod n_c gives different
+ * colours to all sites within torus L1 distance d.  Host only, exact integer
+ * search (n_c ascending, sigma lexicographic, sigma_1 most significant).
+ * dims[nD] (nD = 3 uses X, Y, Z of a timeslice).  colors (host, nullable):
+ * [prod dims] per-site colours, first coordinate fastest.
+ * Returns WD_ENOTSUP if no colouring with n_c <= 4096 exists. */
+int probe_color(const int *dims, int nD, int d, int *n_colors, int *sigma, int32_t *colors);
+
+/* Stochastic trace estimate of tr[B D^{-1}(t,t)] per timeslice (Eq. 21 for
+ * B = g5), B = 1 (WD_TR_DINV) or g5 (WD_TR_G5_DINV).
+ *   WD_HUTCH: Eq. 3 with Rademacher vectors (Sec. 1).
+ *   WD_PROBE: Eqs. 13-14; vectors are Rademacher on one colour of the
+ *             distance-d torus colouring (Eq. 15), times the dilution.
+ *   WD_MLMC2: two-level multigrid MLMC (Eqs. 9-12, L = 2); needs wd_mg_setup.
+ *             N is the level-1 sample count, n2 the level-2 count.
+ * Noise: entry j of sample i is 1 - 2*(top bit of splitmix64(seed ^ (i<<40) ^ j)),
+ * j = 12*site + 3*spin + colour; coarse noise uses sample | 2^23.
+ * dilution: 1 or 12, optionally | WD_DIL_TIME.  batch: RHS solved together
+ * (0 = automatic).  prec, tol: as wd_solve.
+ * Outputs (host): estimate[2*(T+1)] complex mean per timeslice then the total;
+ * sample_var[T+1] sample variance sum |X_i - mean|^2 / (N-1) of the per-sample
+ * values (for WD_MLMC2: V_1/N_1 + V_2/N_2 scaled by N_1, i.e. N_1 times the
+ * variance of the estimate); n_solves_out: number of D (or D_c) solves;
+ * samples_out (nullable): [N][T][2] per-sample values (level 1 for WD_MLMC2). */
+int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, uint64_t seed,
+                   int op, int prec, int batch, double tol, double *estimate, double *sample_var,
+                   int64_t *n_solves_out, double *samples_out);
+
+/* Per-sample level values of the last WD_MLMC2 estimate: level 2 samples
+ * [n2][T][2] (host). */
+int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);
+
+const char *wd_last_error(void);
+
+/* ---- multigrid (Sec. 2) ---------------------------------------------- */
+
+/* Build the aggregation prolongator P and D_c = P^dag D P (Eq. 7).
+ * tv: host complex128 [nv][T][Z][Y][X][4][3] test vectors (nullable: then
+ * nv vectors are generated on the GPU from Rademacher starts with
+ * tv_iters inverse iterations v <- D^{-1} v / ||v|| at tolerance 1e-6).
+ * agg[4]: aggregate extents (must divide dims).  Each test vector is restricted
+ * to each aggregate and chirality half (spins {0,1} / {2,3}) and
+ * orthonormalised by modified Gram-Schmidt in test-vector order; coarse dof
+ * index = 2*nv*Xc + nv*h + k.  Requires nv <= 6 * prod(agg) and 2*nv a
+ * multiple of 8. */
+int wd_mg_setup(wd_ctx *ctx, const double *tv, int nv, const int agg[4], int tv_iters,
+                uint64_t seed);
+
+/* y_c = D_c x_c on the coarse lattice: device complex128 [nrhs][Vc][2nv].
+ * prec WD_FP64 uses FP64 blocks; WD_MIXED_FP32 / WD_MIXED_BF16 run the
+ * 9-point block stencil on tensor cores with BF16 operands, FP32 accumulate. */
+int wd_coarse_apply(wd_ctx *ctx, const double *in, double *out, int nrhs, int prec);
+
+/* Restriction P^dag and prolongation P: fine device complex128
+ * [nrhs][T][Z][Y][X][4][3] <-> coarse [nrhs][Vc][2nv]. */
+int wd_restrict(wd_ctx *ctx, const double *fine, double *coarse, int nrhs);
+int wd_prolong(wd_ctx *ctx, const double *coarse, double *fine, int nrhs);
+
+/* x_c = D_c^{-1} b_c (coarse BiCGStab; FP64 defect correction around a
+ * mixed inner solve when prec != WD_FP64).  Device complex128 [nrhs][Vc][2nv]. */
+int wd_coarse_solve(wd_ctx *ctx, const double *b, double *x, int nrhs, double tol, int prec,
+                    int max_iter, double *true_resid_out);
+
+/* ---- adjoint (derivatives of the estimates) -------------------------- */
+
+/* Link force of X = sum_i w_i^dag ... : for device complex128 fields w, z
+ * [nrhs][T][Z][Y][X][4][3] writes (device, complex128) G and H, each
+ * [4][T][Z][Y][X][3][3], summed over the nrhs fields:
+ *   G_mu(x) = kappa b sum_s z(x+mu)_s [(1-g_mu) w(x)]_s^dag
+ *   H_mu(x) = kappa b sum_s [(1+g_mu) w(x+mu)]_s z(x)_s^dag
+ * (b = bc[mu] on wrapping links, else 1), so that for U -> U + h Delta
+ *   d/dh sum_i (-w_i^dag dD z_i) = sum tr(Delta G) + conj(tr(Delta H)).
+ * accumulate = 1 adds to G, H instead of overwriting. */
+int wd_link_force(wd_ctx *ctx, const double *w, const double *z, int nrhs, double *G, double *H,
+                  int accumulate);
+
+/* Replace the links / kappa of an existing context (same dims and bc). */
+int wd_update_gauge(wd_ctx *ctx, const double *gauge, double kappa);
+
+/* ---- instrumentation ------------------------------------------------- */
+
+/* Kernel timing with CUDA events on the context stream.  kernel ids: */
+enum { WD_K_HOP = 0, WD_K_BLAS = 1, WD_K_COARSE = 2, WD_K_FORCE = 3, WD_K_COUNT = 4 };
+int wd_profile(wd_ctx *ctx, int enable);            /* 1 = start (clears), 0 = stop */
+/* launches, summed event time (ms) and summed algorithmic bytes (or flops for
+   WD_K_COARSE) of the launches of one kernel family since wd_profile(ctx, 1). */
+int wd_profile_get(wd_ctx *ctx, int kernel, int64_t *launches, double *ms, double *bytes);
+/* Number of kernels this context launched since creation (all families). */
+int64_t wd_launch_count(wd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WD_H */

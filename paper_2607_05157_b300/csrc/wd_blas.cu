@@ -1,0 +1,559 @@
+// Krylov BLAS-1 for many right-hand sides on eo fields: layout conversions,
+// precision conversions, fused BiCGStab updates with their dot products,
+// and deterministic two-stage reductions (per-block FP64 partials, then a
+// fixed-order sum), so that every Krylov scalar is an FP64 number.
+//
+// Elementwise kernels treat a parity field as a flat array of complex numbers
+// (rhs-major, 12*Vh per RHS) processed in groups of 4 complex: one 16-byte BF16
+// chunk, two FP32 float4 chunks or four FP64 double2 chunks.
+#include "wd_internal.h"
+
+namespace wd {
+
+template <typename S> struct G4;
+template <> struct G4<double> {
+    typedef double RT;
+    __device__ __forceinline__ static void load(const void *b, long g, cx<double> v[4]) {
+        const double2 *q = (const double2 *)b + 4 * g;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { double2 a = q[j]; v[j] = cmake(a.x, a.y); }
+    }
+    __device__ __forceinline__ static void store(void *b, long g, const cx<double> v[4]) {
+        double2 *q = (double2 *)b + 4 * g;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = make_double2(v[j].re, v[j].im);
+    }
+};
+template <> struct G4<float> {
+    typedef float RT;
+    __device__ __forceinline__ static void load(const void *b, long g, cx<float> v[4]) {
+        const float4 *q = (const float4 *)b + 2 * g;
+        float4 a = q[0], c = q[1];
+        v[0] = cmake(a.x, a.y); v[1] = cmake(a.z, a.w); v[2] = cmake(c.x, c.y); v[3] = cmake(c.z, c.w);
+    }
+    __device__ __forceinline__ static void store(void *b, long g, const cx<float> v[4]) {
+        float4 *q = (float4 *)b + 2 * g;
+        q[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+        q[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
+    }
+};
+template <> struct G4<bf16> {
+    typedef float RT;
+    __device__ __forceinline__ static void load(const void *b, long g, cx<float> v[4]) {
+        uint4 a = ((const uint4 *)b)[g];
+        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&a;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { float2 f = __bfloat1622float2(h[j]); v[j] = cmake(f.x, f.y); }
+    }
+    __device__ __forceinline__ static void store(void *b, long g, const cx<float> v[4]) {
+        uint4 a;
+        __nv_bfloat162 *h = (__nv_bfloat162 *)&a;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[j].re, v[j].im);
+        ((uint4 *)b)[g] = a;
+    }
+};
+
+// load 4 complex of storage S into compute type RT
+template <typename S, typename RT>
+__device__ __forceinline__ void ld4(const void *b, long g, cx<RT> v[4]) {
+    cx<typename G4<S>::RT> t[4];
+    G4<S>::load(b, g, t);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = cmake((RT)t[j].re, (RT)t[j].im);
+}
+template <typename S, typename RT>
+__device__ __forceinline__ void st4(void *b, long g, const cx<RT> v[4]) {
+    typedef typename G4<S>::RT T;
+    cx<T> t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = cmake((T)v[j].re, (T)v[j].im);
+    G4<S>::store(b, g, t);
+}
+
+size_t field_bytes(const Geom &g, int prec, int nrhs) {
+    return (size_t)nrhs * g.Vh * spinor_bytes(prec);
+}
+
+int reduction_bpr(const Geom &g, int nrhs) {
+    // aim for ~4 CTAs of 256 threads per SM over all RHS, >= 8 groups per thread
+    long gpr = 3L * g.Vh;
+    int want = (4 * 148 + nrhs - 1) / (nrhs > 0 ? nrhs : 1);
+    int maxb = (int)((gpr + 2047) / 2048);
+    if (want > maxb) want = maxb;
+    if (want < 1) want = 1;
+    if (want > 256) want = 256;
+    return want;
+}
+
+// ---- block reduction of NQ doubles; thread 0 writes part[(q*nrhs+rhs)*bpr+bx]
+template <int NQ>
+__device__ __forceinline__ void block_partials(double v[NQ], double *part, int nrhs, int bpr) {
+    __shared__ double sh[NQ][32];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q][wid] = v[q];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double a = lane < nw ? sh[q][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) part[((size_t)q * nrhs + blockIdx.y) * bpr + blockIdx.x] = a;
+        }
+    }
+}
+
+__device__ __forceinline__ double sum_part(const double *part, int q, int rhs, int nrhs, int bpr) {
+    const double *p = part + ((size_t)q * nrhs + rhs) * bpr;
+    double a = 0.0;
+    for (int i = 0; i < bpr; ++i) a += p[i];
+    return a;
+}
+
+struct Range { long g0, g1; };
+__device__ __forceinline__ Range my_range(long gpr) {
+    const long chunk = (gpr + gridDim.x - 1) / gridDim.x;
+    Range r;
+    r.g0 = (long)blockIdx.y * gpr + (long)blockIdx.x * chunk;
+    long e = r.g0 + chunk, lim = (long)(blockIdx.y + 1) * gpr;
+    r.g1 = e < lim ? e : lim;
+    return r;
+}
+
+// ---- layout conversion user <-> eo ------------------------------------------
+template <typename TU, typename S>
+__global__ void k_user_to_eo(const TU *user, void *even, void *odd, int nrhs, Geom g) {
+    typedef typename RealOf<S>::type RT;
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long n = (long)g.V * nrhs;
+    if (i >= n) return;
+    const int rhs = (int)(i / g.V), site = (int)(i % g.V);
+    int x = site % g.X, r = site / g.X;
+    int y = r % g.Y; r /= g.Y;
+    int z = r % g.Z, t = r / g.Z;
+    const int p = (x + y + z + t) & 1;
+    const TU *src = user + 24 * i;
+    cx<RT> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = cmake((RT)src[2 * k], (RT)src[2 * k + 1]);
+    constexpr int NCH = SIO<S>::NCH;
+    void *f = p ? odd : even;
+    SIO<S>::store((uint4 *)f + (size_t)rhs * NCH * g.Vh, g.Vh, site >> 1, v);
+}
+
+template <typename S, typename TU>
+__global__ void k_eo_to_user(const void *even, const void *odd, TU *user, int nrhs, Geom g) {
+    typedef typename RealOf<S>::type RT;
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long n = (long)g.V * nrhs;
+    if (i >= n) return;
+    const int rhs = (int)(i / g.V), site = (int)(i % g.V);
+    int x = site % g.X, r = site / g.X;
+    int y = r % g.Y; r /= g.Y;
+    int z = r % g.Z, t = r / g.Z;
+    const int p = (x + y + z + t) & 1;
+    constexpr int NCH = SIO<S>::NCH;
+    const void *f = p ? odd : even;
+    cx<RT> v[12];
+    SIO<S>::load((const uint4 *)f + (size_t)rhs * NCH * g.Vh, g.Vh, site >> 1, v);
+    TU *dst = user + 24 * i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { dst[2 * k] = (TU)v[k].re; dst[2 * k + 1] = (TU)v[k].im; }
+}
+
+#define WD_DISPATCH_PREC(prec, S, ...)                         \
+    do {                                                       \
+        if ((prec) == P64) { typedef double S; __VA_ARGS__; }  \
+        else if ((prec) == P32) { typedef float S; __VA_ARGS__; } \
+        else { typedef bf16 S; __VA_ARGS__; }                  \
+    } while (0)
+
+int user_to_eo(wd_ctx *c, const void *user, bool user_double, int prec, void *even, void *odd, int nrhs) {
+    if (nrhs <= 0) return WD_OK;
+    const long n = (long)c->g.V * nrhs;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((n + th - 1) / th);
+    WD_DISPATCH_PREC(prec, S, {
+        if (user_double) k_user_to_eo<double, S><<<blocks, th, 0, c->st>>>((const double *)user, even, odd, nrhs, c->g);
+        else k_user_to_eo<float, S><<<blocks, th, 0, c->st>>>((const float *)user, even, odd, nrhs, c->g);
+    });
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *user, bool user_double, int nrhs) {
+    if (nrhs <= 0) return WD_OK;
+    const long n = (long)c->g.V * nrhs;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((n + th - 1) / th);
+    WD_DISPATCH_PREC(prec, S, {
+        if (user_double) k_eo_to_user<S, double><<<blocks, th, 0, c->st>>>(even, odd, (double *)user, nrhs, c->g);
+        else k_eo_to_user<S, float><<<blocks, th, 0, c->st>>>(even, odd, (float *)user, nrhs, c->g);
+    });
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// ---- conversions and mixed axpy ---------------------------------------------
+template <typename SA, typename SB>
+__global__ void k_convert(const void *a, void *b, const double *scale, long gpr, long n) {
+    typedef typename G4<SA>::RT RA;
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
+        cx<RA> v[4];
+        ld4<SA, RA>(a, g, v);
+        if (scale) {
+            const RA s = (RA)scale[g / gpr];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = s * v[j];
+        }
+        st4<SB, RA>(b, g, v);
+    }
+}
+
+template <typename SE>
+__global__ void k_axpy_mixed(double *x, const void *e, const double *scale, long gpr, long n) {
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
+        const double s = scale[g / gpr];
+        cx<double> xv[4], ev[4];
+        ld4<double, double>(x, g, xv);
+        ld4<SE, double>(e, g, ev);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { xv[j].re += s * ev[j].re; xv[j].im += s * ev[j].im; }
+        st4<double, double>(x, g, xv);
+    }
+}
+
+static unsigned ew_blocks(long n) {
+    long b = (n + 255) / 256;
+    long cap = 148L * 16;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+int blas_copy_convert(wd_ctx *c, int ps, const void *src, int pd, void *dst, int nrhs, const double *scale) {
+    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    if (n == 0) return WD_OK;
+    WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB, k_convert<SA, SB><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, gpr, n)));
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int blas_axpy_mixed(wd_ctx *c, double *x, int pe, const void *e, const double *scale, int nrhs) {
+    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    if (n == 0) return WD_OK;
+    WD_DISPATCH_PREC(pe, SE, k_axpy_mixed<SE><<<ew_blocks(n), 256, 0, c->st>>>(x, e, scale, gpr, n));
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int blas_zero(wd_ctx *c, void *p, size_t bytes) {
+    WD_CUDA(cudaMemsetAsync(p, 0, bytes, c->st));
+    return WD_OK;
+}
+
+// ---- norms -------------------------------------------------------------------
+template <typename S>
+__global__ void k_norm2_part(const void *a, double *part, long gpr, int nrhs, int bpr) {
+    typedef typename G4<S>::RT RT;
+    Range R = my_range(gpr);
+    RT acc = 0;
+    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
+        cx<RT> v[4];
+        ld4<S, RT>(a, g, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += v[j].re * v[j].re + v[j].im * v[j].im;
+    }
+    double d[1] = {(double)acc};
+    block_partials<1>(d, part, nrhs, bpr);
+}
+
+__global__ void k_sum_partials(const double *part, double *out, int nrhs, int bpr) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x)
+        out[r] = sum_part(part, 0, r, nrhs, bpr);
+}
+
+int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out) {
+    if (nrhs <= 0) return WD_OK;
+    const int bpr = reduction_bpr(c->g, nrhs);
+    double *part;
+    WD_TRY(ws_get(c, "norm_part", sizeof(double) * bpr * nrhs, (void **)&part));
+    const long gpr = 3L * c->g.Vh;
+    dim3 grid(bpr, nrhs);
+    WD_DISPATCH_PREC(prec, S, k_norm2_part<S><<<grid, 256, 0, c->st>>>(a, part, gpr, nrhs, bpr));
+    k_sum_partials<<<(nrhs + 127) / 128, 128, 0, c->st>>>(part, out, nrhs, bpr);
+    c->launches += 2;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// ---- BiCGStab ------------------------------------------------------------------
+// init: x = 0, r = rh = b, p = b (operator precision); partial |b|^2
+template <typename SW, typename SP>
+__global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, double *part, long gpr, int nrhs,
+                            int bpr) {
+    typedef typename G4<SW>::RT RT;
+    Range R = my_range(gpr);
+    RT acc = 0;
+    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
+        cx<RT> v[4], z[4];
+        ld4<SW, RT>(b, g, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { z[j] = cmake(RT(0), RT(0)); acc += v[j].re * v[j].re + v[j].im * v[j].im; }
+        st4<SW, RT>(x, g, z);
+        st4<SW, RT>(r, g, v);
+        st4<SW, RT>(rh, g, v);
+        st4<SP, RT>(p, g, v);
+    }
+    double d[1] = {(double)acc};
+    block_partials<1>(d, part, nrhs, bpr);
+}
+
+__global__ void k_scal_init(BiState *st, const double *part, const double *bnorm2, double tol2, int nrhs, int bpr,
+                            int *count) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+        const double rr = sum_part(part, 0, r, nrhs, bpr);
+        BiState s;
+        s.rho = make_double2(rr, 0.0);
+        s.alpha = make_double2(0.0, 0.0);
+        s.omega = make_double2(0.0, 0.0);
+        s.beta = make_double2(0.0, 0.0);
+        s.rr = rr;
+        s.bb = bnorm2 ? bnorm2[r] : rr;
+        s.thr = tol2 * s.bb;
+        s.iters = 0;
+        s.flag = 0;
+        s.pad = 0;
+        s.active = (rr > s.thr && rr > 0.0 && isfinite(rr)) ? 1 : 0;
+        if (!isfinite(rr)) s.flag = 1;
+        st[r] = s;
+        if (s.active) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count = cnt;
+}
+
+// partial sums of conj(a).b (slots 0, 1) and optionally |a|^2 (slot 2)
+template <typename SA, typename SB, bool NORMA>
+__global__ void k_dot_part(const void *a, const void *b, double *part, long gpr, int nrhs, int bpr) {
+    typedef typename G4<SA>::RT RT;
+    Range R = my_range(gpr);
+    cx<RT> acc = cmake(RT(0), RT(0));
+    RT nn = 0;
+    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
+        cx<RT> va[4], vb[4];
+        ld4<SA, RT>(a, g, va);
+        ld4<SB, RT>(b, g, vb);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cfma_conj(acc, va[j], vb[j]);
+            if (NORMA) nn += va[j].re * va[j].re + va[j].im * va[j].im;
+        }
+    }
+    if (NORMA) {
+        double d[3] = {(double)acc.re, (double)acc.im, (double)nn};
+        block_partials<3>(d, part, nrhs, bpr);
+    } else {
+        double d[2] = {(double)acc.re, (double)acc.im};
+        block_partials<2>(d, part, nrhs, bpr);
+    }
+}
+
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+__global__ void k_scal_alpha(BiState *st, const double *part, int nrhs, int bpr) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
+        BiState &s = st[r];
+        if (!s.active) { s.alpha = make_double2(0, 0); continue; }
+        const double2 d = make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr));
+        double2 al = zdiv(s.rho, d);
+        if ((d.x == 0.0 && d.y == 0.0) || !zfinite(al)) {
+            s.active = 0; s.flag = 1;
+            s.alpha = make_double2(0, 0); s.omega = make_double2(0, 0); s.beta = make_double2(0, 0);
+            continue;
+        }
+        s.alpha = al;
+    }
+}
+
+__global__ void k_scal_omega(BiState *st, const double *part, int nrhs, int bpr) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
+        BiState &s = st[r];
+        if (!s.active) { s.omega = make_double2(0, 0); continue; }
+        const double2 ts = make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr));
+        const double tt = sum_part(part, 2, r, nrhs, bpr);
+        if (tt == 0.0) { s.omega = make_double2(0, 0); continue; }   // t = A s = 0 => s = 0
+        double2 om = make_double2(ts.x / tt, ts.y / tt);
+        if (!zfinite(om)) { s.active = 0; s.flag = 1; s.omega = make_double2(0, 0); s.alpha = make_double2(0, 0); continue; }
+        s.omega = om;
+    }
+}
+
+__global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, int *count) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+        BiState &s = st[r];
+        if (!s.active) { s.beta = make_double2(0, 0); continue; }
+        const double2 rho = make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr));
+        const double rr = sum_part(part, 2, r, nrhs, bpr);
+        s.iters++;
+        s.rr = rr;
+        if (!isfinite(rr)) { s.active = 0; s.flag = 1; }
+        else if (rr <= s.thr) { s.active = 0; }
+        else if ((s.omega.x == 0.0 && s.omega.y == 0.0) || (s.rho.x == 0.0 && s.rho.y == 0.0)) { s.active = 0; s.flag = 1; }
+        if (!s.active) {
+            s.alpha = make_double2(0, 0); s.omega = make_double2(0, 0); s.beta = make_double2(0, 0);
+            continue;
+        }
+        s.beta = zmul(zdiv(rho, s.rho), zdiv(s.alpha, s.omega));
+        s.rho = rho;
+        atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count = cnt;
+}
+
+// s = r - alpha v
+template <typename SW, typename SP>
+__global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long gpr, long n) {
+    typedef typename G4<SW>::RT RT;
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
+        const double2 a = st[g / gpr].alpha;
+        const cx<RT> al = cmake((RT)a.x, (RT)a.y);
+        cx<RT> rv[4], vv[4], o[4];
+        ld4<SW, RT>(r, g, rv);
+        ld4<SW, RT>(v, g, vv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { o[j] = rv[j]; cfma(o[j], cmake(-al.re, -al.im), vv[j]); }
+        st4<SP, RT>(s, g, o);
+    }
+}
+
+// x += alpha p + omega s; r = s - omega t; partials (rh, r) and |r|^2
+template <typename SW, typename SP>
+__global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const void *t, const void *rh,
+                          const BiState *st, double *part, long gpr, int nrhs, int bpr) {
+    typedef typename G4<SW>::RT RT;
+    Range R = my_range(gpr);
+    const double2 a = st[blockIdx.y].alpha, w = st[blockIdx.y].omega;
+    const cx<RT> al = cmake((RT)a.x, (RT)a.y), om = cmake((RT)w.x, (RT)w.y), mom = cmake(-om.re, -om.im);
+    cx<RT> dot = cmake(RT(0), RT(0));
+    RT nn = 0;
+    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
+        cx<RT> xv[4], pv[4], sv[4], tv[4], hv[4];
+        ld4<SW, RT>(x, g, xv);
+        ld4<SP, RT>(p, g, pv);
+        ld4<SP, RT>(s, g, sv);
+        ld4<SW, RT>(t, g, tv);
+        ld4<SW, RT>(rh, g, hv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cfma(xv[j], al, pv[j]);
+            cfma(xv[j], om, sv[j]);
+            cx<RT> rn = sv[j];
+            cfma(rn, mom, tv[j]);
+            cfma_conj(dot, hv[j], rn);
+            nn += rn.re * rn.re + rn.im * rn.im;
+            tv[j] = rn;
+        }
+        st4<SW, RT>(x, g, xv);
+        st4<SW, RT>(r, g, tv);
+    }
+    double d[3] = {(double)dot.re, (double)dot.im, (double)nn};
+    block_partials<3>(d, part, nrhs, bpr);
+}
+
+// p = r + beta (p - omega v)
+template <typename SW, typename SP>
+__global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *st, long gpr, long n) {
+    typedef typename G4<SW>::RT RT;
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
+        const BiState &S = st[g / gpr];
+        const cx<RT> be = cmake((RT)S.beta.x, (RT)S.beta.y), mom = cmake((RT)-S.omega.x, (RT)-S.omega.y);
+        cx<RT> rv[4], pv[4], vv[4];
+        ld4<SW, RT>(r, g, rv);
+        ld4<SP, RT>(p, g, pv);
+        ld4<SW, RT>(v, g, vv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cx<RT> q = pv[j];
+            cfma(q, mom, vv[j]);
+            cx<RT> o = rv[j];
+            cfma(o, be, q);
+            pv[j] = o;
+        }
+        st4<SP, RT>(p, g, pv);
+    }
+}
+
+#define WD_DISPATCH_PAIR(pw, pp, SW, SP, ...)                                         \
+    do {                                                                              \
+        if ((pw) == P64) { typedef double SW; typedef double SP; __VA_ARGS__; }       \
+        else if ((pp) == P32) { typedef float SW; typedef float SP; __VA_ARGS__; }    \
+        else { typedef float SW; typedef bf16 SP; __VA_ARGS__; }                      \
+    } while (0)
+
+int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
+              const double *bnorm2_dev) {
+    const long gpr = 3L * c->g.Vh;
+    dim3 grid(V.bpr, nrhs);
+    WD_DISPATCH_PAIR(pw, pp, SW, SP,
+        k_bicg_init<SW, SP><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, gpr, nrhs, V.bpr));
+    k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count);
+    c->launches += 2;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
+    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    const double k2 = c->kappa * c->kappa;
+    dim3 grid(V.bpr, nrhs);
+    const unsigned eb = ew_blocks(n);
+    const int sb = (nrhs + 127) / 128;
+    // v = A p = p - kappa^2 H_eo H_oe p
+    WD_TRY(hop(c, pp, pp, 1, V.tmp, V.p, nullptr, 0.0, 1.0, nrhs));
+    WD_TRY(hop(c, pp, pw, 0, V.v, V.tmp, V.p, 1.0, -k2, nrhs));
+    WD_DISPATCH_PAIR(pw, pp, SW, SP, {
+        k_dot_part<SW, SW, false><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, gpr, nrhs, V.bpr);
+        k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
+        k_bicg_s<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, gpr, n);
+    });
+    c->launches += 3;
+    // t = A s
+    WD_TRY(hop(c, pp, pp, 1, V.tmp, V.s, nullptr, 0.0, 1.0, nrhs));
+    WD_TRY(hop(c, pp, pw, 0, V.t, V.tmp, V.s, 1.0, -k2, nrhs));
+    WD_DISPATCH_PAIR(pw, pp, SW, SP, {
+        k_dot_part<SW, SP, true><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, gpr, nrhs, V.bpr);
+        k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
+        k_bicg_xr<SW, SP><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, gpr, nrhs, V.bpr);
+        k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
+        k_bicg_p<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, gpr, n);
+    });
+    c->launches += 5;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+}  // namespace wd

@@ -1,0 +1,132 @@
+// Internal declarations of libwd (not part of the C ABI).
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/wd.h"
+#include "wd_common.cuh"
+
+namespace wd {
+
+// ---- errors ----------------------------------------------------------------
+void set_error(const char *fmt, ...);
+#define WD_CUDA(expr)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::wd::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
+            return WD_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+#define WD_TRY(expr)                 \
+    do {                             \
+        int s_ = (expr);             \
+        if (s_ != WD_OK) return s_;  \
+    } while (0)
+
+// ---- kernels ---------------------------------------------------------------
+struct HopArgs {
+    void *out;             // output parity field (rhs 0)
+    const void *in;        // input field of the other parity
+    const void *w;         // same-parity addend (nullable)
+    const void *w2;        // second same-parity addend (nullable)
+    const void *gauge;     // links of the output parity: [8][9][Vh]
+    double a, b, c;        // out = a*w + c*w2 + b*H(in)
+    int p;                 // output parity
+    int nrhs, nrb;
+    Geom g;
+};
+
+template <typename SIn, typename SOut, typename SW, typename G>
+cudaError_t launch_hop(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
+
+// Precision tags of the inner solve
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+// Bytes of one site-spinor (12 complex) and one link (9 complex) per storage
+inline int spinor_bytes(int prec) { return prec == P64 ? 192 : prec == P32 ? 96 : 48; }
+inline int link_bytes(int prec) { return prec == P64 ? 144 : prec == P32 ? 72 : 36; }
+
+// BiCGStab per-RHS state, FP64 scalars
+struct BiState {
+    double2 rho, alpha, omega, beta;
+    double rr, bb, thr;    // |r|^2, |b|^2, convergence threshold on |r|^2
+    int active, flag, iters, pad;
+};
+
+}  // namespace wd
+
+// ---- context ---------------------------------------------------------------
+struct wd_prof_rec {
+    cudaEvent_t a, b;
+    int kernel;
+    double bytes;
+};
+
+struct wd_mg;   // multigrid state (wd_mg.cu)
+
+struct wd_ctx {
+    int dims[4];
+    int bc[4];
+    double kappa;
+    wd::Geom g;
+    cudaStream_t st;
+    void *gauge[3];                 // eo doubled links per precision P64/P32/P16: [2][8][9][Vh]
+    std::map<std::string, std::pair<void *, size_t>> bufs;   // named device workspaces
+    std::map<std::string, std::pair<void *, size_t>> hbufs;  // named pinned host workspaces
+    int64_t launches;
+    bool prof;
+    std::vector<wd_prof_rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+    int hop_R[3];                   // RHS tile per precision (autotuned)
+    int hop_threads[3];
+    wd_mg *mg;
+    std::vector<double> last_level2;    // [n2][T][2]
+    int last_n2;
+};
+
+namespace wd {
+// device workspace by name, grown on demand (contents undefined after growth)
+int ws_get(wd_ctx *c, const char *name, size_t bytes, void **out);
+int hws_get(wd_ctx *c, const char *name, size_t bytes, void **out);
+// profiling brackets around one launch of kernel family `k` moving `bytes`
+void prof_begin(wd_ctx *c, int k, double bytes, int *slot);
+void prof_end(wd_ctx *c, int slot);
+
+// Launch one hop on the context's links: out(parity p) = a*w + c*w2 + b*H(in)
+// for inner precision prec; SIn is the input storage, SOut the output storage.
+int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, const void *w,
+        double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0);
+
+// layout conversions between the user layout and the eo layout
+int user_to_eo(wd_ctx *c, const void *user, bool user_double, int prec, void *even, void *odd, int nrhs);
+int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *user, bool user_double, int nrhs);
+
+// Solver core on eo fields (wd_solver.cu).  b: FP64 eo [2 parities] fields.
+int solve_eo(wd_ctx *c, const double *b_even, const double *b_odd, double *x_even, double *x_odd, int nrhs,
+             double tol, int prec, int max_iter, int *iters_out, double *resid_out);
+
+// blas (wd_blas.cu)
+size_t field_bytes(const Geom &g, int prec, int nrhs);   // one parity
+int blas_copy_convert(wd_ctx *c, int prec_src, const void *src, int prec_dst, void *dst, int nrhs,
+                      const double *scale_dev);
+int blas_axpy_mixed(wd_ctx *c, double *x64, int prec_e, const void *e, const double *scale_dev, int nrhs);
+int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out_dev);
+int blas_zero(wd_ctx *c, void *p, size_t bytes);
+
+// BiCGStab building blocks (wd_blas.cu)
+struct BiVecs {
+    void *x, *r, *rh, *v, *t;   // working precision (SW)
+    void *p, *s;                // operator-input precision (SP)
+    void *tmp;                  // odd-parity intermediate (SP)
+    BiState *st;
+    double *part;               // reduction partials
+    int *count;                 // active count (device)
+    int bpr;                    // reduction blocks per RHS
+};
+int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
+              const double *bnorm2_dev);
+int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
+int reduction_bpr(const Geom &g, int nrhs);
+}  // namespace wd

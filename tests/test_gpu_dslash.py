@@ -1,0 +1,82 @@
+"""Parity of the fine Wilson stencil (row a4, through wd_apply) with the oracle,
+element by element, FP64 / FP32 / BF16, D and D^dag, ragged RHS counts."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import wilson
+from tests.gpu_util import rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+# bounds: FP64 from the benchmark spec's tolerance; FP32 ~ 8 terms of unit size in
+# single precision (eps 6e-8); BF16 storage of links and input (eps 2^-9)
+TOL = {0: 1e-13, 1: 3e-6, 2: 2e-2}
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 8), (6, 2, 4, 2)])
+@pytest.mark.parametrize("nrhs", [1, 3, 5])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_parity(dims, nrhs, prec, dagger):
+    import torch
+    from paper_2607_05157_b300 import Context
+    U = synth.gauge_field(dims, 0.5, 1002)
+    kappa = 0.125
+    psi = synth.spinors(dims, nrhs, 31)
+    ctx = Context(dims, U, kappa, BC)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    y = ctx.apply(to_dev(psi, dt), prec=prec, dagger=dagger).cpu().numpy()
+    f = wilson.apply_dagger if dagger else wilson.apply
+    ref = f(U, psi, kappa, BC)
+    for r in range(nrhs):
+        assert rel(y[r], ref[r]) < TOL[prec], (r, rel(y[r], ref[r]))
+    if prec == 0:
+        assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_apply_full_size_sampled():
+    """16^3 x 32 (the probing workload), 12 RHS in FP32, FP64 on 2: compared on
+    every site of two RHS against the oracle."""
+    import torch
+    from paper_2607_05157_b300 import Context
+    dims = (16, 16, 16, 32)
+    U = synth.gauge_field(dims, 0.5, 1003)
+    psi = synth.spinors(dims, 12, 5)
+    ctx = Context(dims, U, 0.13, BC)
+    y32 = ctx.apply(to_dev(psi, torch.complex64), prec=1).cpu().numpy()
+    y64 = ctx.apply(to_dev(psi[:2]), prec=0).cpu().numpy()
+    for r in (0, 11):
+        ref = wilson.apply(U, psi[r], 0.13, BC)
+        assert rel(y32[r], ref) < TOL[1]
+        if r < 2:
+            assert rel(y64[r], ref) < TOL[0]
+    ref1 = wilson.apply(U, psi[1], 0.13, BC)
+    assert rel(y64[1], ref1) < TOL[0]
+    ctx.close()
+
+
+def test_free_field_plane_wave():
+    """U = 1: D e^{ipx} u = (a + i gamma.b) e^{ipx} u, a property of the
+    operator that holds at any size (checked on 8^3 x 16)."""
+    import torch
+    from paper_2607_05157_b300 import Context
+    from oracle import freefield, gamma
+    dims = (8, 8, 8, 16)
+    X, Y, Z, T = dims
+    kappa = 0.125
+    ctx = Context(dims, synth.unit_gauge(dims), kappa, BC)
+    k = (1, 2, 3, 0)
+    p = [freefield.momenta(L, b)[kk] for L, b, kk in zip(dims, BC, k)]
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X), indexing='ij')
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    u = np.random.default_rng(0).standard_normal((4, 3)) + 0j
+    psi = (phase[..., None, None] * u)[None]
+    out = ctx.apply(to_dev(psi)).cpu().numpy()
+    a = 1 - 2 * kappa * sum(np.cos(q) for q in p)
+    Mp = a * np.eye(4) + 1j * sum(2 * kappa * np.sin(q) * g for q, g in zip(p, gamma.GAMMA))
+    ref = phase[..., None, None] * (Mp @ u)[None]
+    assert np.abs(out[0] - ref).max() < 1e-13
+    ctx.close()

@@ -1,0 +1,76 @@
+"""Parity of the solver path (rows a3-a7): x = D^{-1} b from wd_solve against
+dense LU (4^4 and a ragged small lattice) and, at larger size, against the
+oracle's own operator on the returned x (true FP64 residual)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import solver, wilson
+from tests.gpu_util import rel, to_dev
+
+pytestmark = pytest.mark.gpu
+BC = (1, 1, 1, -1)
+
+
+@pytest.mark.parametrize("dims,kappa,spread", [((4, 4, 4, 4), 0.12, 0.3), ((2, 4, 6, 4), 0.13, 0.5)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_vs_dense(dims, kappa, spread, prec):
+    from paper_2607_05157_b300 import Context
+    U = synth.gauge_field(dims, spread, 1001)
+    b = synth.spinors(dims, 3, 7)
+    ctx = Context(dims, U, kappa, BC)
+    x, it, res = ctx.solve(to_dev(b), tol=1e-10, prec=prec)
+    x = x.cpu().numpy()
+    D = wilson.sparse_matrix(U, kappa, BC).toarray()
+    for r in range(3):
+        xd = np.linalg.solve(D, b[r].reshape(-1))
+        tr = np.linalg.norm(b[r].reshape(-1) - D @ x[r].reshape(-1)) / np.linalg.norm(b[r])
+        assert tr <= 1e-10 * 1.01, tr
+        assert abs(res[r] - tr) < 1e-11
+        assert rel(x[r].reshape(-1), xd) < 1e-8
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_8x8x8x16_true_residual(prec):
+    """The 8^3 x 16 workload (kappa 0.125, spread 0.5): FP64 relative residual
+    <= 1e-10 measured with the oracle's operator."""
+    from paper_2607_05157_b300 import Context
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 0.5, 1002)
+    b = synth.spinors(dims, 4, 8)
+    ctx = Context(dims, U, 0.125, BC)
+    x, it, res = ctx.solve(to_dev(b), tol=1e-10, prec=prec)
+    x = x.cpu().numpy()
+    for r in range(4):
+        tr = np.linalg.norm(b[r] - wilson.apply(U, x[r], 0.125, BC)) / np.linalg.norm(b[r])
+        assert tr <= 1e-10 * 1.01, (r, tr, res[r], it[r])
+    ctx.close()
+
+
+def test_noconv_reported():
+    from paper_2607_05157_b300 import Context, WD_ENOCONV
+    dims = (4, 4, 4, 4)
+    ctx = Context(dims, synth.gauge_field(dims, 0.3, 1), 0.12, BC)
+    b = to_dev(synth.spinors(dims, 2, 1))
+    x, it, res = ctx.solve(b, tol=1e-12, prec=1, max_iter=1, allow_noconv=True)
+    assert np.all(res > 1e-12)
+    import pytest as _p
+    from paper_2607_05157_b300 import WDError
+    with _p.raises(WDError) as e:
+        ctx.solve(b, tol=1e-12, prec=1, max_iter=1)
+    assert e.value.status == WD_ENOCONV
+    ctx.close()
+
+
+def test_zero_rhs():
+    from paper_2607_05157_b300 import Context
+    dims = (4, 4, 4, 4)
+    ctx = Context(dims, synth.gauge_field(dims, 0.3, 1), 0.12, BC)
+    b = np.zeros((2,) + synth.spinors(dims, 1, 0).shape[1:], np.complex128)
+    b[1] = synth.spinors(dims, 1, 3)[0]
+    x, it, res = ctx.solve(to_dev(b), tol=1e-10, prec=1)
+    x = x.cpu().numpy()
+    assert np.all(x[0] == 0) and res[0] == 0
+    assert res[1] <= 1e-10
+    ctx.close()
