@@ -3,83 +3,45 @@
 // and deterministic two-stage reductions (per-block FP64 partials, then a
 // fixed-order sum), so that every Krylov scalar is an FP64 number.
 //
-// Elementwise kernels treat a parity field as a flat array of complex numbers
-// (rhs-major, 12*Vh per RHS) processed in groups of 4 complex: one 16-byte BF16
-// chunk, two FP32 float4 chunks or four FP64 double2 chunks.
+// Elementwise kernels work per (RHS, site) unit: a thread loads the 12
+// complex components of a site of each operand through the layout-aware
+// loaders (the chunk packing differs per precision), so operands of
+// different precisions can be mixed in one kernel.
 #include "wd_internal.h"
 
 namespace wd {
 
-template <typename S> struct G4;
-template <> struct G4<double> {
-    typedef double RT;
-    __device__ __forceinline__ static void load(const void *b, long g, cx<double> v[4]) {
-        const double2 *q = (const double2 *)b + 4 * g;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { double2 a = q[j]; v[j] = cmake(a.x, a.y); }
-    }
-    __device__ __forceinline__ static void store(void *b, long g, const cx<double> v[4]) {
-        double2 *q = (double2 *)b + 4 * g;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = make_double2(v[j].re, v[j].im);
-    }
-};
-template <> struct G4<float> {
-    typedef float RT;
-    __device__ __forceinline__ static void load(const void *b, long g, cx<float> v[4]) {
-        const float4 *q = (const float4 *)b + 2 * g;
-        float4 a = q[0], c = q[1];
-        v[0] = cmake(a.x, a.y); v[1] = cmake(a.z, a.w); v[2] = cmake(c.x, c.y); v[3] = cmake(c.z, c.w);
-    }
-    __device__ __forceinline__ static void store(void *b, long g, const cx<float> v[4]) {
-        float4 *q = (float4 *)b + 2 * g;
-        q[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
-        q[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
-    }
-};
-template <> struct G4<bf16> {
-    typedef float RT;
-    __device__ __forceinline__ static void load(const void *b, long g, cx<float> v[4]) {
-        uint4 a = ((const uint4 *)b)[g];
-        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&a;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { float2 f = __bfloat1622float2(h[j]); v[j] = cmake(f.x, f.y); }
-    }
-    __device__ __forceinline__ static void store(void *b, long g, const cx<float> v[4]) {
-        uint4 a;
-        __nv_bfloat162 *h = (__nv_bfloat162 *)&a;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[j].re, v[j].im);
-        ((uint4 *)b)[g] = a;
-    }
-};
-
-// load 4 complex of storage S into compute type RT
+// Site-level access: unit u = (rhs, site) of a parity field, u = rhs*Vh + s.
+// All elementwise kernels go through the layout-aware SIO loaders, because
+// the chunk packing (and so the flat element order) differs per precision.
 template <typename S, typename RT>
-__device__ __forceinline__ void ld4(const void *b, long g, cx<RT> v[4]) {
-    cx<typename G4<S>::RT> t[4];
-    G4<S>::load(b, g, t);
+__device__ __forceinline__ void ldsite(const void *b, long Vh, long u, cx<RT> v[12]) {
+    typedef typename SIO<S>::real T;
+    const long rhs = u / Vh, s = u - rhs * Vh;
+    cx<T> t[12];
+    SIO<S>::load((const uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = cmake((RT)t[j].re, (RT)t[j].im);
+    for (int j = 0; j < 12; ++j) v[j] = cmake((RT)t[j].re, (RT)t[j].im);
 }
 template <typename S, typename RT>
-__device__ __forceinline__ void st4(void *b, long g, const cx<RT> v[4]) {
-    typedef typename G4<S>::RT T;
-    cx<T> t[4];
+__device__ __forceinline__ void stsite(void *b, long Vh, long u, const cx<RT> v[12]) {
+    typedef typename SIO<S>::real T;
+    const long rhs = u / Vh, s = u - rhs * Vh;
+    cx<T> t[12];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t[j] = cmake((T)v[j].re, (T)v[j].im);
-    G4<S>::store(b, g, t);
+    for (int j = 0; j < 12; ++j) t[j] = cmake((T)v[j].re, (T)v[j].im);
+    SIO<S>::store((uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
 }
+template <typename S> struct RT_of { typedef typename SIO<S>::real type; };
 
 size_t field_bytes(const Geom &g, int prec, int nrhs) {
     return (size_t)nrhs * g.Vh * spinor_bytes(prec);
 }
 
 int reduction_bpr(const Geom &g, int nrhs) {
-    // aim for ~4 CTAs of 256 threads per SM over all RHS, >= 8 groups per thread
-    long gpr = 3L * g.Vh;
+    // aim for ~4 CTAs of 256 threads per SM over all RHS, >= 2 sites per thread
     int want = (4 * 148 + nrhs - 1) / (nrhs > 0 ? nrhs : 1);
-    int maxb = (int)((gpr + 2047) / 2048);
+    int maxb = (int)((g.Vh + 511) / 512);
     if (want > maxb) want = maxb;
     if (want < 1) want = 1;
     if (want > 256) want = 256;
@@ -118,11 +80,12 @@ __device__ __forceinline__ double sum_part(const double *part, int q, int rhs, i
 }
 
 struct Range { long g0, g1; };
-__device__ __forceinline__ Range my_range(long gpr) {
-    const long chunk = (gpr + gridDim.x - 1) / gridDim.x;
+// units [g0, g1) of RHS blockIdx.y handled by block blockIdx.x (per = units per RHS)
+__device__ __forceinline__ Range my_range(long per) {
+    const long chunk = (per + gridDim.x - 1) / gridDim.x;
     Range r;
-    r.g0 = (long)blockIdx.y * gpr + (long)blockIdx.x * chunk;
-    long e = r.g0 + chunk, lim = (long)(blockIdx.y + 1) * gpr;
+    r.g0 = (long)blockIdx.y * per + (long)blockIdx.x * chunk;
+    long e = r.g0 + chunk, lim = (long)(blockIdx.y + 1) * per;
     r.g1 = e < lim ? e : lim;
     return r;
 }
@@ -205,30 +168,30 @@ int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *use
 
 // ---- conversions and mixed axpy ---------------------------------------------
 template <typename SA, typename SB>
-__global__ void k_convert(const void *a, void *b, const double *scale, long gpr, long n) {
-    typedef typename G4<SA>::RT RA;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
-        cx<RA> v[4];
-        ld4<SA, RA>(a, g, v);
+__global__ void k_convert(const void *a, void *b, const double *scale, long Vh, long n) {
+    typedef typename RT_of<SA>::type RA;
+    for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        cx<RA> v[12];
+        ldsite<SA, RA>(a, Vh, u, v);
         if (scale) {
-            const RA s = (RA)scale[g / gpr];
+            const RA s = (RA)scale[u / Vh];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = s * v[j];
+            for (int j = 0; j < 12; ++j) v[j] = s * v[j];
         }
-        st4<SB, RA>(b, g, v);
+        stsite<SB, RA>(b, Vh, u, v);
     }
 }
 
 template <typename SE>
-__global__ void k_axpy_mixed(double *x, const void *e, const double *scale, long gpr, long n) {
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
-        const double s = scale[g / gpr];
-        cx<double> xv[4], ev[4];
-        ld4<double, double>(x, g, xv);
-        ld4<SE, double>(e, g, ev);
+__global__ void k_axpy_mixed(double *x, const void *e, const double *scale, long Vh, long n) {
+    for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        const double s = scale[u / Vh];
+        cx<double> xv[12], ev[12];
+        ldsite<double, double>(x, Vh, u, xv);
+        ldsite<SE, double>(e, Vh, u, ev);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { xv[j].re += s * ev[j].re; xv[j].im += s * ev[j].im; }
-        st4<double, double>(x, g, xv);
+        for (int j = 0; j < 12; ++j) { xv[j].re += s * ev[j].re; xv[j].im += s * ev[j].im; }
+        stsite<double, double>(x, Vh, u, xv);
     }
 }
 
@@ -239,18 +202,18 @@ static unsigned ew_blocks(long n) {
 }
 
 int blas_copy_convert(wd_ctx *c, int ps, const void *src, int pd, void *dst, int nrhs, const double *scale) {
-    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    const long Vh = c->g.Vh, n = Vh * nrhs;
     if (n == 0) return WD_OK;
-    WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB, k_convert<SA, SB><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, gpr, n)));
+    WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB, k_convert<SA, SB><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, Vh, n)));
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
 int blas_axpy_mixed(wd_ctx *c, double *x, int pe, const void *e, const double *scale, int nrhs) {
-    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    const long Vh = c->g.Vh, n = Vh * nrhs;
     if (n == 0) return WD_OK;
-    WD_DISPATCH_PREC(pe, SE, k_axpy_mixed<SE><<<ew_blocks(n), 256, 0, c->st>>>(x, e, scale, gpr, n));
+    WD_DISPATCH_PREC(pe, SE, k_axpy_mixed<SE><<<ew_blocks(n), 256, 0, c->st>>>(x, e, scale, Vh, n));
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
@@ -263,15 +226,15 @@ int blas_zero(wd_ctx *c, void *p, size_t bytes) {
 
 // ---- norms -------------------------------------------------------------------
 template <typename S>
-__global__ void k_norm2_part(const void *a, double *part, long gpr, int nrhs, int bpr) {
-    typedef typename G4<S>::RT RT;
-    Range R = my_range(gpr);
+__global__ void k_norm2_part(const void *a, double *part, long Vh, int nrhs, int bpr) {
+    typedef typename RT_of<S>::type RT;
+    Range R = my_range(Vh);
     RT acc = 0;
-    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
-        cx<RT> v[4];
-        ld4<S, RT>(a, g, v);
+    for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
+        cx<RT> v[12];
+        ldsite<S, RT>(a, Vh, u, v);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc += v[j].re * v[j].re + v[j].im * v[j].im;
+        for (int j = 0; j < 12; ++j) acc += v[j].re * v[j].re + v[j].im * v[j].im;
     }
     double d[1] = {(double)acc};
     block_partials<1>(d, part, nrhs, bpr);
@@ -287,9 +250,9 @@ int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out) {
     const int bpr = reduction_bpr(c->g, nrhs);
     double *part;
     WD_TRY(ws_get(c, "norm_part", sizeof(double) * bpr * nrhs, (void **)&part));
-    const long gpr = 3L * c->g.Vh;
+    const long Vh = c->g.Vh;
     dim3 grid(bpr, nrhs);
-    WD_DISPATCH_PREC(prec, S, k_norm2_part<S><<<grid, 256, 0, c->st>>>(a, part, gpr, nrhs, bpr));
+    WD_DISPATCH_PREC(prec, S, k_norm2_part<S><<<grid, 256, 0, c->st>>>(a, part, Vh, nrhs, bpr));
     k_sum_partials<<<(nrhs + 127) / 128, 128, 0, c->st>>>(part, out, nrhs, bpr);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
@@ -299,20 +262,20 @@ int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out) {
 // ---- BiCGStab ------------------------------------------------------------------
 // init: x = 0, r = rh = b, p = b (operator precision); partial |b|^2
 template <typename SW, typename SP>
-__global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, double *part, long gpr, int nrhs,
+__global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, double *part, long Vh, int nrhs,
                             int bpr) {
-    typedef typename G4<SW>::RT RT;
-    Range R = my_range(gpr);
+    typedef typename RT_of<SW>::type RT;
+    Range R = my_range(Vh);
     RT acc = 0;
-    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
-        cx<RT> v[4], z[4];
-        ld4<SW, RT>(b, g, v);
+    for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
+        cx<RT> v[12], z[12];
+        ldsite<SW, RT>(b, Vh, u, v);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { z[j] = cmake(RT(0), RT(0)); acc += v[j].re * v[j].re + v[j].im * v[j].im; }
-        st4<SW, RT>(x, g, z);
-        st4<SW, RT>(r, g, v);
-        st4<SW, RT>(rh, g, v);
-        st4<SP, RT>(p, g, v);
+        for (int j = 0; j < 12; ++j) { z[j] = cmake(RT(0), RT(0)); acc += v[j].re * v[j].re + v[j].im * v[j].im; }
+        stsite<SW, RT>(x, Vh, u, z);
+        stsite<SW, RT>(r, Vh, u, v);
+        stsite<SW, RT>(rh, Vh, u, v);
+        stsite<SP, RT>(p, Vh, u, v);
     }
     double d[1] = {(double)acc};
     block_partials<1>(d, part, nrhs, bpr);
@@ -347,17 +310,17 @@ __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm
 
 // partial sums of conj(a).b (slots 0, 1) and optionally |a|^2 (slot 2)
 template <typename SA, typename SB, bool NORMA>
-__global__ void k_dot_part(const void *a, const void *b, double *part, long gpr, int nrhs, int bpr) {
-    typedef typename G4<SA>::RT RT;
-    Range R = my_range(gpr);
+__global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, int nrhs, int bpr) {
+    typedef typename RT_of<SA>::type RT;
+    Range R = my_range(Vh);
     cx<RT> acc = cmake(RT(0), RT(0));
     RT nn = 0;
-    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
-        cx<RT> va[4], vb[4];
-        ld4<SA, RT>(a, g, va);
-        ld4<SB, RT>(b, g, vb);
+    for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
+        cx<RT> va[12], vb[12];
+        ldsite<SA, RT>(a, Vh, u, va);
+        ldsite<SB, RT>(b, Vh, u, vb);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 12; ++j) {
             cfma_conj(acc, va[j], vb[j]);
             if (NORMA) nn += va[j].re * va[j].re + va[j].im * va[j].im;
         }
@@ -436,49 +399,49 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
 
 // s = r - alpha v
 template <typename SW, typename SP>
-__global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long gpr, long n) {
-    typedef typename G4<SW>::RT RT;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
-        const double2 a = st[g / gpr].alpha;
-        const cx<RT> al = cmake((RT)a.x, (RT)a.y);
-        cx<RT> rv[4], vv[4], o[4];
-        ld4<SW, RT>(r, g, rv);
-        ld4<SW, RT>(v, g, vv);
+__global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long Vh, long n) {
+    typedef typename RT_of<SW>::type RT;
+    for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        const double2 a = st[u / Vh].alpha;
+        const cx<RT> mal = cmake((RT)-a.x, (RT)-a.y);
+        cx<RT> rv[12], vv[12];
+        ldsite<SW, RT>(r, Vh, u, rv);
+        ldsite<SW, RT>(v, Vh, u, vv);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { o[j] = rv[j]; cfma(o[j], cmake(-al.re, -al.im), vv[j]); }
-        st4<SP, RT>(s, g, o);
+        for (int j = 0; j < 12; ++j) cfma(rv[j], mal, vv[j]);
+        stsite<SP, RT>(s, Vh, u, rv);
     }
 }
 
 // x += alpha p + omega s; r = s - omega t; partials (rh, r) and |r|^2
 template <typename SW, typename SP>
 __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const void *t, const void *rh,
-                          const BiState *st, double *part, long gpr, int nrhs, int bpr) {
-    typedef typename G4<SW>::RT RT;
-    Range R = my_range(gpr);
+                          const BiState *st, double *part, long Vh, int nrhs, int bpr) {
+    typedef typename RT_of<SW>::type RT;
+    Range R = my_range(Vh);
     const double2 a = st[blockIdx.y].alpha, w = st[blockIdx.y].omega;
     const cx<RT> al = cmake((RT)a.x, (RT)a.y), om = cmake((RT)w.x, (RT)w.y), mom = cmake(-om.re, -om.im);
     cx<RT> dot = cmake(RT(0), RT(0));
     RT nn = 0;
-    for (long g = R.g0 + threadIdx.x; g < R.g1; g += blockDim.x) {
-        cx<RT> xv[4], pv[4], sv[4], tv[4], hv[4];
-        ld4<SW, RT>(x, g, xv);
-        ld4<SP, RT>(p, g, pv);
-        ld4<SP, RT>(s, g, sv);
-        ld4<SW, RT>(t, g, tv);
-        ld4<SW, RT>(rh, g, hv);
+    for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
+        cx<RT> xv[12], pv[12], sv[12], tv[12];
+        ldsite<SW, RT>(x, Vh, u, xv);
+        ldsite<SP, RT>(p, Vh, u, pv);
+        ldsite<SP, RT>(s, Vh, u, sv);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            cfma(xv[j], al, pv[j]);
-            cfma(xv[j], om, sv[j]);
+        for (int j = 0; j < 12; ++j) { cfma(xv[j], al, pv[j]); cfma(xv[j], om, sv[j]); }
+        stsite<SW, RT>(x, Vh, u, xv);
+        ldsite<SW, RT>(t, Vh, u, tv);
+        ldsite<SW, RT>(rh, Vh, u, pv);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
             cx<RT> rn = sv[j];
             cfma(rn, mom, tv[j]);
-            cfma_conj(dot, hv[j], rn);
+            cfma_conj(dot, pv[j], rn);
             nn += rn.re * rn.re + rn.im * rn.im;
             tv[j] = rn;
         }
-        st4<SW, RT>(x, g, xv);
-        st4<SW, RT>(r, g, tv);
+        stsite<SW, RT>(r, Vh, u, tv);
     }
     double d[3] = {(double)dot.re, (double)dot.im, (double)nn};
     block_partials<3>(d, part, nrhs, bpr);
@@ -486,24 +449,21 @@ __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const 
 
 // p = r + beta (p - omega v)
 template <typename SW, typename SP>
-__global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *st, long gpr, long n) {
-    typedef typename G4<SW>::RT RT;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x) {
-        const BiState &S = st[g / gpr];
+__global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *st, long Vh, long n) {
+    typedef typename RT_of<SW>::type RT;
+    for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        const BiState &S = st[u / Vh];
         const cx<RT> be = cmake((RT)S.beta.x, (RT)S.beta.y), mom = cmake((RT)-S.omega.x, (RT)-S.omega.y);
-        cx<RT> rv[4], pv[4], vv[4];
-        ld4<SW, RT>(r, g, rv);
-        ld4<SP, RT>(p, g, pv);
-        ld4<SW, RT>(v, g, vv);
+        cx<RT> rv[12], pv[12], vv[12];
+        ldsite<SW, RT>(r, Vh, u, rv);
+        ldsite<SP, RT>(p, Vh, u, pv);
+        ldsite<SW, RT>(v, Vh, u, vv);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            cx<RT> q = pv[j];
-            cfma(q, mom, vv[j]);
-            cx<RT> o = rv[j];
-            cfma(o, be, q);
-            pv[j] = o;
+        for (int j = 0; j < 12; ++j) {
+            cfma(pv[j], mom, vv[j]);
+            cfma(rv[j], be, pv[j]);
         }
-        st4<SP, RT>(p, g, pv);
+        stsite<SP, RT>(p, Vh, u, rv);
     }
 }
 
@@ -516,10 +476,10 @@ __global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *s
 
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev) {
-    const long gpr = 3L * c->g.Vh;
+    const long Vh = c->g.Vh;
     dim3 grid(V.bpr, nrhs);
     WD_DISPATCH_PAIR(pw, pp, SW, SP,
-        k_bicg_init<SW, SP><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, gpr, nrhs, V.bpr));
+        k_bicg_init<SW, SP><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, Vh, nrhs, V.bpr));
     k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
@@ -527,7 +487,7 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
 }
 
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
-    const long gpr = 3L * c->g.Vh, n = gpr * nrhs;
+    const long Vh = c->g.Vh, n = Vh * nrhs;
     const double k2 = c->kappa * c->kappa;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
@@ -536,20 +496,20 @@ int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     WD_TRY(hop(c, pp, pp, 1, V.tmp, V.p, nullptr, 0.0, 1.0, nrhs));
     WD_TRY(hop(c, pp, pw, 0, V.v, V.tmp, V.p, 1.0, -k2, nrhs));
     WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SW, false><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, gpr, nrhs, V.bpr);
+        k_dot_part<SW, SW, false><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr);
         k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
-        k_bicg_s<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, gpr, n);
+        k_bicg_s<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
     });
     c->launches += 3;
     // t = A s
     WD_TRY(hop(c, pp, pp, 1, V.tmp, V.s, nullptr, 0.0, 1.0, nrhs));
     WD_TRY(hop(c, pp, pw, 0, V.t, V.tmp, V.s, 1.0, -k2, nrhs));
     WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SP, true><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, gpr, nrhs, V.bpr);
+        k_dot_part<SW, SP, true><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr);
         k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
-        k_bicg_xr<SW, SP><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, gpr, nrhs, V.bpr);
+        k_bicg_xr<SW, SP><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
         k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
-        k_bicg_p<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, gpr, n);
+        k_bicg_p<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
     });
     c->launches += 5;
     WD_CUDA(cudaGetLastError());
