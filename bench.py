@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the trace-estimation hot path on B300.
+
+Workload (the 8^3 x 16 configuration): Wilson-Dirac operator on an 8^3 x 16
+lattice (antiperiodic in t), kappa = 0.125, synthetic SU(3) links
+(Gram-Schmidt projection of I + 0.5 G, seed 1002) standing in for the paper's
+RQCD ensemble; per step and per GPU 256 right-hand sides = 16 Rademacher
+samples x 16 timeslices (time dilution), estimating the disconnected loop
+O(t) = tr[g5 D^{-1}(t,t)] (Eq. 21), each solve to a true FP64 relative
+residual of 1e-10 by FP32 (or BF16) BiCGStab inside FP64 defect correction.
+
+A step = one trace_estimate call: RHS generation on the device, even-odd
+source, 256-RHS batched mixed-precision solve (stencil, BLAS-1, FP64 residual),
+odd-site reconstruction, FP64 per-timeslice contraction, mean and sample
+variance.  `value` = algorithmic stencil bytes moved by all stencil launches
+of the step / step time (GB/s), so it is the whole job's rate in the metric's
+unit; `roofline` gives the dominant kernel (the FP32/BF16 stencil) against the
+measured HBM copy bandwidth.  `trace_time` compares, at the same noise and so
+the same statistical error, the mixed batched path with the plain FP64
+single-RHS path on the same GPU (the second half of the metric).
+
+python bench.py [--gpus N --steps K --warmup W --prec fp32|bf16 --impl wd|reference]
+Under torchrun each rank draws its own samples (seed offset by rank): no
+collective on the data path; one barrier and a max/sum over ranks of the
+timing only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (8, 8, 8, 16)
+KAPPA = 0.125
+SPREAD = 0.5
+GAUGE_SEED = 1002
+NOISE_SEED = 2002
+SAMPLES = 16
+TOL = 1e-10
+BC = (1, 1, 1, -1)
+METRIC = "Dslash GB/s (% HBM peak); trace time at fixed error, mixed+batched vs FP64"
+WORKLOAD = "8^3x16 Wilson-Dirac, kappa 0.125, 256 time-diluted Rademacher RHS, tr[g5 D^-1(t,t)] to 1e-10"
+
+
+def env_rank():
+    return int(os.environ.get('RANK', 0)), int(os.environ.get('WORLD_SIZE', 1)), int(os.environ.get('LOCAL_RANK', 0))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+    Q = ('clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(['nvidia-smi', '-i', str(self.idx), '--query-gpu=' + self.Q,
+                                       '--format=csv,noheader,nounits', '-lms', '200'],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ''
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ''
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for line in (self.out or '').splitlines():
+            f = [x.strip() for x in line.split(',')]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower().startswith('active'):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hop_traffic(prec):
+    """DRAM bytes per stencil launch from the committed ncu summary, if it was
+    taken on the current stencil source (else None)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, 'profiles', 'hop_traffic.json')))
+        src = open(os.path.join(ROOT, 'paper_2607_05157_b300', 'csrc', 'wd_dslash.cu'), 'rb').read()
+        if rec.get('source_sha256') != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get(prec, {}).get('dram_bytes_per_launch')
+    except Exception:
+        return None
+
+
+def oracle_baseline(n_timeslices=3):
+    """The FP64 CPU oracle on a bounded sample of the same workload: the
+    time-diluted solves of sample 0 for the first n timeslices (plain
+    BiCGStab on D, contraction).  Returns (GB/s of algorithmic stencil bytes,
+    seconds, applies)."""
+    import numpy as np
+    from threadpoolctl import threadpool_limits
+    import synth
+    from oracle import estimators, noise, solver, wilson
+    U = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
+    V = int(np.prod(DIMS))
+    shape = (DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3)
+    napply = [0]
+
+    def A(v):
+        napply[0] += 1
+        return wilson.apply(U, v.reshape(shape), KAPPA, BC)
+    eta = noise.rademacher(NOISE_SEED, 0, 12 * V)
+    ts = wilson.timeslice_of_dof(DIMS)
+    with threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        for t in range(n_timeslices):
+            v = np.where(ts == t, eta, 0).astype(complex)
+            x, it, res = solver.bicgstab(A, v, tol=TOL)
+            estimators.contract(v, x.reshape(-1), DIMS, True)
+        dt = time.perf_counter() - t0
+    # same byte model as the GPU stencil: FP64, one RHS, in + out + addend spinors
+    # and 8 links per output site, two half-lattice hops per application of D
+    bytes_per_apply = V * (3 * 192 + 8 * 144)
+    return napply[0] * bytes_per_apply / dt / 1e9, dt, napply[0]
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; skip untimed steps
+    t_all = 0.0
+    for _ in range(args.steps):
+        gbs, dt, n = oracle_baseline(1)
+        vals.append(gbs)
+        t_all += dt
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: one time-diluted solve per step)"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "one time-diluted RHS of sample 0 per step (1/256 of the GPU step)"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=20)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--prec', choices=['fp32', 'bf16'], default='fp32')
+    ap.add_argument('--impl', choices=['wd', 'reference'], default='wd')
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-fp64-compare', action='store_true')
+    args = ap.parse_args()
+    if args.impl == 'reference':
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    import synth
+    import paper_2607_05157_b300 as wd
+    from paper_2607_05157_b300 import api
+
+    prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
+    T = DIMS[3]
+    gauge = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
+    ctx = wd.Context(DIMS, gauge, KAPPA, BC)
+    seed0 = NOISE_SEED + 7919 * rank
+
+    def step(i, p=prec, batch=SAMPLES * T):
+        return api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, SAMPLES, T, seed=seed0 + i, op=1,
+                                  prec=p, batch=batch, tol=TOL)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = api.wd_launch_count(ctx.h)
+    api.wd_profile(ctx.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        results = [step(1000 + i) for i in range(args.steps)]
+        ev1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = api.wd_launch_count(ctx.h) - l0
+    n_hop, ms_hop, by_hop = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
+    n_h64, ms_h64, by_h64 = api.wd_profile_get(ctx.h, wd.WD_K_HOP64)
+    api.wd_profile(ctx.h, False)
+    step_bytes = by_hop + by_h64
+    if dist:
+        t = torch.tensor([ms, step_bytes], dtype=torch.float64, device='cuda')
+        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, step_bytes = float(mx[0]), float(sm[1])
+    value = step_bytes / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: host (pinned) links uploaded and
+    # re-ingested every step, estimates read back to the host
+    pinned = torch.from_numpy(gauge.view(np.float64)).pin_memory()
+    gptr = pinned.data_ptr()
+    import ctypes
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.wd_profile(ctx.h, True)
+    e0.record()
+    for i in range(args.steps):
+        wd.lib.wd_update_gauge(ctx.h, ctypes.c_void_p(gptr), ctypes.c_double(KAPPA))
+        step(2000 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1)
+    _, _, eb1 = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
+    _, _, eb2 = api.wd_profile_get(ctx.h, wd.WD_K_HOP64)
+    api.wd_profile(ctx.h, False)
+    e_bytes = eb1 + eb2
+    if dist:
+        t = torch.tensor([e_ms, e_bytes], dtype=torch.float64, device='cuda')
+        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        e_ms, e_bytes = float(mx[0]), float(sm[1])
+    h2d = gauge.nbytes
+    d2h = 8 * (2 * (T + 1) + (T + 1))
+
+    peaks = measured_peaks()
+    peak = peaks['hbm_gbs'] if peaks else 6400.0
+    achieved = (by_hop / n_hop) / (ms_hop / n_hop * 1e-3) / 1e9 if n_hop else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": hop_traffic(args.prec),
+            "kernel": f"hop_kernel ({args.prec} storage, {n_hop // max(args.steps, 1)} launches/step, "
+                      f"{by_hop / max(n_hop, 1) / 1e6:.1f} MB algorithmic per launch)",
+            "peak_source": "measured" if peaks else "fallback",
+            "share_of_step": ms_hop / ms if ms else None,
+            "fp64_stencil": {"launches_per_step": n_h64 // max(args.steps, 1),
+                             "GB_s": (by_h64 / (ms_h64 * 1e-3) / 1e9) if ms_h64 else None,
+                             "share_of_step": ms_h64 / ms if ms else None}}
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.prec == 'fp32' else "bf16+f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "kappa": KAPPA,
+                       "rhs_per_step_per_gpu": SAMPLES * T, "inner_precision": args.prec,
+                       "l2": "inputs larger than L2 (each stencil launch streams >100 MB)",
+                       "parallelism": f"replicas x{world} (independent samples)"},
+            "roofline": roof, "clocks": clk.summary(),
+            "e2e": {"value": e_bytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps},
+            "gpu_launches": launches,
+            "solves_per_step": results[-1]['n_solves']}
+
+    if rank == 0 and not args.no_fp64_compare:
+        # trace time at fixed error: same noise (so the same estimate and error)
+        # through the plain FP64 single-RHS path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ref = step(1000, p=wd.WD_FP64, batch=1)
+        torch.cuda.synchronize()
+        t_fp64 = time.perf_counter() - t0
+        mix = results[0]
+        eps = (mix['var_total'] / SAMPLES) ** 0.5
+        line["trace_time"] = {"mixed_batched_ms": ms / args.steps, "fp64_single_rhs_ms": 1e3 * t_fp64,
+                              "speedup": 1e3 * t_fp64 / (ms / args.steps),
+                              "estimate_diff_over_eps": abs(mix['total'] - ref['total']) / eps,
+                              "std_error_eps": eps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gbs, dt, n = oracle_baseline(3)
+        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"3 of the 256 time-diluted solves of one step ({dt:.1f} s, {n} applies of D)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

@@ -177,8 +177,10 @@ int wd_update_gauge(wd_ctx *ctx, const double *gauge, double kappa);
 
 /* ---- instrumentation ------------------------------------------------- */
 
-/* Kernel timing with CUDA events on the context stream.  kernel ids: */
-enum { WD_K_HOP = 0, WD_K_BLAS = 1, WD_K_COARSE = 2, WD_K_FORCE = 3, WD_K_COUNT = 4 };
+/* Kernel timing with CUDA events on the context stream.  kernel ids:
+   WD_K_HOP fine stencil in FP32/BF16 storage, WD_K_HOP64 fine stencil in FP64,
+   WD_K_COARSE coarse block stencil, WD_K_FORCE link force, WD_K_BLAS unused. */
+enum { WD_K_HOP = 0, WD_K_BLAS = 1, WD_K_COARSE = 2, WD_K_FORCE = 3, WD_K_HOP64 = 4, WD_K_COUNT = 5 };
 int wd_profile(wd_ctx *ctx, int enable);            /* 1 = start (clears), 0 = stop */
 /* launches, summed event time (ms) and summed algorithmic bytes (or flops for
    WD_K_COARSE) of the launches of one kernel family since wd_profile(ctx, 1). */

@@ -10,7 +10,7 @@ WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16 = 0, 1, 2
 WD_HUTCH, WD_PROBE, WD_MLMC2 = 0, 1, 2
 WD_TR_DINV, WD_TR_G5_DINV = 0, 1
 WD_DIL_TIME = 0x100
-WD_K_HOP, WD_K_BLAS, WD_K_COARSE, WD_K_FORCE, WD_K_COUNT = 0, 1, 2, 3, 4
+WD_K_HOP, WD_K_BLAS, WD_K_COARSE, WD_K_FORCE, WD_K_HOP64, WD_K_COUNT = 0, 1, 2, 3, 4, 5
 
 _NAMES = {0: 'WD_OK', -1: 'WD_EINVAL', -2: 'WD_ENOMEM', -3: 'WD_ECUDA', -4: 'WD_ENOCONV',
           -5: 'WD_EBREAKDOWN', -6: 'WD_ETIMEOUT', -7: 'WD_ENOTSUP'}

@@ -102,7 +102,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     const double bytes = (double)c->g.Vh *
                          (nrhs * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
-    prof_begin(c, WD_K_HOP, bytes, &slot);
+    prof_begin(c, pin == P64 ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
     cudaError_t e;
     if (pin == P64) e = launch_hop<double, double, double, double>(A, R, dag, th, c->st);
     else if (pin == P32) e = launch_hop<float, float, float, float>(A, R, dag, th, c->st);

@@ -1,0 +1,306 @@
+// Trace estimators (rows a2, a9): Hutchinson (Eq. 3) and stochastic probing
+// with spin-colour / time dilution (Eqs. 13-14), estimating
+// tr[B D^{-1}(t, t)] per timeslice with B = 1 or gamma5 (Eq. 21).
+//
+// The right-hand sides are never stored on the host and never read back:
+//  * k_gen_rhs writes them straight into the FP64 eo fields from a counter
+//    hash -- entry j = 12*site + 3*spin + colour of noise sample i is
+//    1 - 2*topbit(splitmix64(seed ^ (i << 40) ^ j)) (Rademacher, Sec. 1),
+//    masked to one colour c(x) = sum_j sigma_j x_j mod n_c of the torus
+//    colouring (Eq. 15), one spin-colour component and/or one timeslice;
+//  * k_contract regenerates the same entries while it forms
+//    X(t) = sum_{x in t} conj(v(x)) (B D^{-1} v)(x) in FP64.
+// Right-hand sides are enumerated sample-major, (sample, colour, component,
+// timeslice), and solved in batches; per-sample values are accumulated in
+// that fixed order, so results are deterministic.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "wd_internal.h"
+
+namespace wd {
+
+struct EstParams {
+    unsigned long long seed;
+    int m;          // right-hand sides per sample
+    int nc;         // colours (1 = no colour mask)
+    int sigma[4];
+    int dil;        // spin-colour dilution 1 or 12
+    int TT;         // timeslices per sample (1 = no time dilution)
+    int g0;         // global index of the first RHS of the batch
+    int nrhs;       // RHS in this batch
+    int gamma5;     // B = gamma5 (1) or 1 (0)
+    int stream_hi;  // coarse-noise stream bit (0 here)
+};
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Rademacher entry of dof j for noise sample `sample`
+__device__ __forceinline__ double rademacher(unsigned long long seed, unsigned long long sample, unsigned long long j) {
+    const unsigned long long h = splitmix64(seed ^ (sample << 40) ^ j);
+    return (h >> 63) ? -1.0 : 1.0;
+}
+
+struct RhsDesc { int sample, colour, comp, tslice; };
+
+__device__ __forceinline__ RhsDesc describe(const EstParams &P, int g) {
+    RhsDesc d;
+    d.sample = g / P.m;
+    int j = g - d.sample * P.m;
+    d.tslice = P.TT > 1 ? j % P.TT : -1;
+    j /= P.TT;
+    d.comp = P.dil > 1 ? j % P.dil : -1;
+    j /= P.dil;
+    d.colour = P.nc > 1 ? j : -1;
+    return d;
+}
+
+// fills v[12] with the masked noise of site (x,y,z,t); returns false if the whole site is masked
+__device__ __forceinline__ bool site_noise(const EstParams &P, const Geom &g, const RhsDesc &d, int x, int y, int z,
+                                           int t, cx<double> v[12]) {
+    bool on = true;
+    if (d.tslice >= 0 && t != d.tslice) on = false;
+    if (d.colour >= 0) {
+        const long c = (long)P.sigma[0] * x + (long)P.sigma[1] * y + (long)P.sigma[2] * z + (long)P.sigma[3] * t;
+        if ((int)(c % P.nc) != d.colour) on = false;
+    }
+    const unsigned long long site = (unsigned long long)(x + g.X * (y + g.Y * (z + (long)g.Z * t)));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double e = 0.0;
+        if (on && (d.comp < 0 || d.comp == k)) e = rademacher(P.seed, (unsigned long long)d.sample, 12ULL * site + k);
+        v[k] = cmake(e, 0.0);
+    }
+    return on;
+}
+
+// b (FP64 eo, both parities) for the RHS of the batch
+__global__ void k_gen_rhs(EstParams P, Geom g, double *be, double *bo) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)g.V * P.nrhs) return;
+    const int r = (int)(i / g.V), site = (int)(i % g.V);
+    int x = site % g.X, rr = site / g.X;
+    int y = rr % g.Y; rr /= g.Y;
+    int z = rr % g.Z, t = rr / g.Z;
+    const RhsDesc d = describe(P, P.g0 + r);
+    cx<double> v[12];
+    site_noise(P, g, d, x, y, z, t, v);
+    const int p = (x + y + z + t) & 1;
+    SIO<double>::store((uint4 *)(p ? bo : be) + (size_t)r * 12 * g.Vh, g.Vh, site >> 1, v);
+}
+
+// partial X(rhs, t) over a chunk of timeslice t, both parities.
+// grid (bps, nrhs, T); part[((rhs*T + t)*bps + bx)*2 + {re,im}]
+__global__ void k_contract(EstParams P, Geom g, const double *xe, const double *xo, double *part, int bps) {
+    const int r = blockIdx.y, t = blockIdx.z;
+    const RhsDesc d = describe(P, P.g0 + r);
+    const int slice = g.Vh / g.T;          // half-sites per timeslice and parity
+    double are = 0.0, aim = 0.0;
+    if (d.tslice < 0 || d.tslice == t) {
+        const int chunk = (2 * slice + bps - 1) / bps;
+        const int u0 = blockIdx.x * chunk, u1 = min(u0 + chunk, 2 * slice);
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const int p = u >= slice, s = t * slice + (u - p * slice);
+            int x, y, z, tt;
+            eo_coords(g, p, s, x, y, z, tt);
+            cx<double> v[12];
+            if (!site_noise(P, g, d, x, y, z, tt, v)) continue;
+            cx<double> sol[12];
+            SIO<double>::load((const uint4 *)(p ? xo : xe) + (size_t)r * 12 * g.Vh, g.Vh, s, sol);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const double sg = (P.gamma5 && k >= 6) ? -1.0 : 1.0;   // gamma5 = diag(1,1,-1,-1)
+                // conj(v) * B sol with v real
+                are += sg * v[k].re * sol[k].re;
+                aim += sg * v[k].re * sol[k].im;
+            }
+        }
+    }
+    // block reduce
+    __shared__ double sh[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_xor_sync(0xffffffffu, are, o);
+        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { sh[0][wid] = are; sh[1][wid] = aim; }
+    __syncthreads();
+    if (wid == 0) {
+        are = lane < nw ? sh[0][lane] : 0.0;
+        aim = lane < nw ? sh[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            are += __shfl_xor_sync(0xffffffffu, are, o);
+            aim += __shfl_xor_sync(0xffffffffu, aim, o);
+        }
+        if (lane == 0) {
+            double *q = part + (((size_t)r * g.T + t) * bps + blockIdx.x) * 2;
+            q[0] = are;
+            q[1] = aim;
+        }
+    }
+}
+
+// X[sample][t] += sum over this batch's RHS of that sample (fixed order)
+__global__ void k_accumulate(EstParams P, int T, const double *part, int bps, double *X, int first_sample,
+                             int nsamples) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nsamples * T) return;
+    const int si = first_sample + idx / T, t = idx % T;
+    const int a = max(P.g0, si * P.m), b = min(P.g0 + P.nrhs, (si + 1) * P.m);
+    double re = 0.0, im = 0.0;
+    for (int gidx = a; gidx < b; ++gidx) {
+        const double *q = part + ((size_t)(gidx - P.g0) * T + t) * bps * 2;
+        for (int k = 0; k < bps; ++k) { re += q[2 * k]; im += q[2 * k + 1]; }
+    }
+    X[((size_t)si * T + t) * 2] += re;
+    X[((size_t)si * T + t) * 2 + 1] += im;
+}
+
+// mean and sample variance per timeslice and of the total over timeslices.
+// out_mean[2*(T+1)], out_var[T+1]
+__global__ void k_mean_var(const double *X, int N, int T, double *out_mean, double *out_var) {
+    for (int t = threadIdx.x; t <= T; t += blockDim.x) {
+        double mr = 0, mi = 0;
+        for (int i = 0; i < N; ++i) {
+            double xr = 0, xi = 0;
+            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
+            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+            mr += xr; mi += xi;
+        }
+        mr /= N; mi /= N;
+        double v = 0;
+        for (int i = 0; i < N; ++i) {
+            double xr = 0, xi = 0;
+            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
+            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+            v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
+        }
+        out_mean[2 * t] = mr;
+        out_mean[2 * t + 1] = mi;
+        out_var[t] = N > 1 ? v / (N - 1) : NAN;
+    }
+}
+
+// Solve + contract a sample-major range of right-hand sides, accumulating into
+// X (device, [N][T][2]).  Used by every estimator.
+int estimate_rhs_range(wd_ctx *c, EstParams P, int total, int batch, double tol, int prec, double *X, int64_t *nsolves) {
+    const Geom &g = c->g;
+    const int T = g.T;
+    for (int g0 = 0; g0 < total; g0 += batch) {
+        const int nb = min(batch, total - g0);
+        P.g0 = g0;
+        P.nrhs = nb;
+        const size_t f = field_bytes(g, P64, nb);
+        double *be, *bo, *xe, *xo, *part;
+        WD_TRY(ws_get(c, "est.be", f, (void **)&be));
+        WD_TRY(ws_get(c, "est.bo", f, (void **)&bo));
+        WD_TRY(ws_get(c, "est.xe", f, (void **)&xe));
+        WD_TRY(ws_get(c, "est.xo", f, (void **)&xo));
+        const int slice2 = 2 * (g.Vh / T);
+        int bps = (slice2 + 1023) / 1024;
+        if (bps < 1) bps = 1;
+        WD_TRY(ws_get(c, "est.part", sizeof(double) * 2 * (size_t)nb * T * bps, (void **)&part));
+        const long n = (long)g.V * nb;
+        k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, g, be, bo);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
+        int s = solve_eo(c, be, bo, xe, xo, nb, tol, prec, 100000, nullptr, nullptr);
+        if (s != WD_OK) return s;
+        k_contract<<<dim3(bps, nb, T), 256, 0, c->st>>>(P, g, xe, xo, part, bps);
+        const int s_first = g0 / P.m, s_last = (g0 + nb - 1) / P.m;
+        const int ns = s_last - s_first + 1;
+        k_accumulate<<<(ns * T + 127) / 128, 128, 0, c->st>>>(P, T, part, bps, X, s_first, ns);
+        c->launches += 2;
+        WD_CUDA(cudaGetLastError());
+        *nsolves += nb;
+    }
+    return WD_OK;
+}
+
+int auto_batch(wd_ctx *c, int total) {
+    // FP64 eo fields of the estimator and the solver (~14 half-fields) plus the
+    // FP32 Krylov vectors (8 half-fields) per RHS; keep the batch under ~48 GB
+    const double per = (double)c->g.Vh * (14 * 192.0 + 8 * 96.0);
+    int b = (int)(48e9 / per);
+    if (b > 384) b = 384;
+    if (b < 1) b = 1;
+    return b < total ? b : total;
+}
+
+int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double *sample_var, double *samples_out) {
+    const int T = c->g.T;
+    double *mean, *var;
+    WD_TRY(ws_get(c, "est.mean", sizeof(double) * 2 * (T + 1), (void **)&mean));
+    WD_TRY(ws_get(c, "est.var", sizeof(double) * (T + 1), (void **)&var));
+    k_mean_var<<<1, 128, 0, c->st>>>(X, N, T, mean, var);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    WD_CUDA(cudaMemcpyAsync(estimate, mean, sizeof(double) * 2 * (T + 1), cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaMemcpyAsync(sample_var, var, sizeof(double) * (T + 1), cudaMemcpyDeviceToHost, c->st));
+    if (samples_out)
+        WD_CUDA(cudaMemcpyAsync(samples_out, X, sizeof(double) * 2 * (size_t)N * T, cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    return WD_OK;
+}
+
+int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
+                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out);
+
+}  // namespace wd
+
+using namespace wd;
+
+extern "C" int trace_estimate(wd_ctx *c, int method, int dilution, int N, int n2, int d, uint64_t seed, int op,
+                              int prec, int batch, double tol, double *estimate, double *sample_var,
+                              int64_t *n_solves_out, double *samples_out) {
+    if (!c || !estimate || !sample_var || N < 1 || prec < 0 || prec > 2 || !(tol > 0) || (op != 0 && op != 1)) {
+        set_error("trace_estimate: bad argument");
+        return WD_EINVAL;
+    }
+    const int dil = dilution & 0xff;
+    const bool tdil = (dilution & WD_DIL_TIME) != 0;
+    if (dil != 1 && dil != 12) { set_error("trace_estimate: dilution must be 1 or 12 (optionally | WD_DIL_TIME)"); return WD_EINVAL; }
+    int64_t ns = 0;
+    if (method == WD_MLMC2) {
+        if (n2 < 1) { set_error("trace_estimate: MLMC2 needs n2 >= 1"); return WD_EINVAL; }
+        int s = mlmc2_estimate(c, N, n2, seed, op, prec, batch, tol, estimate, sample_var, &ns, samples_out);
+        if (n_solves_out) *n_solves_out = ns;
+        return s;
+    }
+    if (method != WD_HUTCH && method != WD_PROBE) { set_error("trace_estimate: unknown method %d", method); return WD_EINVAL; }
+    EstParams P;
+    memset(&P, 0, sizeof(P));
+    P.seed = seed;
+    P.dil = dil;
+    P.TT = tdil ? c->g.T : 1;
+    P.gamma5 = op == WD_TR_G5_DINV;
+    P.nc = 1;
+    if (method == WD_PROBE) {
+        int nc = 0, sig[4];
+        const int s = probe_color(c->dims, 4, d, &nc, sig, nullptr);
+        if (s != WD_OK) { set_error("trace_estimate: no torus colouring for distance %d", d); return s; }
+        P.nc = nc;
+        for (int j = 0; j < 4; ++j) P.sigma[j] = sig[j];
+    }
+    P.m = P.nc * P.dil * P.TT;
+    const long total = (long)N * P.m;
+    if (total > (1L << 30)) { set_error("trace_estimate: too many right-hand sides"); return WD_EINVAL; }
+    const int T = c->g.T;
+    double *X;
+    WD_TRY(ws_get(c, "est.X", sizeof(double) * 2 * (size_t)N * T, (void **)&X));
+    WD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * 2 * (size_t)N * T, c->st));
+    const int b = batch > 0 ? (int)(batch < total ? batch : total) : auto_batch(c, (int)total);
+    int s = estimate_rhs_range(c, P, (int)total, b, tol, prec, X, &ns);
+    if (n_solves_out) *n_solves_out = ns;
+    if (s != WD_OK) return s;
+    return finish_estimate(c, X, N, estimate, sample_var, samples_out);
+}
