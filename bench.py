@@ -126,8 +126,12 @@ def oracle_baseline(n_timeslices=3):
     time-diluted solves of sample 0 for the first n timeslices (plain
     BiCGStab on D, contraction).  Returns (GB/s of algorithmic stencil bytes,
     seconds, applies)."""
+    import contextlib
     import numpy as np
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:          # numpy's einsum/roll used here are single-threaded anyway
+        threadpool_limits = lambda limits: contextlib.nullcontext()
     import synth
     from oracle import estimators, noise, solver, wilson
     U = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)

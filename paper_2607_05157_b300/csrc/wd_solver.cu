@@ -98,6 +98,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     WD_TRY(hop(c, P64, P64, 0, bhat, b_o, b_e, 1.0, k, nrhs));
 
     std::vector<int> iters(nrhs, 0);
+    std::vector<double> last_rn2(nrhs, 0.0);
     int status = WD_OK;
     const bool verbose = getenv("WD_VERBOSE") != nullptr;
     if (prec == P64) {
@@ -149,6 +150,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
                 fprintf(stderr, "[wd] outer %d: max rel residual %.3e, open %d, inner iterations so far %d\n", outer,
                         worst, open, used);
             }
+            last_rn2 = rn2;
             if (open == 0 || used >= max_iter) break;
             WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
             // b_lo = r / |r|   (zero for converged RHS, which then stay inactive)
@@ -189,8 +191,11 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     }
     // x_o = b_o + k H_oe x_e                                             (a7)
     WD_TRY(hop(c, P64, P64, 1, x_o, x_e, b_o, 1.0, k, nrhs));
-    // true FP64 residual of the full system
-    {
+    // True FP64 residual of the full system, when asked for.  Without it the
+    // last FP64 Schur residual of the outer loop (mixed modes) or the FP64
+    // recursion (FP64 mode) certifies convergence: the full residual of
+    // (x_e, x_o) equals the Schur residual on the even sites.
+    if (resid_out) {
         double *re, *ro, *n2;
         WD_TRY(ws_get(c, "sol.re", f64, (void **)&re));
         WD_TRY(ws_get(c, "sol.ro", f64, (void **)&ro));
@@ -204,8 +209,20 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
         WD_CUDA(cudaStreamSynchronize(c->st));
         for (int r = 0; r < nrhs; ++r) {
             const double res = bnorm2[r] > 0 ? sqrt((h[r] + h[nrhs + r]) / bnorm2[r]) : 0.0;
-            if (resid_out) resid_out[r] = res;
+            resid_out[r] = res;
             if (!(res <= tol * 1.0000001) && status == WD_OK) status = isfinite(res) ? WD_ENOCONV : WD_EBREAKDOWN;
+        }
+    } else if (status == WD_OK) {
+        if (prec == P64) {
+            std::vector<BiState> hs;
+            BiVecs V;
+            WD_TRY(alloc_bivecs(c, P64, P64, nrhs, V, "bi64"));
+            WD_TRY(read_states(c, V.st, nrhs, hs));
+            for (int r = 0; r < nrhs; ++r)
+                if (hs[r].rr > hs[r].thr) status = WD_ENOCONV;
+        } else {
+            for (int r = 0; r < nrhs; ++r)
+                if (bnorm2[r] > 0 && !(last_rn2[r] <= tol * tol * bnorm2[r])) status = WD_ENOCONV;
         }
     }
     if (iters_out)
