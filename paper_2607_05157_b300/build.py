@@ -1,6 +1,6 @@
 """Build libwd.so (the CUDA path behind include/wd.h) in-tree for sm_103a.
 
-Usage: python -m paper_2607_05157_b300.build [--force]
+Usage: python paper_2607_05157_b300/build.py [--force] [--ptxas]
 Each source in csrc/ is compiled with nvcc (-gencode arch=compute_103a,code=sm_103a)
 into _build/, in parallel, then linked into paper_2607_05157_b300/libwd.so.
 """
