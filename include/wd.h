@@ -175,6 +175,24 @@ int wd_link_force(wd_ctx *ctx, const double *w, const double *z, int nrhs, doubl
 /* Replace the links / kappa of an existing context (same dims and bc). */
 int wd_update_gauge(wd_ctx *ctx, const double *gauge, double kappa);
 
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point.
+ * Same result as wd_apply (same arguments, same layouts and precisions), but
+ * the call allocates no memory: for callers that cannot allocate device memory
+ * while running -- services that reserve their whole device-memory budget at
+ * start-up, and frameworks whose caching allocator must own every byte of
+ * device memory.  The even-odd staging fields live in one static device array
+ * of 64 MiB that every GPU loading libwd holds until the process exits; a call
+ * needing more staging (2 input + 2 output half-fields for nrhs fields; e.g.
+ * FP64: 384 bytes per site and right-hand side) is rejected with WD_EINVAL.
+ * The array's device address is looked up on the first call made with a given
+ * device current, so make that first call before any latency-critical use.
+ * All calls share the array and leave its contents behind: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it.  The
+ * context itself must already exist (wd_create allocates). */
+int wd_apply_noalloc(wd_ctx *ctx, const void *in, void *out, int nrhs, int prec, int dagger);
+
 /* ---- instrumentation ------------------------------------------------- */
 
 /* Kernel timing with CUDA events on the context stream.  kernel ids:
