@@ -117,9 +117,10 @@ int probe_color(const int *dims, int nD, int d, int *n_colors, int *sigma, int32
  * (0 = automatic).  prec, tol: as wd_solve.
  * Outputs (host): estimate[2*(T+1)] complex mean per timeslice then the total;
  * sample_var[T+1] sample variance sum |X_i - mean|^2 / (N-1) of the per-sample
- * values (for WD_MLMC2: V_1/N_1 + V_2/N_2 scaled by N_1, i.e. N_1 times the
- * variance of the estimate); n_solves_out: number of D (or D_c) solves;
- * samples_out (nullable): [N][T][2] per-sample values (level 1 for WD_MLMC2). */
+ * values (for WD_MLMC2: the variance of the two-level estimate itself,
+ * s_1^2/N + s_2^2/n2, per timeslice and total); n_solves_out: number of fine
+ * plus coarse solves; samples_out (nullable): [N][T][2] per-sample values
+ * (the level-1 values for WD_MLMC2). */
 int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, uint64_t seed,
                    int op, int prec, int batch, double tol, double *estimate, double *sample_var,
                    int64_t *n_solves_out, double *samples_out);

@@ -11,26 +11,36 @@
 
 namespace wd {
 
-// Site-level access: unit u = (rhs, site) of a parity field, u = rhs*Vh + s.
-// All elementwise kernels go through the layout-aware SIO loaders, because
-// the chunk packing (and so the flat element order) differs per precision.
-template <typename S, typename RT>
+// Site-level access: unit u = (rhs, site) of a field, u = rhs*Vh + s.
+// All elementwise kernels go through these layout-aware loaders, because the
+// chunk packing (and so the flat element order) of the eo layout differs per
+// precision.  FLAT selects the plain layout [rhs][unit][12 complex] used for
+// coarse-grid vectors, whose element order is the same in every precision.
+template <typename S, typename RT, bool FLAT = false>
 __device__ __forceinline__ void ldsite(const void *b, long Vh, long u, cx<RT> v[12]) {
     typedef typename SIO<S>::real T;
-    const long rhs = u / Vh, s = u - rhs * Vh;
     cx<T> t[12];
-    SIO<S>::load((const uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
+    if (FLAT) {
+        SIO<S>::load((const uint4 *)b + u * SIO<S>::NCH, 1, 0, t);
+    } else {
+        const long rhs = u / Vh, s = u - rhs * Vh;
+        SIO<S>::load((const uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
+    }
 #pragma unroll
     for (int j = 0; j < 12; ++j) v[j] = cmake((RT)t[j].re, (RT)t[j].im);
 }
-template <typename S, typename RT>
+template <typename S, typename RT, bool FLAT = false>
 __device__ __forceinline__ void stsite(void *b, long Vh, long u, const cx<RT> v[12]) {
     typedef typename SIO<S>::real T;
-    const long rhs = u / Vh, s = u - rhs * Vh;
     cx<T> t[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) t[j] = cmake((T)v[j].re, (T)v[j].im);
-    SIO<S>::store((uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
+    if (FLAT) {
+        SIO<S>::store((uint4 *)b + u * SIO<S>::NCH, 1, 0, t);
+    } else {
+        const long rhs = u / Vh, s = u - rhs * Vh;
+        SIO<S>::store((uint4 *)b + rhs * SIO<S>::NCH * Vh, Vh, s, t);
+    }
 }
 template <typename S> struct RT_of { typedef typename SIO<S>::real type; };
 
@@ -38,10 +48,10 @@ size_t field_bytes(const Geom &g, int prec, int nrhs) {
     return (size_t)nrhs * g.Vh * spinor_bytes(prec);
 }
 
-int reduction_bpr(const Geom &g, int nrhs) {
-    // aim for ~4 CTAs of 256 threads per SM over all RHS, >= 2 sites per thread
+int reduction_bpr(long units, int nrhs) {
+    // aim for ~4 CTAs of 256 threads per SM over all RHS, >= 2 units per thread
     int want = (4 * 148 + nrhs - 1) / (nrhs > 0 ? nrhs : 1);
-    int maxb = (int)((g.Vh + 511) / 512);
+    int maxb = (int)((units + 511) / 512);
     if (want > maxb) want = maxb;
     if (want < 1) want = 1;
     if (want > 256) want = 256;
@@ -167,31 +177,31 @@ int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *use
 }
 
 // ---- conversions and mixed axpy ---------------------------------------------
-template <typename SA, typename SB>
+template <typename SA, typename SB, bool FL>
 __global__ void k_convert(const void *a, void *b, const double *scale, long Vh, long n) {
     typedef typename RT_of<SA>::type RA;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         cx<RA> v[12];
-        ldsite<SA, RA>(a, Vh, u, v);
+        ldsite<SA, RA, FL>(a, Vh, u, v);
         if (scale) {
             const RA s = (RA)scale[u / Vh];
 #pragma unroll
             for (int j = 0; j < 12; ++j) v[j] = s * v[j];
         }
-        stsite<SB, RA>(b, Vh, u, v);
+        stsite<SB, RA, FL>(b, Vh, u, v);
     }
 }
 
-template <typename SE>
+template <typename SE, bool FL>
 __global__ void k_axpy_mixed(double *x, const void *e, const double *scale, long Vh, long n) {
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const double s = scale[u / Vh];
         cx<double> xv[12], ev[12];
-        ldsite<double, double>(x, Vh, u, xv);
-        ldsite<SE, double>(e, Vh, u, ev);
+        ldsite<double, double, FL>(x, Vh, u, xv);
+        ldsite<SE, double, FL>(e, Vh, u, ev);
 #pragma unroll
         for (int j = 0; j < 12; ++j) { xv[j].re += s * ev[j].re; xv[j].im += s * ev[j].im; }
-        stsite<double, double>(x, Vh, u, xv);
+        stsite<double, double, FL>(x, Vh, u, xv);
     }
 }
 
@@ -201,19 +211,28 @@ static unsigned ew_blocks(long n) {
     return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-int blas_copy_convert(wd_ctx *c, int ps, const void *src, int pd, void *dst, int nrhs, const double *scale) {
-    const long Vh = c->g.Vh, n = Vh * nrhs;
+#define WD_DISPATCH_FLAT(flat, FL, ...)                 \
+    do {                                                \
+        if (flat) { constexpr bool FL = true; __VA_ARGS__; } \
+        else { constexpr bool FL = false; __VA_ARGS__; }     \
+    } while (0)
+
+int blas_copy_convert(wd_ctx *c, const Space &sp, int ps, const void *src, int pd, void *dst, int nrhs,
+                      const double *scale) {
+    const long Vh = sp.units, n = Vh * nrhs;
     if (n == 0) return WD_OK;
-    WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB, k_convert<SA, SB><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, Vh, n)));
+    WD_DISPATCH_FLAT(sp.flat, FL, WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB,
+        k_convert<SA, SB, FL><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, Vh, n))));
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-int blas_axpy_mixed(wd_ctx *c, double *x, int pe, const void *e, const double *scale, int nrhs) {
-    const long Vh = c->g.Vh, n = Vh * nrhs;
+int blas_axpy_mixed(wd_ctx *c, const Space &sp, double *x, int pe, const void *e, const double *scale, int nrhs) {
+    const long Vh = sp.units, n = Vh * nrhs;
     if (n == 0) return WD_OK;
-    WD_DISPATCH_PREC(pe, SE, k_axpy_mixed<SE><<<ew_blocks(n), 256, 0, c->st>>>(x, e, scale, Vh, n));
+    WD_DISPATCH_FLAT(sp.flat, FL, WD_DISPATCH_PREC(pe, SE,
+        k_axpy_mixed<SE, FL><<<ew_blocks(n), 256, 0, c->st>>>(x, e, scale, Vh, n)));
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
@@ -225,14 +244,14 @@ int blas_zero(wd_ctx *c, void *p, size_t bytes) {
 }
 
 // ---- norms -------------------------------------------------------------------
-template <typename S>
+template <typename S, bool FL>
 __global__ void k_norm2_part(const void *a, double *part, long Vh, int nrhs, int bpr) {
     typedef typename RT_of<S>::type RT;
     Range R = my_range(Vh);
     RT acc = 0;
     for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
         cx<RT> v[12];
-        ldsite<S, RT>(a, Vh, u, v);
+        ldsite<S, RT, FL>(a, Vh, u, v);
 #pragma unroll
         for (int j = 0; j < 12; ++j) acc += v[j].re * v[j].re + v[j].im * v[j].im;
     }
@@ -245,14 +264,15 @@ __global__ void k_sum_partials(const double *part, double *out, int nrhs, int bp
         out[r] = sum_part(part, 0, r, nrhs, bpr);
 }
 
-int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out) {
+int blas_norm2(wd_ctx *c, const Space &sp, int prec, const void *a, int nrhs, double *out) {
     if (nrhs <= 0) return WD_OK;
-    const int bpr = reduction_bpr(c->g, nrhs);
+    const int bpr = reduction_bpr(sp.units, nrhs);
     double *part;
     WD_TRY(ws_get(c, "norm_part", sizeof(double) * bpr * nrhs, (void **)&part));
-    const long Vh = c->g.Vh;
+    const long Vh = sp.units;
     dim3 grid(bpr, nrhs);
-    WD_DISPATCH_PREC(prec, S, k_norm2_part<S><<<grid, 256, 0, c->st>>>(a, part, Vh, nrhs, bpr));
+    WD_DISPATCH_FLAT(sp.flat, FL, WD_DISPATCH_PREC(prec, S,
+        k_norm2_part<S, FL><<<grid, 256, 0, c->st>>>(a, part, Vh, nrhs, bpr)));
     k_sum_partials<<<(nrhs + 127) / 128, 128, 0, c->st>>>(part, out, nrhs, bpr);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
@@ -261,7 +281,7 @@ int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out) {
 
 // ---- BiCGStab ------------------------------------------------------------------
 // init: x = 0, r = rh = b, p = b (operator precision); partial |b|^2
-template <typename SW, typename SP>
+template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, double *part, long Vh, int nrhs,
                             int bpr) {
     typedef typename RT_of<SW>::type RT;
@@ -269,13 +289,13 @@ __global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, 
     RT acc = 0;
     for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
         cx<RT> v[12], z[12];
-        ldsite<SW, RT>(b, Vh, u, v);
+        ldsite<SW, RT, FL>(b, Vh, u, v);
 #pragma unroll
         for (int j = 0; j < 12; ++j) { z[j] = cmake(RT(0), RT(0)); acc += v[j].re * v[j].re + v[j].im * v[j].im; }
-        stsite<SW, RT>(x, Vh, u, z);
-        stsite<SW, RT>(r, Vh, u, v);
-        stsite<SW, RT>(rh, Vh, u, v);
-        stsite<SP, RT>(p, Vh, u, v);
+        stsite<SW, RT, FL>(x, Vh, u, z);
+        stsite<SW, RT, FL>(r, Vh, u, v);
+        stsite<SW, RT, FL>(rh, Vh, u, v);
+        stsite<SP, RT, FL>(p, Vh, u, v);
     }
     double d[1] = {(double)acc};
     block_partials<1>(d, part, nrhs, bpr);
@@ -309,7 +329,7 @@ __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm
 }
 
 // partial sums of conj(a).b (slots 0, 1) and optionally |a|^2 (slot 2)
-template <typename SA, typename SB, bool NORMA>
+template <typename SA, typename SB, bool NORMA, bool FL>
 __global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, int nrhs, int bpr) {
     typedef typename RT_of<SA>::type RT;
     Range R = my_range(Vh);
@@ -317,8 +337,8 @@ __global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, 
     RT nn = 0;
     for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
         cx<RT> va[12], vb[12];
-        ldsite<SA, RT>(a, Vh, u, va);
-        ldsite<SB, RT>(b, Vh, u, vb);
+        ldsite<SA, RT, FL>(a, Vh, u, va);
+        ldsite<SB, RT, FL>(b, Vh, u, vb);
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
             cfma_conj(acc, va[j], vb[j]);
@@ -398,23 +418,23 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
 }
 
 // s = r - alpha v
-template <typename SW, typename SP>
+template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long Vh, long n) {
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const double2 a = st[u / Vh].alpha;
         const cx<RT> mal = cmake((RT)-a.x, (RT)-a.y);
         cx<RT> rv[12], vv[12];
-        ldsite<SW, RT>(r, Vh, u, rv);
-        ldsite<SW, RT>(v, Vh, u, vv);
+        ldsite<SW, RT, FL>(r, Vh, u, rv);
+        ldsite<SW, RT, FL>(v, Vh, u, vv);
 #pragma unroll
         for (int j = 0; j < 12; ++j) cfma(rv[j], mal, vv[j]);
-        stsite<SP, RT>(s, Vh, u, rv);
+        stsite<SP, RT, FL>(s, Vh, u, rv);
     }
 }
 
 // x += alpha p + omega s; r = s - omega t; partials (rh, r) and |r|^2
-template <typename SW, typename SP>
+template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const void *t, const void *rh,
                           const BiState *st, double *part, long Vh, int nrhs, int bpr) {
     typedef typename RT_of<SW>::type RT;
@@ -425,14 +445,14 @@ __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const 
     RT nn = 0;
     for (long u = R.g0 + threadIdx.x; u < R.g1; u += blockDim.x) {
         cx<RT> xv[12], pv[12], sv[12], tv[12];
-        ldsite<SW, RT>(x, Vh, u, xv);
-        ldsite<SP, RT>(p, Vh, u, pv);
-        ldsite<SP, RT>(s, Vh, u, sv);
+        ldsite<SW, RT, FL>(x, Vh, u, xv);
+        ldsite<SP, RT, FL>(p, Vh, u, pv);
+        ldsite<SP, RT, FL>(s, Vh, u, sv);
 #pragma unroll
         for (int j = 0; j < 12; ++j) { cfma(xv[j], al, pv[j]); cfma(xv[j], om, sv[j]); }
-        stsite<SW, RT>(x, Vh, u, xv);
-        ldsite<SW, RT>(t, Vh, u, tv);
-        ldsite<SW, RT>(rh, Vh, u, pv);
+        stsite<SW, RT, FL>(x, Vh, u, xv);
+        ldsite<SW, RT, FL>(t, Vh, u, tv);
+        ldsite<SW, RT, FL>(rh, Vh, u, pv);
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
             cx<RT> rn = sv[j];
@@ -441,29 +461,29 @@ __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const 
             nn += rn.re * rn.re + rn.im * rn.im;
             tv[j] = rn;
         }
-        stsite<SW, RT>(r, Vh, u, tv);
+        stsite<SW, RT, FL>(r, Vh, u, tv);
     }
     double d[3] = {(double)dot.re, (double)dot.im, (double)nn};
     block_partials<3>(d, part, nrhs, bpr);
 }
 
 // p = r + beta (p - omega v)
-template <typename SW, typename SP>
+template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *st, long Vh, long n) {
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const BiState &S = st[u / Vh];
         const cx<RT> be = cmake((RT)S.beta.x, (RT)S.beta.y), mom = cmake((RT)-S.omega.x, (RT)-S.omega.y);
         cx<RT> rv[12], pv[12], vv[12];
-        ldsite<SW, RT>(r, Vh, u, rv);
-        ldsite<SP, RT>(p, Vh, u, pv);
-        ldsite<SW, RT>(v, Vh, u, vv);
+        ldsite<SW, RT, FL>(r, Vh, u, rv);
+        ldsite<SP, RT, FL>(p, Vh, u, pv);
+        ldsite<SW, RT, FL>(v, Vh, u, vv);
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
             cfma(pv[j], mom, vv[j]);
             cfma(rv[j], be, pv[j]);
         }
-        stsite<SP, RT>(p, Vh, u, rv);
+        stsite<SP, RT, FL>(p, Vh, u, rv);
     }
 }
 
@@ -476,10 +496,10 @@ __global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *s
 
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev) {
-    const long Vh = c->g.Vh;
+    const long Vh = V.sp.units;
     dim3 grid(V.bpr, nrhs);
-    WD_DISPATCH_PAIR(pw, pp, SW, SP,
-        k_bicg_init<SW, SP><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, Vh, nrhs, V.bpr));
+    WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP,
+        k_bicg_init<SW, SP, FL><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, Vh, nrhs, V.bpr)));
     k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
@@ -487,30 +507,27 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
 }
 
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
-    const long Vh = c->g.Vh, n = Vh * nrhs;
-    const double k2 = c->kappa * c->kappa;
+    const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
-    // v = A p = p - kappa^2 H_eo H_oe p
-    WD_TRY(hop(c, pp, pp, 1, V.tmp, V.p, nullptr, 0.0, 1.0, nrhs));
-    WD_TRY(hop(c, pp, pw, 0, V.v, V.tmp, V.p, 1.0, -k2, nrhs));
-    WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SW, false><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr);
+    // v = A p
+    WD_TRY(V.op(c, V.p, V.v, nrhs, V.op_user));
+    WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
+        k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr);
         k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
-        k_bicg_s<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
-    });
+        k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
+    }));
     c->launches += 3;
     // t = A s
-    WD_TRY(hop(c, pp, pp, 1, V.tmp, V.s, nullptr, 0.0, 1.0, nrhs));
-    WD_TRY(hop(c, pp, pw, 0, V.t, V.tmp, V.s, 1.0, -k2, nrhs));
-    WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SP, true><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr);
+    WD_TRY(V.op(c, V.s, V.t, nrhs, V.op_user));
+    WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
+        k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr);
         k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
-        k_bicg_xr<SW, SP><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
+        k_bicg_xr<SW, SP, FL><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
         k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
-        k_bicg_p<SW, SP><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
-    });
+        k_bicg_p<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
+    }));
     c->launches += 5;
     WD_CUDA(cudaGetLastError());
     return WD_OK;

@@ -255,6 +255,37 @@ int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double 
 int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
                    double *estimate, double *sample_var, int64_t *nsolves, double *samples_out);
 
+// Rademacher noise of samples [sample0, sample0 + nrhs) (no masks) into FP64 eo fields
+int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, double *bo) {
+    EstParams P;
+    memset(&P, 0, sizeof(P));
+    P.seed = seed; P.m = 1; P.nc = 1; P.dil = 1; P.TT = 1; P.g0 = sample0; P.nrhs = nrhs;
+    const long n = (long)c->g.V * nrhs;
+    k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, c->g, be, bo);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// X[sample0 + r][t] += sum_{x in t} conj(eta_r(x)) (B y_r)(x) for unmasked
+// Rademacher noise of samples sample0 + r (r < nrhs); X is [N][T][2]
+int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma5, const double *ye,
+                      const double *yo, double *X) {
+    EstParams P;
+    memset(&P, 0, sizeof(P));
+    P.seed = seed; P.m = 1; P.nc = 1; P.dil = 1; P.TT = 1; P.g0 = sample0; P.nrhs = nrhs; P.gamma5 = gamma5;
+    const Geom &g = c->g;
+    int bps = (2 * (g.Vh / g.T) + 1023) / 1024;
+    if (bps < 1) bps = 1;
+    double *part;
+    WD_TRY(ws_get(c, "est.part", sizeof(double) * 2 * (size_t)nrhs * g.T * bps, (void **)&part));
+    k_contract<<<dim3(bps, nrhs, g.T), 256, 0, c->st>>>(P, g, ye, yo, part, bps);
+    k_accumulate<<<(nrhs * g.T + 127) / 128, 128, 0, c->st>>>(P, g.T, part, bps, X, sample0, nrhs);
+    c->launches += 2;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 }  // namespace wd
 
 using namespace wd;

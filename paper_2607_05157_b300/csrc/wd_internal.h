@@ -64,7 +64,17 @@ struct wd_prof_rec {
     double bytes;
 };
 
-struct wd_mg;   // multigrid state (wd_mg.cu)
+// multigrid state (wd_mg.cu)
+struct wd_mg {
+    int nv, ncd;
+    int agg[4], cd[4];
+    int Vc;
+    double2 *P;        // [2][Vh][12][nv]
+    double2 *Dc;       // [Vc][9][ncd][ncd]
+    int *nbr;          // [Vc][9]
+    void *Wtc;         // tensor-core operand (bf16), built by wd_coarse_tc.cu
+    float2 *Dc32;      // [Vc][9][ncd][ncd] complex64 copy for the FP32 CUDA-core path
+};
 
 struct wd_ctx {
     int dims[4];
@@ -108,25 +118,55 @@ int solve_eo(wd_ctx *c, const double *b_even, const double *b_odd, double *x_eve
              double tol, int prec, int max_iter, int *iters_out, double *resid_out);
 
 // blas (wd_blas.cu)
-size_t field_bytes(const Geom &g, int prec, int nrhs);   // one parity
-int blas_copy_convert(wd_ctx *c, int prec_src, const void *src, int prec_dst, void *dst, int nrhs,
+// A vector space for BLAS-1: `units` 12-complex units per right-hand side, in
+// the eo chunk layout (flat = false, units = Vh) or the plain layout
+// [rhs][unit][12] (flat = true, coarse-grid vectors).
+struct Space {
+    long units;
+    bool flat;
+};
+inline Space fine_space(const Geom &g) { Space s; s.units = g.Vh; s.flat = false; return s; }
+inline size_t space_bytes(const Space &s, int prec, int nrhs) { return (size_t)nrhs * s.units * spinor_bytes(prec); }
+size_t field_bytes(const Geom &g, int prec, int nrhs);   // one parity of a fine field
+int blas_copy_convert(wd_ctx *c, const Space &sp, int prec_src, const void *src, int prec_dst, void *dst, int nrhs,
                       const double *scale_dev);
-int blas_axpy_mixed(wd_ctx *c, double *x64, int prec_e, const void *e, const double *scale_dev, int nrhs);
-int blas_norm2(wd_ctx *c, int prec, const void *a, int nrhs, double *out_dev);
+int blas_axpy_mixed(wd_ctx *c, const Space &sp, double *x64, int prec_e, const void *e, const double *scale_dev,
+                    int nrhs);
+int blas_norm2(wd_ctx *c, const Space &sp, int prec, const void *a, int nrhs, double *out_dev);
 int blas_zero(wd_ctx *c, void *p, size_t bytes);
+
+// out = A in for one operator, in the precisions the solver set up
+typedef int (*OpFn)(wd_ctx *c, const void *in, void *out, int nrhs, void *user);
+// r = b - A x in FP64
+typedef int (*ResFn)(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *user);
 
 // BiCGStab building blocks (wd_blas.cu)
 struct BiVecs {
     void *x, *r, *rh, *v, *t;   // working precision (SW)
     void *p, *s;                // operator-input precision (SP)
-    void *tmp;                  // odd-parity intermediate (SP)
     BiState *st;
     double *part;               // reduction partials
     int *count;                 // active count (device)
     int bpr;                    // reduction blocks per RHS
+    Space sp;
+    OpFn op;
+    void *op_user;
 };
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev);
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
-int reduction_bpr(const Geom &g, int nrhs);
+int reduction_bpr(long units, int nrhs);
+
+// Defect-correction (or plain FP64) BiCGStab solve of A x = b on one space
+// (wd_solver.cu).  b, x: FP64 vectors of the space (x overwritten).
+struct Problem {
+    Space sp;
+    OpFn op64;  void *u64;      // FP64 operator (FP64 mode)
+    OpFn oplo;  void *ulo;      // inner operator, inputs in pp, outputs in pw
+    ResFn res64; void *ures;    // FP64 residual
+    const char *tag;            // workspace name prefix
+};
+int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
+             const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,
+             std::vector<double> &last_rn2);
 }  // namespace wd

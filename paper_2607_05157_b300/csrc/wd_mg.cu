@@ -1,0 +1,600 @@
+// Two-level aggregation multigrid for the MLMC estimator (Sec. 2, row a8).
+//
+// Transfer operators (Sec. 2: R = P^dag, P^dag P = I): the fine lattice is cut
+// into aggregates of agg[mu] sites per direction; every test vector is
+// restricted to each aggregate and each chirality half (g5 = +1: spins 0, 1;
+// g5 = -1: spins 2, 3) and the restricted vectors of one (aggregate, half)
+// are orthonormalised by modified Gram-Schmidt in test-vector order.  Coarse
+// dof i = nv*h + k of coarse site X (ncd = 2 nv dofs per site).
+// P is stored per fine site: P[parity][s][12][nv] complex (eo site order),
+// entry [x][3*spin+colour][k] = component of column (X(x), half(spin), k).
+//
+// Galerkin operator (Eq. 7): D_c = P^dag D P.  Because D couples nearest
+// neighbours and P is block diagonal over aggregates, D_c is a 9-point
+// stencil of ncd x ncd blocks:
+//   y(X) = A_0(X) x(X) + sum_mu [A_{+mu}(X) x(X+mu) + A_{-mu}(X) x(X-mu)],
+// A_0 collecting the identity and every hop that stays inside X, A_{+-mu}
+// the hops that leave X through its +-mu face (with a coarse extent of 1 or
+// 2 the neighbour is X itself or the same site twice; the blocks stay
+// separate and their contributions add).  The blocks are assembled directly
+// from the links and P, hop by hop, in FP64.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "wd_internal.h"
+
+
+
+namespace wd {
+
+// g_mu in the chiral basis: g_k = [[0, -i s_k], [i s_k, 0]], g_4 = [[0, 1], [1, 0]]
+__constant__ double2 c_gamma[4][4][4];
+
+static void host_gamma(double2 g[4][4][4]) {
+    memset(g, 0, sizeof(double2) * 64);
+    // sigma matrices (re, im)
+    const double s[3][2][2][2] = {{{{0, 0}, {1, 0}}, {{1, 0}, {0, 0}}},
+                                  {{{0, 0}, {0, -1}}, {{0, 1}, {0, 0}}},
+                                  {{{1, 0}, {0, 0}}, {{0, 0}, {-1, 0}}}};
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const double re = s[k][a][b][0], im = s[k][a][b][1];
+                // upper right: -i s = (im, -re);  lower left: i s = (-im, re)
+                g[k][a][2 + b] = make_double2(im, -re);
+                g[k][2 + a][b] = make_double2(-im, re);
+            }
+    for (int a = 0; a < 2; ++a) { g[3][a][2 + a] = make_double2(1, 0); g[3][2 + a][a] = make_double2(1, 0); }
+}
+
+__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ double2 zfma_conj(double2 acc, double2 a, double2 b) {   // acc += conj(a) b
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+struct MgGeom {
+    Geom g;
+    int agg[4], cd[4];
+    int nv, ncd, Vc;
+};
+
+// fine site (lexicographic) of the j-th site of aggregate X, j in [0, prod agg)
+__device__ __forceinline__ void agg_site(const MgGeom &M, int X, int j, int c[4]) {
+    int xc[4];
+    int r = X;
+    for (int m = 0; m < 4; ++m) { xc[m] = r % M.cd[m]; r /= M.cd[m]; }
+    int q = j;
+    for (int m = 0; m < 4; ++m) { c[m] = xc[m] * M.agg[m] + q % M.agg[m]; q /= M.agg[m]; }
+}
+__device__ __forceinline__ int lex(const Geom &g, const int c[4]) { return c[0] + g.X * (c[1] + g.Y * (c[2] + g.Z * c[3])); }
+__device__ __forceinline__ int coarse_of(const MgGeom &M, const int c[4]) {
+    return c[0] / M.agg[0] + M.cd[0] * (c[1] / M.agg[1] + M.cd[1] * (c[2] / M.agg[2] + M.cd[2] * (c[3] / M.agg[3])));
+}
+// P entry for (fine lexicographic site, component, k)
+__device__ __forceinline__ size_t pidx(const MgGeom &M, int site, int comp, int k) {
+    const int c0 = site % M.g.X, r = site / M.g.X;
+    const int c1 = r % M.g.Y, c2 = (r / M.g.Y) % M.g.Z, c3 = r / (M.g.Y * M.g.Z);
+    const int par = (c0 + c1 + c2 + c3) & 1;
+    return (((size_t)par * M.g.Vh + (site >> 1)) * 12 + comp) * M.nv + k;
+}
+
+// test vectors (user layout [nv][V][12]) -> P layout
+__global__ void k_tv_to_P(const double2 *tv, double2 *P, MgGeom M) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)M.g.V * 12 * M.nv) return;
+    const int k = (int)(i % M.nv);
+    const long rest = i / M.nv;
+    const int comp = (int)(rest % 12), site = (int)(rest / 12);
+    P[pidx(M, site, comp, k)] = tv[((size_t)k * M.g.V + site) * 12 + comp];
+}
+
+__device__ double2 block_reduce_z(double2 v, double2 *sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double2 a = make_double2(0, 0);
+    for (int w = 0; w < nw; ++w) { a.x += sh[w].x; a.y += sh[w].y; }
+    return a;
+}
+
+// modified Gram-Schmidt of the nv columns of one (aggregate, half) block; one CTA per block
+__global__ void k_block_mgs(double2 *P, MgGeom M) {
+    __shared__ double2 sh[32];
+    const int X = blockIdx.x >> 1, h = blockIdx.x & 1;
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    const int m = nsite * 6;
+    for (int k = 0; k < M.nv; ++k) {
+        for (int j = 0; j < k; ++j) {
+            double2 d = make_double2(0, 0);
+            for (int row = threadIdx.x; row < m; row += blockDim.x) {
+                int c[4];
+                agg_site(M, X, row / 6, c);
+                const int comp = 6 * h + row % 6, site = lex(M.g, c);
+                d = zfma_conj(d, P[pidx(M, site, comp, j)], P[pidx(M, site, comp, k)]);
+            }
+            d = block_reduce_z(d, sh);
+            for (int row = threadIdx.x; row < m; row += blockDim.x) {
+                int c[4];
+                agg_site(M, X, row / 6, c);
+                const int comp = 6 * h + row % 6, site = lex(M.g, c);
+                double2 &q = P[pidx(M, site, comp, k)];
+                const double2 qj = P[pidx(M, site, comp, j)];
+                q.x -= d.x * qj.x - d.y * qj.y;
+                q.y -= d.x * qj.y + d.y * qj.x;
+            }
+            __syncthreads();
+        }
+        double2 nn = make_double2(0, 0);
+        for (int row = threadIdx.x; row < m; row += blockDim.x) {
+            int c[4];
+            agg_site(M, X, row / 6, c);
+            const int comp = 6 * h + row % 6, site = lex(M.g, c);
+            const double2 q = P[pidx(M, site, comp, k)];
+            nn.x += q.x * q.x + q.y * q.y;
+        }
+        nn = block_reduce_z(nn, sh);
+        const double inv = 1.0 / sqrt(nn.x);
+        for (int row = threadIdx.x; row < m; row += blockDim.x) {
+            int c[4];
+            agg_site(M, X, row / 6, c);
+            const int comp = 6 * h + row % 6, site = lex(M.g, c);
+            double2 &q = P[pidx(M, site, comp, k)];
+            q.x *= inv;
+            q.y *= inv;
+        }
+        __syncthreads();
+    }
+}
+
+// coarse neighbour table: b = 0 self, 1+mu forward, 5+mu backward
+__global__ void k_coarse_nbr(int *nbr, MgGeom M) {
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= M.Vc) return;
+    int xc[4], r = X;
+    for (int m = 0; m < 4; ++m) { xc[m] = r % M.cd[m]; r /= M.cd[m]; }
+    nbr[X * 9] = X;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int dir = 0; dir < 2; ++dir) {
+            int y[4] = {xc[0], xc[1], xc[2], xc[3]};
+            y[mu] = dir == 0 ? (y[mu] + 1) % M.cd[mu] : (y[mu] + M.cd[mu] - 1) % M.cd[mu];
+            nbr[X * 9 + 1 + mu + 4 * dir] = y[0] + M.cd[0] * (y[1] + M.cd[1] * (y[2] + M.cd[2] * y[3]));
+        }
+}
+
+// Block b of D_c at coarse site X; one CTA per (X, b).  For each hop x -> y
+// of the block: A += coef * P(x)^dag [Gamma (x) U] P(y), with P(.) the 12 x ncd
+// restriction of the columns to one site.  Shared memory: A (ncd^2), P(x) and
+// W = [Gamma (x) U] P(y) (12 x ncd each).
+__global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double kappa, double2 *Dc, MgGeom M) {
+    extern __shared__ double2 smem[];
+    const int ncd = M.ncd, nv = M.nv;
+    double2 *A = smem, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd;
+    const int X = blockIdx.x / 9, b = blockIdx.x % 9;
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
+    const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
+    for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) A[e] = make_double2(0, 0);
+    __syncthreads();
+    // hop list: for b = 0 the identity (mu = -1) and internal hops; else the face hops of one direction
+    for (int j = 0; j < nsite; ++j) {
+        int c[4];
+        agg_site(M, X, j, c);
+        const int xs = lex(M.g, c);
+        for (int hop = -1; hop < 8; ++hop) {
+            // hop -1: identity; 0..3 forward mu; 4..7 backward mu
+            int mu = hop & 3, fwd = hop < 4;
+            int y[4] = {c[0], c[1], c[2], c[3]};
+            double sgn = 1.0;
+            int blk;
+            if (hop < 0) { blk = 0; }
+            else {
+                const int inside_f = (c[mu] % M.agg[mu]) != M.agg[mu] - 1;
+                const int inside_b = (c[mu] % M.agg[mu]) != 0;
+                if (fwd) {
+                    y[mu] = c[mu] + 1 == L[mu] ? 0 : c[mu] + 1;
+                    if (c[mu] == L[mu] - 1) sgn = bcv[mu];
+                    blk = inside_f ? 0 : 1 + mu;
+                } else {
+                    y[mu] = c[mu] == 0 ? L[mu] - 1 : c[mu] - 1;
+                    if (c[mu] == 0) sgn = bcv[mu];
+                    blk = inside_b ? 0 : 5 + mu;
+                }
+            }
+            if (blk != b) continue;
+            const int ys = lex(M.g, y);
+            // P(x) and P(y) restricted to the site (12 x ncd, zero outside each column's half)
+            for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                const int comp = e / ncd, i = e % ncd, h = i / nv, k = i % nv;
+                const bool on = (comp / 6) == h;
+                Px[e] = on ? P[pidx(M, xs, comp, k)] : make_double2(0, 0);
+                W[e] = on ? P[pidx(M, ys, comp, k)] : make_double2(0, 0);
+            }
+            __syncthreads();
+            double coef;
+            if (hop >= 0) {
+                // T1[s][a][i] = sum_b' U'[a][b'] P(y)[s][b'][i], U' = U_mu(x) (fwd) or U_mu(y)^dag (bwd)
+                const double2 *u = U + ((size_t)mu * M.g.V + (fwd ? xs : ys)) * 9;
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    const int comp = e / ncd, i = e % ncd, s = comp / 3, a = comp % 3;
+                    double2 acc = make_double2(0, 0);
+                    for (int bb = 0; bb < 3; ++bb) {
+                        double2 ul = fwd ? u[3 * a + bb] : make_double2(u[3 * bb + a].x, -u[3 * bb + a].y);
+                        acc = zfma(acc, ul, W[(3 * s + bb) * ncd + i]);
+                    }
+                    T1[e] = acc;
+                }
+                __syncthreads();
+                // W[s][a][i] = sum_s' (1 -/+ g_mu)[s][s'] T1[s'][a][i]
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    const int comp = e / ncd, i = e % ncd, s = comp / 3, a = comp % 3;
+                    double2 acc = T1[e];
+                    for (int sp = 0; sp < 4; ++sp) {
+                        double2 gv = c_gamma[mu][s][sp];
+                        if (fwd) { gv.x = -gv.x; gv.y = -gv.y; }
+                        acc = zfma(acc, gv, T1[(3 * sp + a) * ncd + i]);
+                    }
+                    W[e] = acc;
+                }
+                __syncthreads();
+                coef = -kappa * sgn;
+            } else {
+                coef = 1.0;
+            }
+            // A[i][j] += coef * sum_comp conj(Px[comp][i]) W[comp][j]
+            for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
+                const int i = e / ncd, jj = e % ncd;
+                double2 acc = make_double2(0, 0);
+                for (int comp = 0; comp < 12; ++comp) acc = zfma_conj(acc, Px[comp * ncd + i], W[comp * ncd + jj]);
+                A[e].x += coef * acc.x;
+                A[e].y += coef * acc.y;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) Dc[((size_t)X * 9 + b) * ncd * ncd + e] = A[e];
+}
+
+__global__ void k_dc_to32(const double2 *Dc, float2 *D32, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        D32[i] = make_float2((float)Dc[i].x, (float)Dc[i].y);
+}
+
+// ---- coarse stencil on CUDA cores (FP64 reference path and FP32) -----------
+// y[rhs][X][i] = a*w[rhs][X][i] + beta * sum_b sum_j A_b(X)[i][j] x[rhs][nbr_b(X)][j]
+// One CTA per (X, tile of 8 RHS), threads (i, r).
+template <typename T2, typename R>
+__global__ void k_coarse_apply(const T2 *Dc, const int *nbr, const T2 *x, T2 *y, const T2 *w, double a, double beta,
+                               int ncd, int Vc, int nrhs) {
+    const int X = blockIdx.x, r0 = blockIdx.y * 8;
+    const int i = threadIdx.x % ncd, rr = threadIdx.x / ncd;
+    const int r = r0 + rr;
+    if (rr >= 8 || r >= nrhs) return;
+    R are = 0, aim = 0;
+    for (int b = 0; b < 9; ++b) {
+        const int nb = nbr[X * 9 + b];
+        const T2 *row = Dc + ((size_t)X * 9 + b) * ncd * ncd + (size_t)i * ncd;
+        const T2 *xv = x + ((size_t)r * Vc + nb) * ncd;
+        for (int j = 0; j < ncd; ++j) {
+            const T2 m = row[j], v = xv[j];
+            are = fma((R)m.x, (R)v.x, are); are = fma(-(R)m.y, (R)v.y, are);
+            aim = fma((R)m.x, (R)v.y, aim); aim = fma((R)m.y, (R)v.x, aim);
+        }
+    }
+    const size_t o = ((size_t)r * Vc + X) * ncd + i;
+    R ore = (R)beta * are, oim = (R)beta * aim;
+    if (w) { ore += (R)a * (R)w[o].x; oim += (R)a * (R)w[o].y; }
+    T2 out;
+    out.x = ore; out.y = oim;
+    y[o] = out;
+}
+
+// ---- restriction / prolongation on eo FP64 fine fields ----------------------
+// yc[rhs][X][nv*h + k] = sum_{x in X, spin in h, colour} conj(P[x][comp][k]) v[x][comp]
+__global__ void k_restrict(const double2 *P, const double *ve, const double *vo, double2 *yc, MgGeom M, int nrhs) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)nrhs * M.Vc * M.ncd) return;
+    const int i = (int)(t % M.ncd);
+    const long rest = t / M.ncd;
+    const int X = (int)(rest % M.Vc), r = (int)(rest / M.Vc);
+    const int h = i / M.nv, k = i % M.nv;
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    double2 acc = make_double2(0, 0);
+    for (int j = 0; j < nsite; ++j) {
+        int c[4];
+        agg_site(M, X, j, c);
+        const int site = lex(M.g, c), par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
+        const double2 *f = (const double2 *)(par ? vo : ve) + (size_t)r * 12 * M.g.Vh;
+        for (int q = 0; q < 6; ++q) {
+            const int comp = 6 * h + q;
+            acc = zfma_conj(acc, P[(((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv + k], f[(size_t)comp * M.g.Vh + s]);
+        }
+    }
+    yc[t] = acc;
+}
+
+// v[x][comp] = sum_k P[x][comp][k] yc[X][nv*h(comp) + k]   (overwrites v)
+__global__ void k_prolong(const double2 *P, const double2 *yc, double *ve, double *vo, MgGeom M, int nrhs) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)nrhs * M.g.V * 12) return;
+    const int comp = (int)(t % 12);
+    const long rest = t / 12;
+    const int site = (int)(rest % M.g.V), r = (int)(rest / M.g.V);
+    int c[4];
+    c[0] = site % M.g.X;
+    int q = site / M.g.X;
+    c[1] = q % M.g.Y; q /= M.g.Y;
+    c[2] = q % M.g.Z; c[3] = q / M.g.Z;
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
+    const int X = coarse_of(M, c), h = comp / 6;
+    const double2 *pr = P + (((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv;
+    const double2 *yv = yc + ((size_t)r * M.Vc + X) * M.ncd + h * M.nv;
+    double2 acc = make_double2(0, 0);
+    for (int k = 0; k < M.nv; ++k) acc = zfma(acc, pr[k], yv[k]);
+    double2 *f = (double2 *)(par ? vo : ve) + (size_t)r * 12 * M.g.Vh;
+    f[(size_t)comp * M.g.Vh + s] = acc;
+}
+
+static MgGeom mg_geom(wd_ctx *c) {
+    MgGeom M;
+    M.g = c->g;
+    for (int m = 0; m < 4; ++m) { M.agg[m] = c->mg->agg[m]; M.cd[m] = c->mg->cd[m]; }
+    M.nv = c->mg->nv;
+    M.ncd = c->mg->ncd;
+    M.Vc = c->mg->Vc;
+    return M;
+}
+
+Space coarse_space(wd_ctx *c) {
+    Space s;
+    s.units = (long)c->mg->Vc * c->mg->ncd / 12;
+    s.flat = true;
+    return s;
+}
+
+int coarse_apply64(wd_ctx *c, const double *x, double *y, const double *w, double a, double beta, int nrhs) {
+    wd_mg *g = c->mg;
+    dim3 grid(g->Vc, (nrhs + 7) / 8);
+    int slot;
+    prof_begin(c, WD_K_COARSE, 8.0 * g->ncd * g->ncd * 9.0 * g->Vc * nrhs, &slot);
+    k_coarse_apply<double2, double><<<grid, g->ncd * 8, 0, c->st>>>(g->Dc, g->nbr, (const double2 *)x, (double2 *)y,
+                                                                   (const double2 *)w, a, beta, g->ncd, g->Vc, nrhs);
+    prof_end(c, slot);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int coarse_apply32(wd_ctx *c, const float *x, float *y, int nrhs) {
+    wd_mg *g = c->mg;
+    dim3 grid(g->Vc, (nrhs + 7) / 8);
+    int slot;
+    prof_begin(c, WD_K_COARSE, 8.0 * g->ncd * g->ncd * 9.0 * g->Vc * nrhs, &slot);
+    k_coarse_apply<float2, float><<<grid, g->ncd * 8, 0, c->st>>>(g->Dc32, g->nbr, (const float2 *)x, (float2 *)y,
+                                                                  nullptr, 0.0, 1.0, g->ncd, g->Vc, nrhs);
+    prof_end(c, slot);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs) {
+    MgGeom M = mg_geom(c);
+    const long n = (long)nrhs * M.Vc * M.ncd;
+    k_restrict<<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->P, ve, vo, (double2 *)yc, M, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs) {
+    MgGeom M = mg_geom(c);
+    const long n = (long)nrhs * M.g.V * 12;
+    k_prolong<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(c->mg->P, (const double2 *)yc, ve, vo, M, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// ---- coarse solves ------------------------------------------------------------
+int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs);   // wd_coarse_tc.cu
+int coarse_tc_build(wd_ctx *c);
+bool coarse_tc_ok(wd_ctx *c);
+
+static int cop64(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
+    return coarse_apply64(c, (const double *)in, (double *)out, nullptr, 0.0, 1.0, nrhs);
+}
+static int cop32(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
+    return coarse_apply32(c, (const float *)in, (float *)out, nrhs);
+}
+static int coptc(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
+    return coarse_tc_apply(c, in, (float *)out, nrhs);
+}
+static int cres64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *) {
+    return coarse_apply64(c, x, r, b, 1.0, -1.0, nrhs);
+}
+
+// x = D_c^{-1} b on coarse FP64 vectors [nrhs][Vc][ncd]
+int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
+                 double *resid_out) {
+    const Space sp = coarse_space(c);
+    double *bn2;
+    WD_TRY(ws_get(c, "cs.bn2", sizeof(double) * nrhs, (void **)&bn2));
+    WD_TRY(blas_norm2(c, sp, P64, b, nrhs, bn2));
+    std::vector<double> bnorm2(nrhs);
+    WD_CUDA(cudaMemcpyAsync(bnorm2.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    Problem P;
+    P.sp = sp;
+    P.op64 = cop64; P.u64 = nullptr;
+    // mixed: BF16 operands on tensor cores when available (both mixed modes feed
+    // the tensor cores BF16 operands; FP32 mode falls back to FP32 CUDA cores
+    // only when the tensor-core operand could not be built)
+    const bool tc = prec != P64 && coarse_tc_ok(c);
+    P.oplo = tc ? coptc : cop32; P.ulo = nullptr;
+    P.res64 = cres64; P.ures = nullptr;
+    P.tag = "coarse";
+    const int inner = tc ? P16 : P32;
+    std::vector<int> iters;
+    std::vector<double> last;
+    int s = dc_solve(c, P, b, x, nrhs, bn2, bnorm2, tol, prec == P64 ? P64 : inner, max_iter, iters, last);
+    if (resid_out) {
+        double *r, *n2;
+        WD_TRY(ws_get(c, "cs.r", space_bytes(sp, P64, nrhs), (void **)&r));
+        WD_TRY(ws_get(c, "cs.n2", sizeof(double) * nrhs, (void **)&n2));
+        WD_TRY(cres64(c, b, x, r, nrhs, nullptr));
+        WD_TRY(blas_norm2(c, sp, P64, r, nrhs, n2));
+        std::vector<double> h(nrhs);
+        WD_CUDA(cudaMemcpyAsync(h.data(), n2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
+        WD_CUDA(cudaStreamSynchronize(c->st));
+        for (int i = 0; i < nrhs; ++i) resid_out[i] = bnorm2[i] > 0 ? sqrt(h[i] / bnorm2[i]) : 0.0;
+    }
+    return s;
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+void wd_mg_free(wd_ctx *c) {
+    if (!c || !c->mg) return;
+    wd_mg *g = c->mg;
+    cudaFree(g->P);
+    cudaFree(g->Dc);
+    cudaFree(g->nbr);
+    if (g->Wtc) cudaFree(g->Wtc);
+    if (g->Dc32) cudaFree(g->Dc32);
+    delete g;
+    c->mg = nullptr;
+}
+
+namespace wd {
+int mg_generate_tv(wd_ctx *c, int nv, int iters, uint64_t seed, double *tv_dev);   // wd_mlmc.cu
+}
+
+extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4], int tv_iters, uint64_t seed) {
+    if (!c || !agg || nv < 1 || nv % 6 != 0) {
+        set_error("wd_mg_setup: bad argument (nv must be a positive multiple of 6)");
+        return WD_EINVAL;
+    }
+    int nsite = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (agg[m] < 1 || c->dims[m] % agg[m]) { set_error("wd_mg_setup: aggregate extent %d does not divide %d", agg[m], c->dims[m]); return WD_EINVAL; }
+        nsite *= agg[m];
+    }
+    if (nv > 6 * nsite) { set_error("wd_mg_setup: nv > 6 * aggregate volume"); return WD_EINVAL; }
+    const int ncd = 2 * nv;
+    const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 3 * 12 * ncd);
+    if (smem > 227 * 1024) { set_error("wd_mg_setup: nv too large for the block assembly"); return WD_ENOTSUP; }
+    wd_mg_free(c);
+    wd_mg *g = new wd_mg();
+    memset(g, 0, sizeof(*g));
+    c->mg = g;
+    g->nv = nv;
+    g->ncd = ncd;
+    g->Vc = 1;
+    for (int m = 0; m < 4; ++m) { g->agg[m] = agg[m]; g->cd[m] = c->dims[m] / agg[m]; g->Vc *= g->cd[m]; }
+    const size_t nP = (size_t)c->g.V * 12 * nv;
+    const size_t nD = (size_t)g->Vc * 9 * ncd * ncd;
+    if (cudaMalloc(&g->P, nP * sizeof(double2)) != cudaSuccess || cudaMalloc(&g->Dc, nD * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        wd_mg_free(c);
+        set_error("wd_mg_setup: allocation failed");
+        return WD_ENOMEM;
+    }
+    MgGeom M = mg_geom(c);
+    double *tvd;
+    WD_TRY(ws_get(c, "mg.tv", nP * sizeof(double2), (void **)&tvd));
+    if (tv) {
+        WD_CUDA(cudaMemcpyAsync(tvd, tv, nP * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    } else {
+        WD_TRY(mg_generate_tv(c, nv, tv_iters, seed, tvd));
+    }
+    k_tv_to_P<<<(unsigned)((nP + 255) / 256), 256, 0, c->st>>>((const double2 *)tvd, g->P, M);
+    k_block_mgs<<<2 * g->Vc, 256, 0, c->st>>>(g->P, M);
+    k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
+    double2 hg[4][4][4];
+    host_gamma(hg);
+    WD_CUDA(cudaMemcpyToSymbolAsync(c_gamma, hg, sizeof(hg), 0, cudaMemcpyHostToDevice, c->st));
+    // links in lexicographic FP64 (kept by gauge ingest)
+    void *ulex = nullptr;
+    {
+        auto it = c->bufs.find("gauge.lex");
+        if (it == c->bufs.end()) { set_error("wd_mg_setup: links not resident"); return WD_ECUDA; }
+        ulex = it->second.first;
+    }
+    WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int4 bc = make_int4(c->bc[0], c->bc[1], c->bc[2], c->bc[3]);
+    k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, (long)nD);
+    c->launches += 5;
+    WD_CUDA(cudaGetLastError());
+    WD_TRY(coarse_tc_build(c));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    return WD_OK;
+}
+
+extern "C" int wd_coarse_apply(wd_ctx *c, const double *in, double *out, int nrhs, int prec) {
+    if (!c || !c->mg) { set_error("wd_coarse_apply: call wd_mg_setup first"); return WD_EINVAL; }
+    if (nrhs < 0 || ((!in || !out) && nrhs > 0) || prec < 0 || prec > 2) { set_error("wd_coarse_apply: bad argument"); return WD_EINVAL; }
+    if (nrhs == 0) return WD_OK;
+    if (prec == P64) return coarse_apply64(c, in, out, nullptr, 0.0, 1.0, nrhs);
+    const Space sp = coarse_space(c);
+    const bool tc = coarse_tc_ok(c);
+    void *xl, *yl;
+    WD_TRY(ws_get(c, "ca.x", space_bytes(sp, tc ? P16 : P32, nrhs), &xl));
+    WD_TRY(ws_get(c, "ca.y", space_bytes(sp, P32, nrhs), &yl));
+    WD_TRY(blas_copy_convert(c, sp, P64, in, tc ? P16 : P32, xl, nrhs, nullptr));
+    if (tc) WD_TRY(coarse_tc_apply(c, xl, (float *)yl, nrhs));
+    else WD_TRY(coarse_apply32(c, (const float *)xl, (float *)yl, nrhs));
+    WD_TRY(blas_copy_convert(c, sp, P32, yl, P64, out, nrhs, nullptr));
+    return WD_OK;
+}
+
+extern "C" int wd_restrict(wd_ctx *c, const double *fine, double *coarse, int nrhs) {
+    if (!c || !c->mg) { set_error("wd_restrict: call wd_mg_setup first"); return WD_EINVAL; }
+    if (nrhs <= 0) return nrhs == 0 ? WD_OK : WD_EINVAL;
+    const size_t f = field_bytes(c->g, P64, nrhs);
+    double *e, *o;
+    WD_TRY(ws_get(c, "rp.e", f, (void **)&e));
+    WD_TRY(ws_get(c, "rp.o", f, (void **)&o));
+    WD_TRY(user_to_eo(c, fine, true, P64, e, o, nrhs));
+    return mg_restrict_eo(c, e, o, coarse, nrhs);
+}
+
+extern "C" int wd_prolong(wd_ctx *c, const double *coarse, double *fine, int nrhs) {
+    if (!c || !c->mg) { set_error("wd_prolong: call wd_mg_setup first"); return WD_EINVAL; }
+    if (nrhs <= 0) return nrhs == 0 ? WD_OK : WD_EINVAL;
+    const size_t f = field_bytes(c->g, P64, nrhs);
+    double *e, *o;
+    WD_TRY(ws_get(c, "rp.e", f, (void **)&e));
+    WD_TRY(ws_get(c, "rp.o", f, (void **)&o));
+    WD_TRY(mg_prolong_eo(c, coarse, e, o, nrhs));
+    return eo_to_user(c, e, o, P64, fine, true, nrhs);
+}
+
+extern "C" int wd_coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
+                               double *true_resid_out) {
+    if (!c || !c->mg) { set_error("wd_coarse_solve: call wd_mg_setup first"); return WD_EINVAL; }
+    if (nrhs < 0 || ((!b || !x) && nrhs > 0) || !(tol > 0) || max_iter < 1 || prec < 0 || prec > 2) {
+        set_error("wd_coarse_solve: bad argument");
+        return WD_EINVAL;
+    }
+    if (nrhs == 0) return WD_OK;
+    int s = coarse_solve(c, b, x, nrhs, tol, prec, max_iter, true_resid_out);
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    return s;
+}

@@ -1,0 +1,295 @@
+// Two-level multigrid multilevel Monte Carlo (Sec. 2, Eqs. 9-12 with L = 2)
+// and the GPU test-vector setup.
+//
+// tr(B D^{-1}) = tr(B M_1) + tr(B P D_c^{-1} P^dag), M_1 = D^{-1} - P D_c^{-1} P^dag.
+// Level 1, N_1 fine Rademacher samples eta:
+//   X_1(t) = sum_{x in t} eta^dag B (D^{-1} eta - P D_c^{-1} P^dag eta)
+// Level 2, N_2 coarse Rademacher samples xi (coarse dof j = ncd*X + i, noise
+// sample | 2^23):   X_2(t) = sum_{x in t} (P xi)^dag B (P D_c^{-1} xi),
+// an unbiased estimate of tr(P^dag B(t) P D_c^{-1}) = tr(B(t) P D_c^{-1} P^dag)
+// (for B = 1 it is xi^dag D_c^{-1} xi since P^dag P = I).
+// The estimate is mean(X_1) + mean(X_2), its variance s_1^2/N_1 + s_2^2/N_2.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "wd_internal.h"
+
+namespace wd {
+
+int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, double *bo);
+int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma5, const double *ye,
+                      const double *yo, double *X);
+int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
+int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
+int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
+                 double *resid_out);
+Space coarse_space(wd_ctx *c);
+int auto_batch(wd_ctx *c, int total);
+int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double *sample_var, double *samples_out);
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// coarse Rademacher noise: xi[r][j] for samples (sample0 + r) | 2^23
+__global__ void k_coarse_noise(double2 *xi, unsigned long long seed, int sample0, long ncoarse, int nrhs) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= ncoarse * nrhs) return;
+    const unsigned long long r = (unsigned long long)(i / ncoarse), j = (unsigned long long)(i % ncoarse);
+    const unsigned long long sample = ((unsigned long long)sample0 + r) | (1ULL << 23);
+    const unsigned long long h = mix64(seed ^ (sample << 40) ^ j);
+    xi[i] = make_double2((h >> 63) ? -1.0 : 1.0, 0.0);
+}
+
+// d = z - w on FP64 eo fields (both parities stored separately); elementwise
+__global__ void k_sub(double *z, const double *w, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] -= w[i];
+}
+
+// partial X(rhs, t) = sum_{x in t} conj(a(x)) (B b)(x) for explicit eo fields a, b
+__global__ void k_contract_fields(Geom g, const double *ae, const double *ao, const double *be, const double *bo,
+                                  int gamma5, double *part, int bps) {
+    const int r = blockIdx.y, t = blockIdx.z;
+    const int slice = g.Vh / g.T;
+    const int chunk = (2 * slice + bps - 1) / bps;
+    const int u0 = blockIdx.x * chunk, u1 = min(u0 + chunk, 2 * slice);
+    double are = 0.0, aim = 0.0;
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        const int p = u >= slice, s = t * slice + (u - p * slice);
+        cx<double> va[12], vb[12];
+        SIO<double>::load((const uint4 *)(p ? ao : ae) + (size_t)r * 12 * g.Vh, g.Vh, s, va);
+        SIO<double>::load((const uint4 *)(p ? bo : be) + (size_t)r * 12 * g.Vh, g.Vh, s, vb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double sg = (gamma5 && k >= 6) ? -1.0 : 1.0;
+            are += sg * (va[k].re * vb[k].re + va[k].im * vb[k].im);
+            aim += sg * (va[k].re * vb[k].im - va[k].im * vb[k].re);
+        }
+    }
+    __shared__ double sh[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_xor_sync(0xffffffffu, are, o);
+        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { sh[0][wid] = are; sh[1][wid] = aim; }
+    __syncthreads();
+    if (wid == 0) {
+        are = lane < nw ? sh[0][lane] : 0.0;
+        aim = lane < nw ? sh[1][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            are += __shfl_xor_sync(0xffffffffu, are, o);
+            aim += __shfl_xor_sync(0xffffffffu, aim, o);
+        }
+        if (lane == 0) {
+            double *q = part + (((size_t)r * g.T + t) * bps + blockIdx.x) * 2;
+            q[0] = are;
+            q[1] = aim;
+        }
+    }
+}
+
+// X[sample0 + r][t] += sum_k part[r][t][k]
+__global__ void k_accumulate_fields(int T, const double *part, int bps, double *X, int sample0, int nrhs) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrhs * T) return;
+    const int r = idx / T, t = idx % T;
+    const double *q = part + ((size_t)r * T + t) * bps * 2;
+    double re = 0, im = 0;
+    for (int k = 0; k < bps; ++k) { re += q[2 * k]; im += q[2 * k + 1]; }
+    X[((size_t)(sample0 + r) * T + t) * 2] += re;
+    X[((size_t)(sample0 + r) * T + t) * 2 + 1] += im;
+}
+
+// estimate = mean_1 + mean_2, variance = var_1 / N1 + var_2 / N2
+__global__ void k_mlmc_combine(const double *m1, const double *v1, const double *m2, const double *v2, int N1, int N2,
+                               int n, double *mean, double *var) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        mean[2 * t] = m1[2 * t] + m2[2 * t];
+        mean[2 * t + 1] = m1[2 * t + 1] + m2[2 * t + 1];
+        var[t] = v1[t] / N1 + v2[t] / N2;
+    }
+}
+
+static int contract_fields(wd_ctx *c, const double *ae, const double *ao, const double *be, const double *bo,
+                           int gamma5, int nrhs, double *X, int sample0) {
+    const Geom &g = c->g;
+    int bps = (2 * (g.Vh / g.T) + 1023) / 1024;
+    if (bps < 1) bps = 1;
+    double *part;
+    WD_TRY(ws_get(c, "mlmc.part", sizeof(double) * 2 * (size_t)nrhs * g.T * bps, (void **)&part));
+    k_contract_fields<<<dim3(bps, nrhs, g.T), 256, 0, c->st>>>(g, ae, ao, be, bo, gamma5, part, bps);
+    k_accumulate_fields<<<(nrhs * g.T + 127) / 128, 128, 0, c->st>>>(g.T, part, bps, X, sample0, nrhs);
+    c->launches += 2;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double *var);
+
+int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
+                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out) {
+    if (!c->mg) { set_error("trace_estimate: MLMC2 needs wd_mg_setup"); return WD_EINVAL; }
+    const Geom &g = c->g;
+    const int T = g.T;
+    const long ncoarse = (long)c->mg->Vc * c->mg->ncd;
+    const int B = batch > 0 ? batch : auto_batch(c, N1 > N2 ? N1 : N2);
+    double *X1, *X2;
+    WD_TRY(ws_get(c, "mlmc.X1", sizeof(double) * 2 * (size_t)N1 * T, (void **)&X1));
+    WD_TRY(ws_get(c, "mlmc.X2", sizeof(double) * 2 * (size_t)N2 * T, (void **)&X2));
+    WD_CUDA(cudaMemsetAsync(X1, 0, sizeof(double) * 2 * (size_t)N1 * T, c->st));
+    WD_CUDA(cudaMemsetAsync(X2, 0, sizeof(double) * 2 * (size_t)N2 * T, c->st));
+    int64_t ns = 0;
+    // ---- level 1: eta^dag B (D^{-1} - P D_c^{-1} P^dag) eta
+    for (int s0 = 0; s0 < N1; s0 += B) {
+        const int nb = N1 - s0 < B ? N1 - s0 : B;
+        const size_t f = field_bytes(g, P64, nb);
+        double *be, *bo, *ze, *zo, *we, *wo, *bc, *yc;
+        WD_TRY(ws_get(c, "mlmc.be", f, (void **)&be));
+        WD_TRY(ws_get(c, "mlmc.bo", f, (void **)&bo));
+        WD_TRY(ws_get(c, "mlmc.ze", f, (void **)&ze));
+        WD_TRY(ws_get(c, "mlmc.zo", f, (void **)&zo));
+        WD_TRY(ws_get(c, "mlmc.we", f, (void **)&we));
+        WD_TRY(ws_get(c, "mlmc.wo", f, (void **)&wo));
+        WD_TRY(ws_get(c, "mlmc.bc", sizeof(double2) * ncoarse * nb, (void **)&bc));
+        WD_TRY(ws_get(c, "mlmc.yc", sizeof(double2) * ncoarse * nb, (void **)&yc));
+        WD_TRY(gen_noise_eo(c, seed, s0, nb, be, bo));
+        int s = solve_eo(c, be, bo, ze, zo, nb, tol, prec, 100000, nullptr, nullptr);
+        if (s != WD_OK) return s;
+        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb));
+        s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
+        if (s != WD_OK) return s;
+        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb));
+        const long n = (long)nb * 24 * g.Vh;
+        k_sub<<<1184, 256, 0, c->st>>>(ze, we, n);
+        k_sub<<<1184, 256, 0, c->st>>>(zo, wo, n);
+        c->launches += 2;
+        WD_TRY(contract_noise_eo(c, seed, s0, nb, gamma5, ze, zo, X1));
+        ns += 2 * nb;
+    }
+    // ---- level 2: (P xi)^dag B (P D_c^{-1} xi)
+    for (int s0 = 0; s0 < N2; s0 += B) {
+        const int nb = N2 - s0 < B ? N2 - s0 : B;
+        const size_t f = field_bytes(g, P64, nb);
+        double *xi, *yc, *ae, *ao, *be, *bo;
+        WD_TRY(ws_get(c, "mlmc.bc", sizeof(double2) * ncoarse * nb, (void **)&xi));
+        WD_TRY(ws_get(c, "mlmc.yc", sizeof(double2) * ncoarse * nb, (void **)&yc));
+        WD_TRY(ws_get(c, "mlmc.be", f, (void **)&ae));
+        WD_TRY(ws_get(c, "mlmc.bo", f, (void **)&ao));
+        WD_TRY(ws_get(c, "mlmc.ze", f, (void **)&be));
+        WD_TRY(ws_get(c, "mlmc.zo", f, (void **)&bo));
+        const long n = ncoarse * nb;
+        k_coarse_noise<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, s0, ncoarse, nb);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
+        int s = coarse_solve(c, xi, yc, nb, tol, prec, 100000, nullptr);
+        if (s != WD_OK) return s;
+        WD_TRY(mg_prolong_eo(c, xi, ae, ao, nb));
+        WD_TRY(mg_prolong_eo(c, yc, be, bo, nb));
+        WD_TRY(contract_fields(c, ae, ao, be, bo, gamma5, nb, X2, s0));
+        ns += nb;
+    }
+    double *m1, *v1, *m2, *v2, *mean, *var;
+    WD_TRY(ws_get(c, "mlmc.m1", sizeof(double) * 2 * (T + 1), (void **)&m1));
+    WD_TRY(ws_get(c, "mlmc.v1", sizeof(double) * (T + 1), (void **)&v1));
+    WD_TRY(ws_get(c, "mlmc.m2", sizeof(double) * 2 * (T + 1), (void **)&m2));
+    WD_TRY(ws_get(c, "mlmc.v2", sizeof(double) * (T + 1), (void **)&v2));
+    WD_TRY(ws_get(c, "mlmc.mean", sizeof(double) * 2 * (T + 1), (void **)&mean));
+    WD_TRY(ws_get(c, "mlmc.var", sizeof(double) * (T + 1), (void **)&var));
+    WD_TRY(mean_var_dev(c, X1, N1, m1, v1));
+    WD_TRY(mean_var_dev(c, X2, N2, m2, v2));
+    k_mlmc_combine<<<1, 128, 0, c->st>>>(m1, v1, m2, v2, N1, N2, T + 1, mean, var);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    WD_CUDA(cudaMemcpyAsync(estimate, mean, sizeof(double) * 2 * (T + 1), cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaMemcpyAsync(sample_var, var, sizeof(double) * (T + 1), cudaMemcpyDeviceToHost, c->st));
+    if (samples_out)
+        WD_CUDA(cudaMemcpyAsync(samples_out, X1, sizeof(double) * 2 * (size_t)N1 * T, cudaMemcpyDeviceToHost, c->st));
+    c->last_level2.resize((size_t)2 * N2 * T);
+    WD_CUDA(cudaMemcpyAsync(c->last_level2.data(), X2, sizeof(double) * 2 * (size_t)N2 * T, cudaMemcpyDeviceToHost,
+                            c->st));
+    c->last_n2 = N2;
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    *nsolves = ns;
+    return WD_OK;
+}
+
+__global__ void k_mean_var2(const double *X, int N, int T, double *out_mean, double *out_var) {
+    for (int t = threadIdx.x; t <= T; t += blockDim.x) {
+        double mr = 0, mi = 0;
+        for (int i = 0; i < N; ++i) {
+            double xr = 0, xi = 0;
+            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
+            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+            mr += xr; mi += xi;
+        }
+        mr /= N; mi /= N;
+        double v = 0;
+        for (int i = 0; i < N; ++i) {
+            double xr = 0, xi = 0;
+            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
+            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+            v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
+        }
+        out_mean[2 * t] = mr;
+        out_mean[2 * t + 1] = mi;
+        out_var[t] = N > 1 ? v / (N - 1) : 0.0;
+    }
+}
+
+static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double *var) {
+    k_mean_var2<<<1, 128, 0, c->st>>>(X, N, c->g.T, mean, var);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// ---- test vectors: tv_iters inverse iterations v <- D^{-1} v / |v| from Rademacher starts
+__global__ void k_scale_by(double *f, const double *n2a, const double *n2b, long per_rhs, int nrhs) {
+    const long n = per_rhs * nrhs;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / per_rhs);
+        f[i] *= 1.0 / sqrt(n2a[r] + n2b[r]);
+    }
+}
+
+int mg_generate_tv(wd_ctx *c, int nv, int iters, uint64_t seed, double *tv_dev) {
+    const Geom &g = c->g;
+    const size_t f = field_bytes(g, P64, nv);
+    double *ve, *vo, *xe, *xo, *n2;
+    WD_TRY(ws_get(c, "tv.ve", f, (void **)&ve));
+    WD_TRY(ws_get(c, "tv.vo", f, (void **)&vo));
+    WD_TRY(ws_get(c, "tv.xe", f, (void **)&xe));
+    WD_TRY(ws_get(c, "tv.xo", f, (void **)&xo));
+    WD_TRY(ws_get(c, "tv.n2", sizeof(double) * 2 * nv, (void **)&n2));
+    WD_TRY(gen_noise_eo(c, seed, 1 << 22, nv, ve, vo));
+    const Space sp = fine_space(g);
+    for (int it = 0; it < iters; ++it) {
+        int s = solve_eo(c, ve, vo, xe, xo, nv, 1e-6, P32, 100000, nullptr, nullptr);
+        if (s != WD_OK && s != WD_ENOCONV) return s;
+        WD_TRY(blas_norm2(c, sp, P64, xe, nv, n2));
+        WD_TRY(blas_norm2(c, sp, P64, xo, nv, n2 + nv));
+        const long per = 24L * g.Vh;
+        k_scale_by<<<1184, 256, 0, c->st>>>(xe, n2, n2 + nv, per, nv);
+        k_scale_by<<<1184, 256, 0, c->st>>>(xo, n2, n2 + nv, per, nv);
+        c->launches += 2;
+        std::swap(ve, xe);
+        std::swap(vo, xo);
+    }
+    return eo_to_user(c, ve, vo, P64, tv_dev, true, nv);
+}
+
+}  // namespace wd
+
+using namespace wd;
+
+extern "C" int wd_mlmc_level2_samples(wd_ctx *c, double *samples_out, int n2) {
+    if (!c || !samples_out || n2 != c->last_n2) { set_error("wd_mlmc_level2_samples: no matching MLMC2 estimate"); return WD_EINVAL; }
+    memcpy(samples_out, c->last_level2.data(), sizeof(double) * c->last_level2.size());
+    return WD_OK;
+}

@@ -20,9 +20,8 @@
 
 namespace wd {
 
-static int alloc_bivecs(wd_ctx *c, int pw, int pp, int nrhs, BiVecs &V, const char *tag) {
-    const size_t fw = field_bytes(c->g, pw, nrhs), fp = field_bytes(c->g, pp, nrhs);
-    std::string t(tag);
+static int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V, const std::string &t) {
+    const size_t fw = space_bytes(sp, pw, nrhs), fp = space_bytes(sp, pp, nrhs);
     WD_TRY(ws_get(c, (t + ".x").c_str(), fw, &V.x));
     WD_TRY(ws_get(c, (t + ".r").c_str(), fw, &V.r));
     WD_TRY(ws_get(c, (t + ".rh").c_str(), fw, &V.rh));
@@ -30,17 +29,16 @@ static int alloc_bivecs(wd_ctx *c, int pw, int pp, int nrhs, BiVecs &V, const ch
     WD_TRY(ws_get(c, (t + ".t").c_str(), fw, &V.t));
     WD_TRY(ws_get(c, (t + ".p").c_str(), fp, &V.p));
     WD_TRY(ws_get(c, (t + ".s").c_str(), fp, &V.s));
-    WD_TRY(ws_get(c, (t + ".tmp").c_str(), fp, &V.tmp));
     WD_TRY(ws_get(c, (t + ".st").c_str(), sizeof(BiState) * nrhs, (void **)&V.st));
-    V.bpr = reduction_bpr(c->g, nrhs);
+    V.sp = sp;
+    V.bpr = reduction_bpr(sp.units, nrhs);
     WD_TRY(ws_get(c, (t + ".part").c_str(), sizeof(double) * 3 * V.bpr * nrhs, (void **)&V.part));
     WD_TRY(ws_get(c, (t + ".count").c_str(), sizeof(int), (void **)&V.count));
     return WD_OK;
 }
 
-// Run BiCGStab iterations until no RHS is active or max_iter is reached.
-// Returns the number of iterations run; host sees the active count every
-// `check` iterations.
+// Run BiCGStab iterations until no RHS is active or max_iter is reached; the
+// host reads the active count every `check` iterations.
 static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter, int *ran) {
     int *hcount;
     WD_TRY(hws_get(c, "count", sizeof(int), (void **)&hcount));
@@ -69,132 +67,158 @@ static int read_states(wd_ctx *c, const BiState *dst, int nrhs, std::vector<BiSt
     return WD_OK;
 }
 
-int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
-             int prec, int max_iter, int *iters_out, double *resid_out) {
-    if (nrhs <= 0) return WD_OK;
-    const double k = c->kappa, k2 = k * k;
-    const size_t f64 = field_bytes(c->g, P64, nrhs);
-    double *bhat, *bn2, *tmp64;
-    WD_TRY(ws_get(c, "sol.bhat", f64, (void **)&bhat));
-    WD_TRY(ws_get(c, "sol.tmp64", f64, (void **)&tmp64));
-    WD_TRY(ws_get(c, "sol.bn2", sizeof(double) * 2 * nrhs, (void **)&bn2));
-    // |b|^2 over both parities
-    WD_TRY(blas_norm2(c, P64, b_e, nrhs, bn2));
-    WD_TRY(blas_norm2(c, P64, b_o, nrhs, bn2 + nrhs));
-    {
-        double *bsum;
-        WD_TRY(ws_get(c, "sol.bsum", sizeof(double) * nrhs, (void **)&bsum));
-        // bsum = bn2_e + bn2_o (tiny host round trip keeps this simple)
-        std::vector<double> h(2 * nrhs);
-        WD_CUDA(cudaMemcpyAsync(h.data(), bn2, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->st));
-        WD_CUDA(cudaStreamSynchronize(c->st));
-        for (int r = 0; r < nrhs; ++r) h[r] += h[nrhs + r];
-        WD_CUDA(cudaMemcpyAsync(bsum, h.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
-        bn2 = bsum;
-    }
-    std::vector<double> bnorm2(nrhs);
-    WD_CUDA(cudaMemcpyAsync(bnorm2.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
-    // b_hat = b_e + k H_eo b_o                                         (a3)
-    WD_TRY(hop(c, P64, P64, 0, bhat, b_o, b_e, 1.0, k, nrhs));
-
-    std::vector<int> iters(nrhs, 0);
-    std::vector<double> last_rn2(nrhs, 0.0);
-    int status = WD_OK;
+int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
+             const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,
+             std::vector<double> &last_rn2) {
+    const size_t f64 = space_bytes(P.sp, P64, nrhs);
+    const std::string tag(P.tag);
     const bool verbose = getenv("WD_VERBOSE") != nullptr;
+    iters.assign(nrhs, 0);
+    last_rn2.assign(nrhs, 0.0);
+    int status = WD_OK;
     if (prec == P64) {
         BiVecs V;
-        WD_TRY(alloc_bivecs(c, P64, P64, nrhs, V, "bi64"));
+        WD_TRY(alloc_bivecs(c, P.sp, P64, P64, nrhs, V, tag + ".bi64"));
+        V.op = P.op64;
+        V.op_user = P.u64;
         // the recursive residual drifts from the true one: aim at half the tolerance
-        WD_TRY(bicg_init(c, P64, P64, V, bhat, nrhs, 0.5 * tol, bn2));
+        WD_TRY(bicg_init(c, P64, P64, V, b, nrhs, 0.5 * tol, bnorm2_dev));
         int ran = 0;
         WD_TRY(bicg_run(c, P64, P64, V, nrhs, max_iter, &ran));
-        WD_CUDA(cudaMemcpyAsync(x_e, V.x, f64, cudaMemcpyDeviceToDevice, c->st));
+        WD_CUDA(cudaMemcpyAsync(x, V.x, f64, cudaMemcpyDeviceToDevice, c->st));
         std::vector<BiState> hs;
         WD_TRY(read_states(c, V.st, nrhs, hs));
         for (int r = 0; r < nrhs; ++r) {
             iters[r] = hs[r].iters;
+            last_rn2[r] = hs[r].rr;
             if (hs[r].flag) status = WD_EBREAKDOWN;
+            else if (hs[r].rr > hs[r].thr && status == WD_OK) status = WD_ENOCONV;
         }
-    } else {
-        const int pw = P32, pp = prec == P32 ? P32 : P16;
-        const double inner_tol = prec == P32 ? 1e-5 : 1e-2;
-        BiVecs V;
-        WD_TRY(alloc_bivecs(c, pw, pp, nrhs, V, prec == P32 ? "bi32" : "bi16"));
-        double *r64, *scale_d, *rn2_d, *blo;
-        WD_TRY(ws_get(c, "sol.r64", f64, (void **)&r64));
-        WD_TRY(ws_get(c, "sol.blo", field_bytes(c->g, pw, nrhs), (void **)&blo));
-        WD_TRY(ws_get(c, "sol.scale", sizeof(double) * 2 * nrhs, (void **)&scale_d));
-        WD_TRY(ws_get(c, "sol.rn2", sizeof(double) * nrhs, (void **)&rn2_d));
-        double *hsc;
-        WD_TRY(hws_get(c, "sol.hscale", sizeof(double) * 2 * nrhs, (void **)&hsc));
-        WD_TRY(blas_zero(c, x_e, f64));
-        WD_CUDA(cudaMemcpyAsync(r64, bhat, f64, cudaMemcpyDeviceToDevice, c->st));
-        std::vector<double> rn2(nrhs);
-        int used = 0;
-        for (int outer = 0; outer < 64; ++outer) {
-            WD_TRY(blas_norm2(c, P64, r64, nrhs, rn2_d));
-            WD_CUDA(cudaMemcpyAsync(rn2.data(), rn2_d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
-            WD_CUDA(cudaStreamSynchronize(c->st));
-            int open = 0;
-            for (int r = 0; r < nrhs; ++r) {
-                const bool done = !(rn2[r] > tol * tol * bnorm2[r]) || bnorm2[r] == 0.0;
-                if (!isfinite(rn2[r])) status = WD_EBREAKDOWN;
-                hsc[r] = done || !isfinite(rn2[r]) ? 0.0 : 1.0 / sqrt(rn2[r]);
-                hsc[nrhs + r] = done || !isfinite(rn2[r]) ? 0.0 : sqrt(rn2[r]);
-                open += hsc[r] != 0.0;
-            }
-            if (verbose) {
-                double worst = 0;
-                for (int r = 0; r < nrhs; ++r)
-                    if (bnorm2[r] > 0) worst = fmax(worst, sqrt(rn2[r] / bnorm2[r]));
-                fprintf(stderr, "[wd] outer %d: max rel residual %.3e, open %d, inner iterations so far %d\n", outer,
-                        worst, open, used);
-            }
-            last_rn2 = rn2;
-            if (open == 0 || used >= max_iter) break;
-            WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
-            // b_lo = r / |r|   (zero for converged RHS, which then stay inactive)
-            WD_TRY(blas_copy_convert(c, P64, r64, pw, blo, nrhs, scale_d));
-            WD_TRY(bicg_init(c, pw, pp, V, blo, nrhs, inner_tol, nullptr));
-            int ran = 0;
-            WD_TRY(bicg_run(c, pw, pp, V, nrhs, max_iter - used, &ran));
-            used += ran;
-            std::vector<BiState> hs;
-            WD_TRY(read_states(c, V.st, nrhs, hs));
-            for (int r = 0; r < nrhs; ++r) iters[r] += hs[r].iters;
-            if (verbose) {
-                int flags = 0, mx = 0;
-                double rr = 0;
-                for (int r = 0; r < nrhs; ++r) { flags += hs[r].flag; mx = hs[r].iters > mx ? hs[r].iters : mx; rr = fmax(rr, hs[r].rr); }
-                fprintf(stderr, "[wd]   inner: ran %d, max iters %d, max |r|^2 %.3e, breakdowns %d\n", ran, mx, rr, flags);
-                // true inner residual |b_lo - D_hat e|^2 in the inner precision (V.v, V.t as scratch)
-                WD_TRY(hop(c, pp == P16 ? P32 : pp, P32, 1, V.t, V.x, nullptr, 0.0, 1.0, nrhs));
-                double *tn;
-                WD_TRY(ws_get(c, "sol.dbg", sizeof(double) * nrhs, (void **)&tn));
-                if (pp == P32) {
-                    WD_TRY(hop(c, P32, P32, 0, V.v, V.t, blo, 1.0, k2, nrhs, false, V.x, -1.0));
-                    WD_TRY(blas_norm2(c, P32, V.v, nrhs, tn));
-                    std::vector<double> ht(nrhs);
-                    WD_CUDA(cudaMemcpyAsync(ht.data(), tn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
-                    WD_CUDA(cudaStreamSynchronize(c->st));
-                    double w = 0;
-                    for (int r = 0; r < nrhs; ++r) w = fmax(w, ht[r]);
-                    fprintf(stderr, "[wd]   inner true |b - A e|^2 (fp32): %.3e\n", w);
-                }
-            }
-            // x += |r| e  (FP64)
-            WD_TRY(blas_axpy_mixed(c, x_e, pw, V.x, scale_d + nrhs, nrhs));
-            // r = b_hat - D_hat x = b_hat - x + k^2 H_eo H_oe x          (FP64)
-            WD_TRY(hop(c, P64, P64, 1, tmp64, x_e, nullptr, 0.0, 1.0, nrhs));
-            WD_TRY(hop(c, P64, P64, 0, r64, tmp64, bhat, 1.0, k2, nrhs, false, x_e, -1.0));
-        }
+        return status;
     }
+    const int pw = P32, pp = prec == P32 ? P32 : P16;
+    const double inner_tol = prec == P32 ? 1e-5 : 1e-2;
+    BiVecs V;
+    WD_TRY(alloc_bivecs(c, P.sp, pw, pp, nrhs, V, tag + (prec == P32 ? ".bi32" : ".bi16")));
+    V.op = P.oplo;
+    V.op_user = P.ulo;
+    double *r64, *scale_d, *rn2_d, *blo, *hsc;
+    WD_TRY(ws_get(c, (tag + ".r64").c_str(), f64, (void **)&r64));
+    WD_TRY(ws_get(c, (tag + ".blo").c_str(), space_bytes(P.sp, pw, nrhs), (void **)&blo));
+    WD_TRY(ws_get(c, (tag + ".scale").c_str(), sizeof(double) * 2 * nrhs, (void **)&scale_d));
+    WD_TRY(ws_get(c, (tag + ".rn2").c_str(), sizeof(double) * nrhs, (void **)&rn2_d));
+    WD_TRY(hws_get(c, (tag + ".hscale").c_str(), sizeof(double) * 2 * nrhs, (void **)&hsc));
+    WD_TRY(blas_zero(c, x, f64));
+    WD_CUDA(cudaMemcpyAsync(r64, b, f64, cudaMemcpyDeviceToDevice, c->st));
+    std::vector<double> rn2(nrhs);
+    int used = 0;
+    for (int outer = 0; outer < 64; ++outer) {
+        WD_TRY(blas_norm2(c, P.sp, P64, r64, nrhs, rn2_d));
+        WD_CUDA(cudaMemcpyAsync(rn2.data(), rn2_d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
+        WD_CUDA(cudaStreamSynchronize(c->st));
+        int open = 0;
+        for (int r = 0; r < nrhs; ++r) {
+            const bool done = !(rn2[r] > tol * tol * bnorm2[r]) || bnorm2[r] == 0.0;
+            if (!isfinite(rn2[r])) status = WD_EBREAKDOWN;
+            hsc[r] = done || !isfinite(rn2[r]) ? 0.0 : 1.0 / sqrt(rn2[r]);
+            hsc[nrhs + r] = done || !isfinite(rn2[r]) ? 0.0 : sqrt(rn2[r]);
+            open += hsc[r] != 0.0;
+        }
+        last_rn2 = rn2;
+        if (verbose) {
+            double worst = 0;
+            for (int r = 0; r < nrhs; ++r)
+                if (bnorm2[r] > 0) worst = fmax(worst, sqrt(rn2[r] / bnorm2[r]));
+            fprintf(stderr, "[wd] %s outer %d: max rel residual %.3e, open %d, inner iterations so far %d\n",
+                    P.tag, outer, worst, open, used);
+        }
+        if (open == 0 || used >= max_iter) break;
+        WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
+        // b_lo = r / |r|   (zero for converged RHS, which then stay inactive)
+        WD_TRY(blas_copy_convert(c, P.sp, P64, r64, pw, blo, nrhs, scale_d));
+        WD_TRY(bicg_init(c, pw, pp, V, blo, nrhs, inner_tol, nullptr));
+        int ran = 0;
+        WD_TRY(bicg_run(c, pw, pp, V, nrhs, max_iter - used, &ran));
+        used += ran;
+        std::vector<BiState> hs;
+        WD_TRY(read_states(c, V.st, nrhs, hs));
+        for (int r = 0; r < nrhs; ++r) iters[r] += hs[r].iters;
+        if (verbose) {
+            int flags = 0, mx = 0;
+            for (int r = 0; r < nrhs; ++r) { flags += hs[r].flag; mx = hs[r].iters > mx ? hs[r].iters : mx; }
+            fprintf(stderr, "[wd]   inner: ran %d, max iters %d, breakdowns %d\n", ran, mx, flags);
+        }
+        // x += |r| e  (FP64), then the FP64 residual r = b - A x
+        WD_TRY(blas_axpy_mixed(c, P.sp, x, pw, V.x, scale_d + nrhs, nrhs));
+        WD_TRY(P.res64(c, b, x, r64, nrhs, P.ures));
+    }
+    if (status == WD_OK)
+        for (int r = 0; r < nrhs; ++r)
+            if (bnorm2[r] > 0 && !(last_rn2[r] <= tol * tol * bnorm2[r])) status = WD_ENOCONV;
+    return status;
+}
+
+// ---- the even-site Schur operator D_hat = 1 - k^2 H_eo H_oe ----------------
+struct SchurArgs {
+    int pin, pout;
+    void *tmp;      // odd-parity field in precision pin
+};
+
+static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
+    SchurArgs *S = (SchurArgs *)u;
+    WD_TRY(hop(c, S->pin, S->pin, 1, S->tmp, in, nullptr, 0.0, 1.0, nrhs));
+    return hop(c, S->pin, S->pout, 0, out, S->tmp, in, 1.0, -c->kappa * c->kappa, nrhs);
+}
+
+// r = b - D_hat x = b - x + k^2 H_eo H_oe x, FP64
+static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
+    SchurArgs *S = (SchurArgs *)u;
+    WD_TRY(hop(c, P64, P64, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
+    return hop(c, P64, P64, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
+}
+
+int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
+             int prec, int max_iter, int *iters_out, double *resid_out) {
+    if (nrhs <= 0) return WD_OK;
+    const double k = c->kappa;
+    const Space sp = fine_space(c->g);
+    const size_t f64 = field_bytes(c->g, P64, nrhs);
+    double *bhat, *bn2, *tmp64;
+    WD_TRY(ws_get(c, "sol.bhat", f64, (void **)&bhat));
+    WD_TRY(ws_get(c, "sol.tmp64", f64, (void **)&tmp64));
+    WD_TRY(ws_get(c, "sol.bn2", sizeof(double) * 3 * nrhs, (void **)&bn2));
+    // |b|^2 over both parities
+    WD_TRY(blas_norm2(c, sp, P64, b_e, nrhs, bn2));
+    WD_TRY(blas_norm2(c, sp, P64, b_o, nrhs, bn2 + nrhs));
+    std::vector<double> bnorm2(2 * nrhs);
+    WD_CUDA(cudaMemcpyAsync(bnorm2.data(), bn2, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    for (int r = 0; r < nrhs; ++r) bnorm2[r] += bnorm2[nrhs + r];
+    bnorm2.resize(nrhs);
+    WD_CUDA(cudaMemcpyAsync(bn2 + 2 * nrhs, bnorm2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
+    // b_hat = b_e + k H_eo b_o                                         (a3)
+    WD_TRY(hop(c, P64, P64, 0, bhat, b_o, b_e, 1.0, k, nrhs));
+
+    const int pp = prec == P16 ? P16 : (prec == P32 ? P32 : P64);
+    void *tmplo = nullptr;
+    if (prec != P64) WD_TRY(ws_get(c, "sol.tmplo", field_bytes(c->g, pp, nrhs), &tmplo));
+    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo};
+    Problem P;
+    P.sp = sp;
+    P.op64 = schur_op; P.u64 = &s64;
+    P.oplo = schur_op; P.ulo = &slo;
+    P.res64 = schur_res64; P.ures = &s64;
+    P.tag = "fine";
+    std::vector<int> iters;
+    std::vector<double> last_rn2;
+    int status = dc_solve(c, P, bhat, x_e, nrhs, bn2 + 2 * nrhs, bnorm2, tol, prec, max_iter, iters, last_rn2);
+    if (status != WD_OK && status != WD_ENOCONV && status != WD_EBREAKDOWN) return status;
     // x_o = b_o + k H_oe x_e                                             (a7)
     WD_TRY(hop(c, P64, P64, 1, x_o, x_e, b_o, 1.0, k, nrhs));
     // True FP64 residual of the full system, when asked for.  Without it the
-    // last FP64 Schur residual of the outer loop (mixed modes) or the FP64
-    // recursion (FP64 mode) certifies convergence: the full residual of
-    // (x_e, x_o) equals the Schur residual on the even sites.
+    // last FP64 Schur residual (mixed modes) or the FP64 recursion (FP64 mode)
+    // certifies convergence: the full residual of (x_e, x_o) equals the Schur
+    // residual on the even sites.
     if (resid_out) {
         double *re, *ro, *n2;
         WD_TRY(ws_get(c, "sol.re", f64, (void **)&re));
@@ -202,27 +226,16 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
         WD_TRY(ws_get(c, "sol.n2", sizeof(double) * 2 * nrhs, (void **)&n2));
         WD_TRY(hop(c, P64, P64, 0, re, x_o, b_e, 1.0, k, nrhs, false, x_e, -1.0));
         WD_TRY(hop(c, P64, P64, 1, ro, x_e, b_o, 1.0, k, nrhs, false, x_o, -1.0));
-        WD_TRY(blas_norm2(c, P64, re, nrhs, n2));
-        WD_TRY(blas_norm2(c, P64, ro, nrhs, n2 + nrhs));
+        WD_TRY(blas_norm2(c, sp, P64, re, nrhs, n2));
+        WD_TRY(blas_norm2(c, sp, P64, ro, nrhs, n2 + nrhs));
         std::vector<double> h(2 * nrhs);
         WD_CUDA(cudaMemcpyAsync(h.data(), n2, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->st));
         WD_CUDA(cudaStreamSynchronize(c->st));
+        status = status == WD_EBREAKDOWN ? status : WD_OK;
         for (int r = 0; r < nrhs; ++r) {
             const double res = bnorm2[r] > 0 ? sqrt((h[r] + h[nrhs + r]) / bnorm2[r]) : 0.0;
             resid_out[r] = res;
             if (!(res <= tol * 1.0000001) && status == WD_OK) status = isfinite(res) ? WD_ENOCONV : WD_EBREAKDOWN;
-        }
-    } else if (status == WD_OK) {
-        if (prec == P64) {
-            std::vector<BiState> hs;
-            BiVecs V;
-            WD_TRY(alloc_bivecs(c, P64, P64, nrhs, V, "bi64"));
-            WD_TRY(read_states(c, V.st, nrhs, hs));
-            for (int r = 0; r < nrhs; ++r)
-                if (hs[r].rr > hs[r].thr) status = WD_ENOCONV;
-        } else {
-            for (int r = 0; r < nrhs; ++r)
-                if (bnorm2[r] > 0 && !(last_rn2[r] <= tol * tol * bnorm2[r])) status = WD_ENOCONV;
         }
     }
     if (iters_out)
