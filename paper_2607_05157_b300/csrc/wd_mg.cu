@@ -410,6 +410,7 @@ int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs)
 
 // ---- coarse solves ------------------------------------------------------------
 int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs);   // wd_coarse_tc.cu
+int coarse_tc_check(wd_ctx *c);
 int coarse_tc_build(wd_ctx *c);
 bool coarse_tc_ok(wd_ctx *c);
 
@@ -450,6 +451,7 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
     std::vector<int> iters;
     std::vector<double> last;
     int s = dc_solve(c, P, b, x, nrhs, bn2, bnorm2, tol, prec == P64 ? P64 : inner, max_iter, iters, last);
+    if (tc) WD_TRY(coarse_tc_check(c));
     if (resid_out) {
         double *r, *n2;
         WD_TRY(ws_get(c, "cs.r", space_bytes(sp, P64, nrhs), (void **)&r));
@@ -561,6 +563,7 @@ extern "C" int wd_coarse_apply(wd_ctx *c, const double *in, double *out, int nrh
     if (tc) WD_TRY(coarse_tc_apply(c, xl, (float *)yl, nrhs));
     else WD_TRY(coarse_apply32(c, (const float *)xl, (float *)yl, nrhs));
     WD_TRY(blas_copy_convert(c, sp, P32, yl, P64, out, nrhs, nullptr));
+    if (tc) WD_TRY(coarse_tc_check(c));
     return WD_OK;
 }
 
