@@ -173,7 +173,19 @@ int wd_coarse_solve(wd_ctx *ctx, const double *b, double *x, int nrhs, double to
 int wd_link_force(wd_ctx *ctx, const double *w, const double *z, int nrhs, double *G, double *H,
                   int accumulate);
 
-/* Replace the links / kappa of an existing context (same dims and bc). */
+/* Derivatives of the estimate of L = Re sum_t weights[t] * mean_i X_i(t) for
+ * the Hutchinson / probing estimators of trace_estimate (same method,
+ * dilution, N, d, seed, op, prec, batch, tol; weights host [T], nullable =
+ * all ones).  Writes dkappa (host) and the link force G, H (device complex128
+ * [4][T][Z][Y][X][3][3], overwritten) so that for U -> U + h Delta,
+ * dL/dh = Re sum tr(Delta (G + H)); i.e. the gradient in PyTorch's convention
+ * is (G + H)^dagger per link.  One extra solve per RHS unless op = g5 with
+ * equal weights (then w = g5 z by gamma5-hermiticity). */
+int trace_gradient(wd_ctx *ctx, int method, int dilution, int N, int d, uint64_t seed, int op, int prec,
+                   int batch, double tol, const double *weights, double *dkappa, double *G, double *H);
+
+/* Replace the links / kappa of an existing context (same dims and bc).
+ * gauge: host or device pointer (unified addressing), layout as wd_create. */
 int wd_update_gauge(wd_ctx *ctx, const double *gauge, double kappa);
 
 /* ---- allocation-free variant ------------------------------------------ */

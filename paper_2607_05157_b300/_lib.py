@@ -48,6 +48,8 @@ _SIGS = {
     'wd_coarse_solve': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p]),
     'wd_link_force': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int]),
     'wd_update_gauge': (c_int, [c_void_p, c_void_p, c_double]),
+    'trace_gradient': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int, c_int, c_double,
+                               c_void_p, P(c_double), c_void_p, c_void_p]),
     'wd_profile': (c_int, [c_void_p, c_int]),
     'wd_profile_get': (c_int, [c_void_p, c_int, P(c_int64), P(c_double), P(c_double)]),
     'wd_launch_count': (c_int64, [c_void_p]),

@@ -213,3 +213,22 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def trace_gradient(h, method, dilution, N, T, d=0, seed=0, op=1, prec=WD_MIXED_FP32, batch=0, tol=1e-10,
+                   weights=None, G=None, H=None, link_shape=None):
+    """Returns (dkappa, G, H) for L = Re sum_t weights[t] mean_i X_i(t)."""
+    import torch
+    if G is None:
+        G = torch.empty(link_shape, dtype=torch.complex128, device='cuda')
+        H = torch.empty_like(G)
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        assert w.shape == (T,)
+    dk = ctypes.c_double()
+    check(lib.trace_gradient(h, int(method), int(dilution), int(N), int(d), ctypes.c_uint64(seed), int(op),
+                             int(prec), int(batch), float(tol), _host_ptr(w) if w is not None else None,
+                             ctypes.byref(dk), _dev_ptr(G, torch.complex128, 'G'), _dev_ptr(H, torch.complex128, 'H')),
+          'trace_gradient')
+    return dk.value, G, H

@@ -171,7 +171,7 @@ static int ingest_gauge(wd_ctx *c, const double *gauge_host) {
     const size_t n = (size_t)4 * c->g.V * 18;
     double *dU;
     WD_TRY(ws_get(c, "gauge.lex", n * sizeof(double), (void **)&dU));
-    WD_CUDA(cudaMemcpyAsync(dU, gauge_host, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    WD_CUDA(cudaMemcpyAsync(dU, gauge_host, n * sizeof(double), cudaMemcpyDefault, c->st));
     const int4 bc = make_int4(c->bc[0], c->bc[1], c->bc[2], c->bc[3]);
     const unsigned blocks = (unsigned)((c->g.V + 127) / 128);
     k_gauge_eo<double><<<blocks, 128, 0, c->st>>>(dU, c->gauge[P64], c->g, bc);

@@ -286,6 +286,44 @@ int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma
     return WD_OK;
 }
 
+// Estimator parameters for Hutchinson / probing with the given dilution
+int est_params(wd_ctx *c, int method, int dilution, int d, uint64_t seed, int gamma5, EstParams &P) {
+    memset(&P, 0, sizeof(P));
+    const int dil = dilution & 0xff;
+    if (dil != 1 && dil != 12) { set_error("dilution must be 1 or 12 (optionally | WD_DIL_TIME)"); return WD_EINVAL; }
+    P.seed = seed;
+    P.dil = dil;
+    P.TT = (dilution & WD_DIL_TIME) ? c->g.T : 1;
+    P.gamma5 = gamma5;
+    P.nc = 1;
+    if (method == WD_PROBE) {
+        int nc = 0, sig[4];
+        const int s = probe_color(c->dims, 4, d, &nc, sig, nullptr);
+        if (s != WD_OK) { set_error("no torus colouring for distance %d", d); return s; }
+        P.nc = nc;
+        for (int j = 0; j < 4; ++j) P.sigma[j] = sig[j];
+    }
+    P.m = P.nc * P.dil * P.TT;
+    return WD_OK;
+}
+
+// RHS [g0, g0 + nrhs) of the sample-major enumeration into FP64 eo fields
+// (nrhs = 0: only report the RHS count per sample)
+int gen_masked_eo(wd_ctx *c, int method, int dilution, int d, uint64_t seed, int g0, int nrhs, double *be,
+                  double *bo, int *per_sample) {
+    EstParams P;
+    WD_TRY(est_params(c, method, dilution, d, seed, 0, P));
+    *per_sample = P.m;
+    if (nrhs <= 0) return WD_OK;
+    P.g0 = g0;
+    P.nrhs = nrhs;
+    const long n = (long)c->g.V * nrhs;
+    k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, c->g, be, bo);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 }  // namespace wd
 
 using namespace wd;
@@ -297,9 +335,10 @@ extern "C" int trace_estimate(wd_ctx *c, int method, int dilution, int N, int n2
         set_error("trace_estimate: bad argument");
         return WD_EINVAL;
     }
-    const int dil = dilution & 0xff;
-    const bool tdil = (dilution & WD_DIL_TIME) != 0;
-    if (dil != 1 && dil != 12) { set_error("trace_estimate: dilution must be 1 or 12 (optionally | WD_DIL_TIME)"); return WD_EINVAL; }
+    if ((dilution & 0xff) != 1 && (dilution & 0xff) != 12) {
+        set_error("trace_estimate: dilution must be 1 or 12 (optionally | WD_DIL_TIME)");
+        return WD_EINVAL;
+    }
     int64_t ns = 0;
     if (method == WD_MLMC2) {
         if (n2 < 1) { set_error("trace_estimate: MLMC2 needs n2 >= 1"); return WD_EINVAL; }
@@ -309,20 +348,7 @@ extern "C" int trace_estimate(wd_ctx *c, int method, int dilution, int N, int n2
     }
     if (method != WD_HUTCH && method != WD_PROBE) { set_error("trace_estimate: unknown method %d", method); return WD_EINVAL; }
     EstParams P;
-    memset(&P, 0, sizeof(P));
-    P.seed = seed;
-    P.dil = dil;
-    P.TT = tdil ? c->g.T : 1;
-    P.gamma5 = op == WD_TR_G5_DINV;
-    P.nc = 1;
-    if (method == WD_PROBE) {
-        int nc = 0, sig[4];
-        const int s = probe_color(c->dims, 4, d, &nc, sig, nullptr);
-        if (s != WD_OK) { set_error("trace_estimate: no torus colouring for distance %d", d); return s; }
-        P.nc = nc;
-        for (int j = 0; j < 4; ++j) P.sigma[j] = sig[j];
-    }
-    P.m = P.nc * P.dil * P.TT;
+    WD_TRY(est_params(c, method, dilution, d, seed, op == WD_TR_G5_DINV, P));
     const long total = (long)N * P.m;
     if (total > (1L << 30)) { set_error("trace_estimate: too many right-hand sides"); return WD_EINVAL; }
     const int T = c->g.T;
