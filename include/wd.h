@@ -188,6 +188,29 @@ int trace_gradient(wd_ctx *ctx, int method, int dilution, int N, int d, uint64_t
  * gauge: host or device pointer (unified addressing), layout as wd_create. */
 int wd_update_gauge(wd_ctx *ctx, const double *gauge, double kappa);
 
+/* ---- batched solves over several lattices ------------------------------ */
+
+typedef struct wd_batch wd_batch;
+
+/* Group 1..8 contexts (lattices of any even extents, distinct contexts) that
+ * were created on the same CUDA stream. */
+int wd_batch_create(wd_batch **out, wd_ctx *const *ctxs, int n);
+int wd_batch_destroy(wd_batch *b);
+
+/* Solve D_j x_j = b_j for every lattice j of the batch in lockstep, mixed
+ * precision only (WD_MIXED_FP32 or WD_MIXED_BF16 inner, FP64 defect
+ * correction).  Each inner BiCGStab iteration applies all lattices' even-odd
+ * operators with two persistent batched stencil launches (one static work
+ * list over all lattices' site and RHS tiles).  use_graph = 1 captures the
+ * inner iterations between convergence checks into a CUDA graph and replays
+ * it.  rhs[j], x[j]: device complex128 [nrhs[j]][T][Z][Y][X][4][3] of lattice j.
+ * iters_out (host, nullable) [n]: inner iterations of the slowest RHS per
+ * lattice; resid_out (host, nullable) [sum nrhs]: final FP64 relative residual
+ * ||b - D x|| / ||b|| per RHS (the even-site Schur residual, which equals the
+ * full residual since the odd sites are reconstructed exactly). */
+int wd_batch_solve(wd_batch *b, const double *const *rhs, double *const *x, const int *nrhs, double tol, int prec,
+                   int max_iter, int use_graph, int *iters_out, double *resid_out);
+
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* The paper has no counterpart to this entry point.

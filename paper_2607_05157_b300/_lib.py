@@ -35,6 +35,10 @@ _SIGS = {
     'wd_destroy': (c_int, [c_void_p]),
     'wd_apply': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int]),
     'wd_apply_noalloc': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int]),
+    'wd_batch_create': (c_int, [P(c_void_p), P(c_void_p), c_int]),
+    'wd_batch_destroy': (c_int, [c_void_p]),
+    'wd_batch_solve': (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_int), c_double, c_int, c_int, c_int,
+                               c_void_p, c_void_p]),
     'wd_solve': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p]),
     'probe_color': (c_int, [P(c_int), c_int, c_int, P(c_int), P(c_int), c_void_p]),
     'trace_estimate': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int, c_int,

@@ -232,3 +232,38 @@ def trace_gradient(h, method, dilution, N, T, d=0, seed=0, op=1, prec=WD_MIXED_F
                              ctypes.byref(dk), _dev_ptr(G, torch.complex128, 'G'), _dev_ptr(H, torch.complex128, 'H')),
           'trace_gradient')
     return dk.value, G, H
+
+
+class Batch:
+    """wd_batch over several Contexts sharing one stream (lattices of any sizes)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        self.h = ctypes.c_void_p()
+        check(lib.wd_batch_create(ctypes.byref(self.h), arr, len(self.contexts)), 'wd_batch_create')
+
+    def solve(self, rhs, tol=1e-10, prec=WD_MIXED_FP32, max_iter=100000, use_graph=True):
+        """rhs: list of complex128 CUDA tensors; returns (xs, iters[n], resid[sum nrhs])."""
+        import torch
+        xs = [torch.empty_like(b) for b in rhs]
+        n = len(rhs)
+        rp = (ctypes.c_void_p * n)(*[_dev_ptr(b, torch.complex128).value for b in rhs])
+        xp = (ctypes.c_void_p * n)(*[_dev_ptr(x, torch.complex128).value for x in xs])
+        nr = (ctypes.c_int * n)(*[b.shape[0] for b in rhs])
+        iters = np.zeros(n, np.int32)
+        res = np.zeros(sum(b.shape[0] for b in rhs), np.float64)
+        check(lib.wd_batch_solve(self.h, rp, xp, nr, float(tol), int(prec), int(max_iter), int(bool(use_graph)),
+                                 _host_ptr(iters), _host_ptr(res)), 'wd_batch_solve')
+        return xs, iters, res
+
+    def close(self):
+        if getattr(self, 'h', None) is not None:
+            lib.wd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -88,6 +88,59 @@ static const void *gauge_parity(wd_ctx *c, int prec, int p) {
     return (const char *)c->gauge[prec] + p * per;
 }
 
+static cudaError_t launch_hop_any(int pin, int pout, const HopArgs &A, int R, bool dag, int th, cudaStream_t st) {
+    if (pin == P64) return launch_hop<double, double, double, double>(A, R, dag, th, st);
+    if (pin == P32) return launch_hop<float, float, float, float>(A, R, dag, th, st);
+    if (pout == P16) return launch_hop<bf16, bf16, bf16, bf16>(A, R, dag, th, st);
+    return launch_hop<bf16, float, bf16, bf16>(A, R, dag, th, st);
+}
+
+static int rhs_bucket(int nrhs) {
+    int b = 1;
+    while (b < nrhs && b < 4096) b <<= 1;
+    return b;
+}
+
+// Autotuner: time every (RHS tile, block size) candidate on this launch's own
+// buffers (the real launch follows and overwrites `out`), keep the fastest per
+// (input precision, output precision, RHS bucket).  Not usable during stream
+// capture: the caller must tune (one uncaptured call) before capturing.
+static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, int *R, int *th) {
+    const int key = (pin * 4 + pout) * 8192 + rhs_bucket(A.nrhs);
+    auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) { *R = it->second.first; *th = it->second.second; return WD_OK; }
+    *R = c->hop_R[pin];
+    *th = c->hop_threads[pin];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->st, &cs);
+    if (!c->autotune || cs != cudaStreamCaptureStatusNone) return WD_OK;
+    const int Rs[3] = {1, 2, 4}, Ts[3] = {64, 128, 256};
+    cudaEvent_t e0, e1;
+    WD_CUDA(cudaEventCreate(&e0));
+    WD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (pin == P64 && Rs[i] > 2) continue;          // FP64 R = 4 spills
+            WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));   // warm
+            WD_CUDA(cudaEventRecord(e0, c->st));
+            for (int k = 0; k < 3; ++k) WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));
+            WD_CUDA(cudaEventRecord(e1, c->st));
+            WD_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            WD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            c->launches += 4;
+            if (ms < best) { best = ms; *R = Rs[i]; *th = Ts[j]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tuned[key] = std::make_pair(*R, *th);
+    if (getenv("WD_VERBOSE"))
+        fprintf(stderr, "[wd] tuned stencil in=%d out=%d nrhs<=%d: R=%d threads=%d (%.3f ms/launch)\n", pin, pout,
+                rhs_bucket(A.nrhs), *R, *th, best / 3);
+    return WD_OK;
+}
+
 int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const void *w, double a, double b,
         int nrhs, bool dag, const void *w2, double cc) {
     if (nrhs <= 0) return WD_OK;
@@ -96,18 +149,15 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field
     A.gauge = gauge_parity(c, pin, p);
-    const int R = c->hop_R[pin], th = c->hop_threads[pin];
+    int R, th;
+    WD_TRY(tune_hop(c, pin, pout, A, dag, &R, &th));
     // algorithmic bytes: nrhs x (in + out [+ w + w2]) spinors + 8 links per output site
     const double sb_in = spinor_bytes(pin), sb_out = spinor_bytes(pout);
     const double bytes = (double)c->g.Vh *
                          (nrhs * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
     prof_begin(c, pin == P64 ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
-    cudaError_t e;
-    if (pin == P64) e = launch_hop<double, double, double, double>(A, R, dag, th, c->st);
-    else if (pin == P32) e = launch_hop<float, float, float, float>(A, R, dag, th, c->st);
-    else if (pout == P16) e = launch_hop<bf16, bf16, bf16, bf16>(A, R, dag, th, c->st);
-    else e = launch_hop<bf16, float, bf16, bf16>(A, R, dag, th, c->st);
+    cudaError_t e = launch_hop_any(pin, pout, A, R, dag, th, c->st);
     prof_end(c, slot);
     c->launches++;
     if (e != cudaSuccess) { set_error("hop launch: %s", cudaGetErrorString(e)); return WD_ECUDA; }
@@ -211,6 +261,7 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->mg = nullptr;
     c->last_n2 = 0;
     for (int p = 0; p < 3; ++p) { c->hop_R[p] = p == P64 ? 1 : 2; c->hop_threads[p] = 128; c->gauge[p] = nullptr; }
+    c->autotune = getenv("WD_NO_AUTOTUNE") == nullptr;
     const size_t nl = (size_t)2 * 8 * 9 * c->g.Vh;
     const size_t eb[3] = {16, 8, 4};
     for (int p = 0; p < 3; ++p) {

@@ -506,21 +506,28 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
     return WD_OK;
 }
 
-int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
+// BLAS half after v = A p: alpha = rho / (rh, v), s = r - alpha v
+int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
-    // v = A p
-    WD_TRY(V.op(c, V.p, V.v, nrhs, V.op_user));
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
         k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr);
         k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
     }));
     c->launches += 3;
-    // t = A s
-    WD_TRY(V.op(c, V.s, V.t, nrhs, V.op_user));
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// BLAS half after t = A s: omega, x and r updates, rho and beta, p update
+int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
+    const long Vh = V.sp.units, n = Vh * nrhs;
+    dim3 grid(V.bpr, nrhs);
+    const unsigned eb = ew_blocks(n);
+    const int sb = (nrhs + 127) / 128;
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
         k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr);
         k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
@@ -531,6 +538,13 @@ int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     c->launches += 5;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
+}
+
+int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
+    WD_TRY(V.op(c, V.p, V.v, nrhs, V.op_user));       // v = A p
+    WD_TRY(bicg_after_v(c, pw, pp, V, nrhs));
+    WD_TRY(V.op(c, V.s, V.t, nrhs, V.op_user));       // t = A s
+    return bicg_after_t(c, pw, pp, V, nrhs);
 }
 
 }  // namespace wd

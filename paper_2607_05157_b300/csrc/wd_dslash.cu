@@ -13,6 +13,8 @@
 // work: (1 -/+ g_mu) psi has rank 2 in the chiral basis, g_mu = [[0,A],[A^dag,0]]:
 //   h = psi_up + sign*A psi_down,  lower half = sign*A^dag (U h).
 // Epilogue: out = a*w + c*w2 + b*(H in), w/w2 same-parity fields (nullable).
+#include <type_traits>
+
 #include "wd_internal.h"
 
 namespace wd {
@@ -87,7 +89,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, int s, int nb, int rb,
 }
 
 template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
-__global__ void __launch_bounds__(128) hop_kernel(HopArgs A) {
+__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     typedef typename RealOf<SIn>::type RT;
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
@@ -141,6 +143,214 @@ __global__ void __launch_bounds__(128) hop_kernel(HopArgs A) {
     }
 }
 
+// ---- FP32 arithmetic on packed pairs (Blackwell f32x2 FMA/ADD) -------------
+// Complex numbers are float2 (re, im).  A complex multiply-add u*h + acc is two
+// packed FMAs: (u.re, u.re) * (h.re, h.im) + acc, then (-u.im, u.im) * (h.im, h.re);
+// the broadcast / sign pairs of a link are built once and reused by both
+// half-spinor spins and every RHS of the tile, the swapped h once per h.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sw(float2 a) { return make_float2(a.y, a.x); }
+
+template <int MU, int SIGN>
+__device__ __forceinline__ void proj_f2(const float2 p[12], float2 h[6]) {
+    const float S = (float)SIGN;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+        if (MU == 0) {        // A = -i s1: (A pd) = (-i p3, -i p2); -i q = (q.im, -q.re)
+            h[c] = __ffma2_rn(sw(p3), f2(S, -S), p0);
+            h[3 + c] = __ffma2_rn(sw(p2), f2(S, -S), p1);
+        } else if (MU == 1) { // A = -i s2: (-p3, p2)
+            h[c] = __ffma2_rn(p3, f2(-S, -S), p0);
+            h[3 + c] = __ffma2_rn(p2, f2(S, S), p1);
+        } else if (MU == 2) { // A = -i s3: (-i p2, i p3); i q = (-q.im, q.re)
+            h[c] = __ffma2_rn(sw(p2), f2(S, -S), p0);
+            h[3 + c] = __ffma2_rn(sw(p3), f2(-S, S), p1);
+        } else {              // A = 1
+            h[c] = __ffma2_rn(p2, f2(S, S), p0);
+            h[3 + c] = __ffma2_rn(p3, f2(S, S), p1);
+        }
+    }
+}
+
+template <int MU, int SIGN>
+__device__ __forceinline__ void recon_f2(float2 acc[12], const float2 h[6]) {
+    const float S = (float)SIGN;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 h0 = h[c], h1 = h[3 + c];
+        acc[c] = __fadd2_rn(acc[c], h0);
+        acc[3 + c] = __fadd2_rn(acc[3 + c], h1);
+        if (MU == 0) {        // A^dag (h0, h1) = (i h1, i h0)
+            acc[6 + c] = __ffma2_rn(sw(h1), f2(-S, S), acc[6 + c]);
+            acc[9 + c] = __ffma2_rn(sw(h0), f2(-S, S), acc[9 + c]);
+        } else if (MU == 1) { // (h1, -h0)
+            acc[6 + c] = __ffma2_rn(h1, f2(S, S), acc[6 + c]);
+            acc[9 + c] = __ffma2_rn(h0, f2(-S, -S), acc[9 + c]);
+        } else if (MU == 2) { // (i h0, -i h1)
+            acc[6 + c] = __ffma2_rn(sw(h0), f2(-S, S), acc[6 + c]);
+            acc[9 + c] = __ffma2_rn(sw(h1), f2(S, -S), acc[9 + c]);
+        } else {              // (h0, h1)
+            acc[6 + c] = __ffma2_rn(h0, f2(S, S), acc[6 + c]);
+            acc[9 + c] = __ffma2_rn(h1, f2(S, S), acc[9 + c]);
+        }
+    }
+}
+
+template <typename S> __device__ __forceinline__ void load_f2(const void *p, long Vh, long s, float2 v[12]) {
+    cx<float> t[12];
+    SIO<S>::load(p, Vh, s, t);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2(t[k].re, t[k].im);
+}
+
+template <typename SIn, typename G, int R, int D, bool DAG>
+__device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int rb, float2 acc[][12]) {
+    constexpr int MU = D & 3;
+    constexpr bool FWD = D < 4;
+    constexpr int SIGN = (FWD != DAG) ? -1 : +1;
+    const long Vh = A.g.Vh;
+    cx<float> u[9];
+    LIO<G>::load((const char *)A.gauge + (size_t)D * 9 * Vh * LIO<G>::ELEM, Vh, s, u);
+    float2 ur[9], ui[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { ur[k] = f2(u[k].re, u[k].re); ui[k] = f2(-u[k].im, u[k].im); }
+    constexpr int NCH = SIO<SIn>::NCH;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int rhs = rb * R + r;
+        if (rhs < A.nrhs) {
+            float2 psi[12], h[6], hs[6], uh[6];
+            load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi);
+            proj_f2<MU, SIGN>(psi, h);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hs[k] = sw(h[k]);
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float2 a = __fmul2_rn(ur[3 * i], h[3 * sp]);
+                    a = __ffma2_rn(ui[3 * i], hs[3 * sp], a);
+#pragma unroll
+                    for (int j = 1; j < 3; ++j) {
+                        a = __ffma2_rn(ur[3 * i + j], h[3 * sp + j], a);
+                        a = __ffma2_rn(ui[3 * i + j], hs[3 * sp + j], a);
+                    }
+                    uh[3 * sp + i] = a;
+                }
+            recon_f2<MU, SIGN>(acc[r], uh);
+        }
+    }
+}
+
+// one output site s for RHS tile rb
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
+__device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
+    const Geom &g = A.g;
+    int x, y, z, t;
+    eo_coords(g, A.p, s, x, y, z, t);
+    const int xp = x + 1 == g.X ? 0 : x + 1, xm = x == 0 ? g.X - 1 : x - 1;
+    const int yp = y + 1 == g.Y ? 0 : y + 1, ym = y == 0 ? g.Y - 1 : y - 1;
+    const int zp = z + 1 == g.Z ? 0 : z + 1, zm = z == 0 ? g.Z - 1 : z - 1;
+    const int tp = t + 1 == g.T ? 0 : t + 1, tm = t == 0 ? g.T - 1 : t - 1;
+    float2 acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = f2(0.f, 0.f);
+    hop_dir_f2<SIn, G, R, 0, DAG>(A, s, eo_index(g, xp, y, z, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 1, DAG>(A, s, eo_index(g, x, yp, z, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 2, DAG>(A, s, eo_index(g, x, y, zp, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 3, DAG>(A, s, eo_index(g, x, y, z, tp), rb, acc);
+    hop_dir_f2<SIn, G, R, 4, DAG>(A, s, eo_index(g, xm, y, z, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 5, DAG>(A, s, eo_index(g, x, ym, z, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 6, DAG>(A, s, eo_index(g, x, y, zm, t), rb, acc);
+    hop_dir_f2<SIn, G, R, 7, DAG>(A, s, eo_index(g, x, y, z, tm), rb, acc);
+    const long Vh = g.Vh;
+    constexpr int NO = SIO<SOut>::NCH, NW = SIO<SW>::NCH;
+    const float2 a2 = f2((float)A.a, (float)A.a), b2 = f2((float)A.b, (float)A.b), c2 = f2((float)A.c, (float)A.c);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int rhs = rb * R + r;
+        if (rhs >= A.nrhs) break;
+        float2 o[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = __fmul2_rn(b2, acc[r][k]);
+        if (A.w) {
+            float2 wv[12];
+            load_f2<SW>((const uint4 *)A.w + (size_t)rhs * NW * Vh, Vh, s, wv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(a2, wv[k], o[k]);
+        }
+        if (A.w2) {
+            float2 wv[12];
+            load_f2<SW>((const uint4 *)A.w2 + (size_t)rhs * NW * Vh, Vh, s, wv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(c2, wv[k], o[k]);
+        }
+        cx<float> oc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) oc[k] = cmake(o[k].x, o[k].y);
+        SIO<SOut>::store((uint4 *)A.out + (size_t)rhs * NO * Vh, Vh, s, oc);
+    }
+}
+
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
+__global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
+    const int rb = blockIdx.x % A.nrb;
+    const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
+    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG>(A, rb, s);
+}
+
+// Persistent batched stencil over several lattices (row a11): one launch walks
+// a static work list of (lattice, site tile, RHS tile) items -- the items of
+// lattice j are the blocks [base_j, base_j + blocks_j) -- with a grid sized to
+// the resident CTAs of the GPU; CTA i takes items i, i + gridDim.x, ...  No
+// atomics and no waits: the assignment is fixed, so the result is
+// deterministic and nothing can hang.
+template <typename SIn, typename SOut, typename SW, typename G, int R>
+__global__ void __launch_bounds__(128) hop_batched_f2(const __grid_constant__ HopBatch B) {
+    for (int item = blockIdx.x; item < B.total; item += gridDim.x) {
+        int j = 0, base = 0;
+        while (j + 1 < B.njobs && item - base >= B.blocks[j]) { base += B.blocks[j]; ++j; }
+        const HopArgs &A = B.job[j];
+        const int lb = item - base;
+        const int rb = lb % A.nrb;
+        const int s = (lb / A.nrb) * blockDim.x + threadIdx.x;
+        if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, false>(A, rb, s);
+    }
+}
+
+template <typename SIn, typename SOut, typename SW, typename G>
+cudaError_t launch_hop_batched(HopBatch B, int R, cudaStream_t st) {
+    if (R != 1 && R != 2 && R != 4) R = 2;
+    const int th = 128;
+    B.total = 0;
+    for (int j = 0; j < B.njobs; ++j) {
+        B.job[j].nrb = (B.job[j].nrhs + R - 1) / R;
+        B.blocks[j] = ((B.job[j].g.Vh + th - 1) / th) * B.job[j].nrb;
+        B.total += B.blocks[j];
+    }
+    if (B.total == 0) return cudaSuccess;
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+#define WD_HB_CASE(RR)                                                                             \
+    if (R == RR) {                                                                                 \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hop_batched_f2<SIn, SOut, SW, G, RR>, th, 0); \
+        int grid = sms * (per > 0 ? per : 1);                                                      \
+        if (grid > B.total) grid = B.total;                                                        \
+        hop_batched_f2<SIn, SOut, SW, G, RR><<<grid, th, 0, st>>>(B);                              \
+    }
+    WD_HB_CASE(1) WD_HB_CASE(2) WD_HB_CASE(4)
+#undef WD_HB_CASE
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_hop_batched<float, float, float, float>(HopBatch, int, cudaStream_t);
+template cudaError_t launch_hop_batched<bf16, bf16, bf16, bf16>(HopBatch, int, cudaStream_t);
+template cudaError_t launch_hop_batched<bf16, float, bf16, bf16>(HopBatch, int, cudaStream_t);
+
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStream_t st) {
     HopArgs A = A0;
@@ -149,10 +359,16 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     A.nrb = (A.nrhs + R - 1) / R;
     const int sblocks = (A.g.Vh + threads - 1) / threads;
     dim3 grid((unsigned)(sblocks * A.nrb));
-#define WD_HOP_CASE(RR)                                                                        \
-    if (R == RR) {                                                                             \
-        if (dag) hop_kernel<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);          \
-        else hop_kernel<SIn, SOut, SW, G, RR, false><<<grid, threads, 0, st>>>(A);             \
+    constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
+#define WD_HOP_CASE(RR)                                                                                \
+    if (R == RR) {                                                                                     \
+        if constexpr (PACKED) {                                                                        \
+            if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);           \
+            else hop_kernel_f2<SIn, SOut, SW, G, RR, false><<<grid, threads, 0, st>>>(A);              \
+        } else {                                                                                       \
+            if (dag) hop_kernel<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);              \
+            else hop_kernel<SIn, SOut, SW, G, RR, false><<<grid, threads, 0, st>>>(A);                 \
+        }                                                                                              \
     }
     WD_HOP_CASE(1) WD_HOP_CASE(2) WD_HOP_CASE(4)
 #undef WD_HOP_CASE

@@ -41,6 +41,16 @@ struct HopArgs {
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
 
+// several lattices' stencils in one persistent launch (FP32 arithmetic only)
+static constexpr int WD_MAX_BATCH = 8;
+struct HopBatch {
+    HopArgs job[WD_MAX_BATCH];
+    int blocks[WD_MAX_BATCH];
+    int njobs, total;
+};
+template <typename SIn, typename SOut, typename SW, typename G>
+cudaError_t launch_hop_batched(HopBatch B, int R, cudaStream_t st);
+
 // Precision tags of the inner solve
 enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 
@@ -89,8 +99,10 @@ struct wd_ctx {
     bool prof;
     std::vector<wd_prof_rec> recs;
     std::vector<cudaEvent_t> event_pool;
-    int hop_R[3];                   // RHS tile per precision (autotuned)
+    int hop_R[3];                   // default RHS tile per input precision
     int hop_threads[3];
+    bool autotune;                  // time the stencil launch shapes on first use
+    std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
     std::vector<double> last_level2;    // [n2][T][2]
     int last_n2;
@@ -155,7 +167,10 @@ struct BiVecs {
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev);
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
+int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
+int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
 int reduction_bpr(long units, int nrhs);
+int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V, const std::string &tag);
 
 // Defect-correction (or plain FP64) BiCGStab solve of A x = b on one space
 // (wd_solver.cu).  b, x: FP64 vectors of the space (x overwritten).

@@ -20,7 +20,7 @@
 
 namespace wd {
 
-static int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V, const std::string &t) {
+int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V, const std::string &t) {
     const size_t fw = space_bytes(sp, pw, nrhs), fp = space_bytes(sp, pp, nrhs);
     WD_TRY(ws_get(c, (t + ".x").c_str(), fw, &V.x));
     WD_TRY(ws_get(c, (t + ".r").c_str(), fw, &V.r));
