@@ -114,14 +114,15 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(c->st, &cs);
     if (!c->autotune || cs != cudaStreamCaptureStatusNone) return WD_OK;
-    const int Rs[3] = {1, 2, 4}, Ts[3] = {64, 128, 256};
+    // RHS tile R (1, 2, 4; +10 = software-pipelined FP32 variant) x block size
+    const int Rs[5] = {1, 2, 4, 11, 12}, Ts[3] = {64, 128, 256};
     cudaEvent_t e0, e1;
     WD_CUDA(cudaEventCreate(&e0));
     WD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 5; ++i)
         for (int j = 0; j < 3; ++j) {
-            if (pin == P64 && Rs[i] > 2) continue;          // FP64 R = 4 spills
+            if (pin == P64 && Rs[i] > 2) continue;          // FP64: plain R = 1, 2 only (R = 4 spills)
             WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));   // warm
             WD_CUDA(cudaEventRecord(e0, c->st));
             for (int k = 0; k < 3; ++k) WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));

@@ -21,7 +21,9 @@
 
 struct wd_batch {
     std::vector<wd_ctx *> c;
-    cudaStream_t st;
+    cudaStream_t st;      // the contexts' stream
+    cudaStream_t priv;    // private non-blocking stream the solves run on (capturable)
+    cudaEvent_t ev;
 };
 
 namespace wd {
@@ -103,17 +105,49 @@ extern "C" int wd_batch_create(wd_batch **out, wd_ctx *const *ctxs, int n) {
     wd_batch *b = new wd_batch();
     b->c.assign(ctxs, ctxs + n);
     b->st = ctxs[0]->st;
+    if (cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        set_error("wd_batch_create: stream creation failed");
+        return WD_ECUDA;
+    }
     *out = b;
     return WD_OK;
 }
 
 extern "C" int wd_batch_destroy(wd_batch *b) {
+    if (!b) return WD_OK;
+    cudaStreamSynchronize(b->priv);
+    cudaStreamDestroy(b->priv);
+    cudaEventDestroy(b->ev);
     delete b;
     return WD_OK;
 }
 
+static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *rhs, double *const *x,
+                            const int *nrhs, double tol, int prec, int max_iter, int use_graph, int *iters_out,
+                            double *resid_out);
+
+// The solve runs on the batch's private stream (a CUDA graph cannot be captured
+// on the legacy default stream), ordered after prior work of the contexts'
+// stream and before later work on it.
 extern "C" int wd_batch_solve(wd_batch *b, const double *const *rhs, double *const *x, const int *nrhs, double tol,
                               int prec, int max_iter, int use_graph, int *iters_out, double *resid_out) {
+    if (!b) { set_error("wd_batch_solve: null batch"); return WD_EINVAL; }
+    WD_CUDA(cudaEventRecord(b->ev, b->st));
+    WD_CUDA(cudaStreamWaitEvent(b->priv, b->ev, 0));
+    for (auto *c : b->c) c->st = b->priv;
+    const int s = batch_solve_impl(b, b->priv, rhs, x, nrhs, tol, prec, max_iter, use_graph, iters_out, resid_out);
+    cudaEventRecord(b->ev, b->priv);
+    cudaStreamWaitEvent(b->st, b->ev, 0);
+    for (auto *c : b->c) c->st = b->st;
+    return s;
+}
+
+static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *rhs, double *const *x,
+                            const int *nrhs, double tol, int prec, int max_iter, int use_graph, int *iters_out,
+                            double *resid_out) {
     if (!b || !rhs || !x || !nrhs || !(tol > 0) || max_iter < 1 || (prec != P32 && prec != P16)) {
         set_error("wd_batch_solve: bad argument (prec must be WD_MIXED_FP32 or WD_MIXED_BF16)");
         return WD_EINVAL;
@@ -170,7 +204,7 @@ extern "C" int wd_batch_solve(wd_batch *b, const double *const *rhs, double *con
             WD_TRY(blas_norm2(l.c, sp, P64, l.r64, l.nrhs, l.rn2));
             WD_CUDA(cudaMemcpyAsync(l.last.data(), l.rn2, sizeof(double) * l.nrhs, cudaMemcpyDeviceToHost, l.c->st));
         }
-        WD_CUDA(cudaStreamSynchronize(b->st));
+        WD_CUDA(cudaStreamSynchronize(bst));
         for (auto &l : L) {
             l.open = false;
             for (int r = 0; r < l.nrhs; ++r) {
@@ -197,15 +231,15 @@ extern "C" int wd_batch_solve(wd_batch *b, const double *const *rhs, double *con
             if (graph) {
                 if (!exec) {
                     cudaGraph_t g;
-                    WD_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+                    WD_CUDA(cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal));
                     int s = iter_multi(L, pp, K);
-                    cudaError_t e = cudaStreamEndCapture(b->st, &g);
+                    cudaError_t e = cudaStreamEndCapture(bst, &g);
                     if (s != WD_OK) return s;
                     WD_CUDA(e);
                     WD_CUDA(cudaGraphInstantiate(&exec, g, 0));
                     cudaGraphDestroy(g);
                 }
-                WD_CUDA(cudaGraphLaunch(exec, b->st));
+                WD_CUDA(cudaGraphLaunch(exec, bst));
                 L[0].c->launches += 1;
             } else {
                 WD_TRY(iter_multi(L, pp, K));
@@ -240,7 +274,7 @@ extern "C" int wd_batch_solve(wd_batch *b, const double *const *rhs, double *con
         ri += l.nrhs;
         if (iters_out) iters_out[j] = mx;
     }
-    WD_CUDA(cudaStreamSynchronize(b->st));
+    WD_CUDA(cudaStreamSynchronize(bst));
     if (status != WD_OK) set_error("wd_batch_solve: %s", status == WD_ENOCONV ? "not converged" : "breakdown");
     return status;
 }

@@ -243,8 +243,78 @@ __device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int 
     }
 }
 
+// Split form of one direction for the software-pipelined variant: the loads of
+// direction d+1 (link + R neighbour spinors) are issued before the arithmetic
+// of direction d, so each thread keeps two directions of loads in flight.
+template <typename SIn, typename G, int R, int D>
+__device__ __forceinline__ void load_dir_f2(const HopArgs &A, int s, int nb, int rb, cx<float> u[9],
+                                            float2 psi[][12]) {
+    const long Vh = A.g.Vh;
+    LIO<G>::load((const char *)A.gauge + (size_t)D * 9 * Vh * LIO<G>::ELEM, Vh, s, u);
+    constexpr int NCH = SIO<SIn>::NCH;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int rhs = rb * R + r;
+        if (rhs < A.nrhs) load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi[r]);
+    }
+}
+
+template <int R, int D, bool DAG>
+__device__ __forceinline__ void compute_dir_f2(const HopArgs &A, int rb, const cx<float> u[9], float2 psi[][12],
+                                               float2 acc[][12]) {
+    constexpr int MU = D & 3;
+    constexpr bool FWD = D < 4;
+    constexpr int SIGN = (FWD != DAG) ? -1 : +1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (rb * R + r < A.nrhs) {
+            float2 h[6], hs[6], uh[6];
+            proj_f2<MU, SIGN>(psi[r], h);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hs[k] = sw(h[k]);
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float2 a = __fmul2_rn(f2(u[3 * i].re, u[3 * i].re), h[3 * sp]);
+                    a = __ffma2_rn(f2(-u[3 * i].im, u[3 * i].im), hs[3 * sp], a);
+#pragma unroll
+                    for (int j = 1; j < 3; ++j) {
+                        a = __ffma2_rn(f2(u[3 * i + j].re, u[3 * i + j].re), h[3 * sp + j], a);
+                        a = __ffma2_rn(f2(-u[3 * i + j].im, u[3 * i + j].im), hs[3 * sp + j], a);
+                    }
+                    uh[3 * sp + i] = a;
+                }
+            recon_f2<MU, SIGN>(acc[r], uh);
+        }
+    }
+}
+
+template <typename SIn, typename G, int R, bool DAG>
+__device__ __forceinline__ void hop_dirs_pipelined(const HopArgs &A, int s, int rb, const int nb[8],
+                                                   float2 acc[][12]) {
+    cx<float> ua[9], ub[9];
+    float2 pa[R][12], pb[R][12];
+    load_dir_f2<SIn, G, R, 0>(A, s, nb[0], rb, ua, pa);
+    load_dir_f2<SIn, G, R, 1>(A, s, nb[1], rb, ub, pb);
+    compute_dir_f2<R, 0, DAG>(A, rb, ua, pa, acc);
+    load_dir_f2<SIn, G, R, 2>(A, s, nb[2], rb, ua, pa);
+    compute_dir_f2<R, 1, DAG>(A, rb, ub, pb, acc);
+    load_dir_f2<SIn, G, R, 3>(A, s, nb[3], rb, ub, pb);
+    compute_dir_f2<R, 2, DAG>(A, rb, ua, pa, acc);
+    load_dir_f2<SIn, G, R, 4>(A, s, nb[4], rb, ua, pa);
+    compute_dir_f2<R, 3, DAG>(A, rb, ub, pb, acc);
+    load_dir_f2<SIn, G, R, 5>(A, s, nb[5], rb, ub, pb);
+    compute_dir_f2<R, 4, DAG>(A, rb, ua, pa, acc);
+    load_dir_f2<SIn, G, R, 6>(A, s, nb[6], rb, ua, pa);
+    compute_dir_f2<R, 5, DAG>(A, rb, ub, pb, acc);
+    load_dir_f2<SIn, G, R, 7>(A, s, nb[7], rb, ub, pb);
+    compute_dir_f2<R, 6, DAG>(A, rb, ua, pa, acc);
+    compute_dir_f2<R, 7, DAG>(A, rb, ub, pb, acc);
+}
+
 // one output site s for RHS tile rb
-template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE = false>
 __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     const Geom &g = A.g;
     int x, y, z, t;
@@ -258,14 +328,21 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[r][k] = f2(0.f, 0.f);
-    hop_dir_f2<SIn, G, R, 0, DAG>(A, s, eo_index(g, xp, y, z, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 1, DAG>(A, s, eo_index(g, x, yp, z, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 2, DAG>(A, s, eo_index(g, x, y, zp, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 3, DAG>(A, s, eo_index(g, x, y, z, tp), rb, acc);
-    hop_dir_f2<SIn, G, R, 4, DAG>(A, s, eo_index(g, xm, y, z, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 5, DAG>(A, s, eo_index(g, x, ym, z, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 6, DAG>(A, s, eo_index(g, x, y, zm, t), rb, acc);
-    hop_dir_f2<SIn, G, R, 7, DAG>(A, s, eo_index(g, x, y, z, tm), rb, acc);
+    if constexpr (PIPE) {
+        const int nb[8] = {eo_index(g, xp, y, z, t), eo_index(g, x, yp, z, t), eo_index(g, x, y, zp, t),
+                           eo_index(g, x, y, z, tp), eo_index(g, xm, y, z, t), eo_index(g, x, ym, z, t),
+                           eo_index(g, x, y, zm, t), eo_index(g, x, y, z, tm)};
+        hop_dirs_pipelined<SIn, G, R, DAG>(A, s, rb, nb, acc);
+    } else {
+        hop_dir_f2<SIn, G, R, 0, DAG>(A, s, eo_index(g, xp, y, z, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 1, DAG>(A, s, eo_index(g, x, yp, z, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 2, DAG>(A, s, eo_index(g, x, y, zp, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 3, DAG>(A, s, eo_index(g, x, y, z, tp), rb, acc);
+        hop_dir_f2<SIn, G, R, 4, DAG>(A, s, eo_index(g, xm, y, z, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 5, DAG>(A, s, eo_index(g, x, ym, z, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 6, DAG>(A, s, eo_index(g, x, y, zm, t), rb, acc);
+        hop_dir_f2<SIn, G, R, 7, DAG>(A, s, eo_index(g, x, y, z, tm), rb, acc);
+    }
     const long Vh = g.Vh;
     constexpr int NO = SIO<SOut>::NCH, NW = SIO<SW>::NCH;
     const float2 a2 = f2((float)A.a, (float)A.a), b2 = f2((float)A.b, (float)A.b), c2 = f2((float)A.c, (float)A.c);
@@ -295,11 +372,11 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     }
 }
 
-template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE>
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG>(A, rb, s);
+    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s);
 }
 
 // Persistent batched stencil over several lattices (row a11): one launch walks
@@ -355,6 +432,9 @@ template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStream_t st) {
     HopArgs A = A0;
     if (A.nrhs <= 0) return cudaSuccess;
+    // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined (FP32 arithmetic only)
+    const bool pipe = R > 10;
+    if (pipe) R -= 10;
     if (R != 1 && R != 2 && R != 4) R = 1;
     A.nrb = (A.nrhs + R - 1) / R;
     const int sblocks = (A.g.Vh + threads - 1) / threads;
@@ -363,8 +443,13 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
 #define WD_HOP_CASE(RR)                                                                                \
     if (R == RR) {                                                                                     \
         if constexpr (PACKED) {                                                                        \
-            if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);           \
-            else hop_kernel_f2<SIn, SOut, SW, G, RR, false><<<grid, threads, 0, st>>>(A);              \
+            if (pipe) {                                                                                \
+                if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, true><<<grid, threads, 0, st>>>(A); \
+                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, true><<<grid, threads, 0, st>>>(A);    \
+            } else {                                                                                   \
+                if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, false><<<grid, threads, 0, st>>>(A); \
+                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, false><<<grid, threads, 0, st>>>(A);   \
+            }                                                                                          \
         } else {                                                                                       \
             if (dag) hop_kernel<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);              \
             else hop_kernel<SIn, SOut, SW, G, RR, false><<<grid, threads, 0, st>>>(A);                 \
