@@ -180,6 +180,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512)):
+    """Row a8: tcgen05 coarse 9-point block stencil on the 24^3x48 two-level
+    workload (4^4 aggregates, 24 test vectors -> 48x48 blocks, 2592 coarse
+    sites), CUDA-event times of the kernel, algorithmic TFLOP/s (8 ncd^2 per
+    block, 9 blocks per site and RHS) and block-stream GB/s."""
+    dims = (24, 24, 24, 48)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
+    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=0, seed=3)
+    Vc, ncd = 6 * 6 * 6 * 12, 48
+    out = []
+    for nrhs in rhs_list:
+        x = torch.randn((nrhs, Vc, ncd), dtype=torch.complex128, device='cuda')
+        y = torch.empty_like(x)
+        for _ in range(2):
+            api.wd_coarse_apply(ctx.h, x, y, 1)
+        torch.cuda.synchronize()
+        api.wd_profile(ctx.h, True)
+        for _ in range(5):
+            api.wd_coarse_apply(ctx.h, x, y, 1)
+        n, ms, fl = api.wd_profile_get(ctx.h, wd.WD_K_COARSE)
+        api.wd_profile(ctx.h, False)
+        per = ms / n
+        wbytes = Vc * 96 * 864 * 2
+        out.append({"nrhs": nrhs, "ms_per_launch": per, "TFLOP_s": fl / n / (per * 1e-3) / 1e12,
+                    "block_stream_GB_s": wbytes / (per * 1e-3) / 1e9})
+    ctx.close()
+    peaks = measured_peaks()
+    return {"workload": "24^3x48, 4^4 aggregates, nv=24 (48x48 blocks), BF16 tcgen05, FP32 accumulate",
+            "bf16_peak_TFLOP_s": peaks['bf16_tflops'] if peaks else 1800.0, "points": out}
+
+
+def gradient_measure(wd, api, torch, synth):
+    """Row a10: d/dkappa and the link force of the probing (d=2, full dilution)
+    estimate of tr[g5 D^-1] on 8^3x16 (192 solves + force), wall time."""
+    dims = (8, 8, 8, 16)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1005), KAPPA, BC)
+    shape = (4, 16, 8, 8, 8, 3, 3)
+    api.trace_gradient(ctx.h, wd.WD_PROBE, 12, 1, 16, d=2, seed=1, op=1, tol=TOL, link_shape=shape)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.trace_gradient(ctx.h, wd.WD_PROBE, 12, 1, 16, d=2, seed=2, op=1, tol=TOL, link_shape=shape)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "8^3x16 probing d=2 x 12 dilution (192 RHS), gamma5, dkappa + link force",
+            "ms": 1e3 * dt}
+
+
+def batched_measure(wd, torch, synth):
+    """Row a11: 8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16) solved together
+    (persistent multi-lattice stencil, CUDA graph) vs one after another."""
+    specs = [((8, 8, 8, 16), 0.125, 64), ((12, 12, 12, 24), 0.13, 32), ((16, 16, 16, 32), 0.13, 16)]
+    ctxs, bs = [], []
+    for i, (d, k, n) in enumerate(specs):
+        ctxs.append(wd.Context(d, synth.gauge_field(d, SPREAD, 1100 + i), k, BC))
+        bs.append(torch.from_numpy(synth.spinors(d, n, 1200 + i)).cuda())
+    B = wd.Batch(ctxs)
+    res = {}
+    for g in (True, False):
+        B.solve(bs, use_graph=g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            B.solve(bs, use_graph=g)
+        torch.cuda.synchronize()
+        res["batched_graph_ms" if g else "batched_nograph_ms"] = (time.perf_counter() - t0) / 3 * 1e3
+    for c, b in zip(ctxs, bs):
+        c.solve(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        for c, b in zip(ctxs, bs):
+            c.solve(b)
+    torch.cuda.synchronize()
+    res["sequential_ms"] = (time.perf_counter() - t0) / 3 * 1e3
+    B.close()
+    for c in ctxs:
+        c.close()
+    res["workload"] = "8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16), mixed FP32/FP64 to 1e-10"
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -189,6 +271,8 @@ def main():
     ap.add_argument('--impl', choices=['wd', 'reference'], default='wd')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-fp64-compare', action='store_true')
+    ap.add_argument('--no-secondary', action='store_true', help='skip the coarse / gradient / batched measurements')
+    ap.add_argument('--coarse-only', action='store_true', help='only the tensor-core coarse stencil measurement')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)
@@ -204,6 +288,11 @@ def main():
     import synth
     import paper_2607_05157_b300 as wd
     from paper_2607_05157_b300 import api
+
+    if args.coarse_only:
+        if rank == 0:
+            print(json.dumps({"coarse_tc": coarse_measure(wd, api, torch, synth, (64, 128, 256, 512))}), flush=True)
+        return
 
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
     T = DIMS[3]
@@ -312,6 +401,11 @@ def main():
                               "speedup": 1e3 * t_fp64 / (ms / args.steps),
                               "estimate_diff_over_eps": abs(mix['total'] - ref['total']) / eps,
                               "std_error_eps": eps}
+    if rank == 0 and not args.no_secondary:
+        # secondary measurements of the other rows, outside the timed region
+        line["secondary"] = {"coarse_tc": coarse_measure(wd, api, torch, synth),
+                             "gradient": gradient_measure(wd, api, torch, synth),
+                             "batched": batched_measure(wd, torch, synth)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, dt, n = oracle_baseline(3)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
