@@ -1,6 +1,7 @@
 // C ABI entry points of libwd: context life cycle, gauge ingest (row a1),
 // D / D^dag application and solves, workspaces, profiling.
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -106,6 +107,12 @@ static int rhs_bucket(int nrhs) {
 // (input precision, output precision, RHS bucket).  Not usable during stream
 // capture: the caller must tune (one uncaptured call) before capturing.
 static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, int *R, int *th) {
+    // WD_HOP_R overrides the FP32/BF16 launch shape (R code as below, 128 threads
+    // for the plain variants), for experiments and for tests that pin a variant
+    if (pin != P64) {
+        const char *ov = getenv("WD_HOP_R");
+        if (ov && atoi(ov) > 0) { *R = atoi(ov); *th = 128; return WD_OK; }
+    }
     const int key = (pin * 4 + pout) * 8192 + rhs_bucket(A.nrhs);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) { *R = it->second.first; *th = it->second.second; return WD_OK; }
@@ -115,15 +122,21 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     cudaStreamIsCapturing(c->st, &cs);
     if (!c->autotune || cs != cudaStreamCaptureStatusNone) return WD_OK;
     // RHS tile R (1, 2, 4; +10 = software-pipelined FP32 variant) x block size
-    const int Rs[5] = {1, 2, 4, 11, 12}, Ts[3] = {64, 128, 256};
+    // (21, 22, 24 = timeslices staged through shared memory; block size fixed by the kernel)
+    const int Rs[8] = {1, 2, 4, 11, 12, 21, 22, 24}, Ts[3] = {64, 128, 256};
     cudaEvent_t e0, e1;
     WD_CUDA(cudaEventCreate(&e0));
     WD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 3; ++j) {
             if (pin == P64 && Rs[i] > 2) continue;          // FP64: plain R = 1, 2 only (R = 4 spills)
-            WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));   // warm
+            if (Rs[i] > 20 && j > 0) continue;              // staged: one block size
+            {
+                const cudaError_t e = launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st);   // warm
+                if (e == cudaErrorNotSupported) continue;    // variant does not apply to this shape
+                WD_CUDA(e);
+            }
             WD_CUDA(cudaEventRecord(e0, c->st));
             for (int k = 0; k < 3; ++k) WD_CUDA(launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st));
             WD_CUDA(cudaEventRecord(e1, c->st));
@@ -142,11 +155,25 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     return WD_OK;
 }
 
+// WD_ETIMEOUT if a staged stencil launch gave up a bounded wait since the last check
+int hop_err_check(wd_ctx *c) {
+    int h = 0;
+    WD_CUDA(cudaMemcpyAsync(&h, c->hop_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    if (h) {
+        WD_CUDA(cudaMemsetAsync(c->hop_err, 0, sizeof(int), c->st));
+        set_error("staged stencil: a bounded wait gave up");
+        return WD_ETIMEOUT;
+    }
+    return WD_OK;
+}
+
 int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const void *w, double a, double b,
         int nrhs, bool dag, const void *w2, double cc) {
     if (nrhs <= 0) return WD_OK;
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
+    A.err = c->hop_err;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field
     A.gauge = gauge_parity(c, pin, p);
@@ -263,6 +290,13 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->last_n2 = 0;
     for (int p = 0; p < 3; ++p) { c->hop_R[p] = p == P64 ? 1 : 2; c->hop_threads[p] = 128; c->gauge[p] = nullptr; }
     c->autotune = getenv("WD_NO_AUTOTUNE") == nullptr;
+    c->hop_err = nullptr;
+    if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("wd_create: allocation failed");
+        wd_destroy(c);
+        return WD_ENOMEM;
+    }
     const size_t nl = (size_t)2 * 8 * 9 * c->g.Vh;
     const size_t eb[3] = {16, 8, 4};
     for (int p = 0; p < 3; ++p) {
@@ -292,6 +326,7 @@ extern "C" int wd_destroy(wd_ctx *c) {
     cudaStreamSynchronize(c->st);
     wd_mg_free(c);
     for (int p = 0; p < 3; ++p) if (c->gauge[p]) cudaFree(c->gauge[p]);
+    if (c->hop_err) cudaFree(c->hop_err);
     for (auto &b : c->bufs) cudaFree(b.second.first);
     for (auto &b : c->hbufs) cudaFreeHost(b.second.first);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

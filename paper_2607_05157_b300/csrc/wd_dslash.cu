@@ -428,11 +428,239 @@ template cudaError_t launch_hop_batched<float, float, float, float>(HopBatch, in
 template cudaError_t launch_hop_batched<bf16, bf16, bf16, bf16>(HopBatch, int, cudaStream_t);
 template cudaError_t launch_hop_batched<bf16, float, bf16, bf16>(HopBatch, int, cudaStream_t);
 
+// ---- staged variant: timeslices through shared memory by bulk async copies ----
+// For many right-hand sides on lattices with small timeslices.  A CTA walks a
+// column of consecutive timeslices t in [ta, tb) for one group of R RHS; a ring
+// of 4 shared-memory slots holds the input (other parity) timeslices t-1, t,
+// t+1 and the prefetched t+2, each brought in by cp.async.bulk (TMA, 1D) on an
+// mbarrier.  All 8 neighbour spinors come from shared memory; every input
+// spinor of the column is read from global memory once; the loads in flight
+// cost no registers.  Links and the epilogue addends are read from global.
+static constexpr int ST_SLOTS = 4;
+static constexpr long ST_SPIN = 1L << 24;
+
+__device__ __forceinline__ uint32_t st_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool st_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = st_u32(bar);
+    for (long i = 0; i < ST_SPIN; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (i > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+// Bulk copies of input timeslice u (unwrapped; slot (u - ta + 1) & 3) for the nr
+// RHS of the group: NCH rows of Sl 16-byte chunks per RHS.  Thread 0 only.
+template <int NCH>
+__device__ __forceinline__ void st_issue(unsigned char *smem, size_t slot_bytes, uint64_t *full, int *loads,
+                                         const uint4 *in, long Vh, int Sl, int T, int ta, int u, int r0, int nr) {
+    const int q = (u - ta + 1) & 3;
+    const int tt = ((u % T) + T) % T;
+    const uint32_t bytes = (uint32_t)nr * NCH * Sl * 16;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(st_u32(&full[q])), "r"(bytes) : "memory");
+    for (int r = 0; r < nr; ++r)
+        for (int k = 0; k < NCH; ++k) {
+            unsigned char *dst = smem + q * slot_bytes + (size_t)(r * NCH + k) * Sl * 16;
+            const uint4 *src = in + ((size_t)(r0 + r) * NCH + k) * Vh + (size_t)tt * Sl;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(st_u32(dst)), "l"((uint64_t)src), "r"((uint32_t)Sl * 16), "r"(st_u32(&full[q]))
+                         : "memory");
+        }
+    loads[q] += 1;
+}
+
+// one site's 12 complex components from a shared-memory slice [k][Sl] of 16-byte chunks
+template <typename S> __device__ __forceinline__ void load_smem_f2(const unsigned char *p, int Sl, int o, float2 v[12]);
+template <> __device__ __forceinline__ void load_smem_f2<float>(const unsigned char *p, int Sl, int o, float2 v[12]) {
+    const float4 *q = (const float4 *)p + o;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 a = q[k * Sl];
+        v[2 * k] = f2(a.x, a.y);
+        v[2 * k + 1] = f2(a.z, a.w);
+    }
+}
+template <> __device__ __forceinline__ void load_smem_f2<bf16>(const unsigned char *p, int Sl, int o, float2 v[12]) {
+    const uint4 *q = (const uint4 *)p + o;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 a = q[k * Sl];
+        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&a;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[4 * k + j] = __bfloat1622float2(h[j]);
+    }
+}
+
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG>
+__global__ void __launch_bounds__(256, 1) hop_staged_f2(HopArgs A, int tlen) {
+    constexpr int NCH = SIO<SIn>::NCH;
+    const Geom &g = A.g;
+    const long Vh = g.Vh;
+    const int T = g.T, Sl = g.Vh / g.T;
+    const int rg = blockIdx.x % A.nrb, tcol = blockIdx.x / A.nrb;
+    const int ta = tcol * tlen, tb = min(ta + tlen, T);
+    const int r0 = rg * R, nr = min(R, A.nrhs - r0);
+    const size_t slot_bytes = (size_t)R * NCH * Sl * 16;
+    extern __shared__ __align__(128) unsigned char st_smem[];
+    uint64_t *full = (uint64_t *)(st_smem + ST_SLOTS * slot_bytes);
+    __shared__ int s_fail;
+    __shared__ int s_loads[ST_SLOTS];
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < ST_SLOTS; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(st_u32(&full[q])));
+            s_loads[q] = 0;
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int u = ta - 1; u <= min(ta + 2, tb); ++u)
+            st_issue<NCH>(st_smem, slot_bytes, full, s_loads, (const uint4 *)A.in, Vh, Sl, T, ta, u, r0, nr);
+    for (int t = ta; t < tb; ++t) {
+        // slices t-1, t, t+1 must have landed
+        bool ok = true;
+        for (int u = t - 1; u <= t + 1; ++u)
+            ok = ok && st_wait(&full[(u - ta + 1) & 3], ((u - ta + 1) >> 2) & 1);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const unsigned char *sm = st_smem + ((t - 1 - ta + 1) & 3) * slot_bytes;
+        const unsigned char *s0 = st_smem + ((t - ta + 1) & 3) * slot_bytes;
+        const unsigned char *sp = st_smem + ((t + 1 - ta + 1) & 3) * slot_bytes;
+        for (int so = threadIdx.x; so < Sl; so += blockDim.x) {
+            const int s = t * Sl + so;
+            int x, y, z, tt;
+            eo_coords(g, A.p, s, x, y, z, tt);
+            const int xp = x + 1 == g.X ? 0 : x + 1, xm = x == 0 ? g.X - 1 : x - 1;
+            const int yp = y + 1 == g.Y ? 0 : y + 1, ym = y == 0 ? g.Y - 1 : y - 1;
+            const int zp = z + 1 == g.Z ? 0 : z + 1, zm = z == 0 ? g.Z - 1 : z - 1;
+            const int base = t * Sl;
+            const int onb[8] = {eo_index(g, xp, y, z, t) - base, eo_index(g, x, yp, z, t) - base,
+                                eo_index(g, x, y, zp, t) - base, eo_index(g, x, y, z, 0),
+                                eo_index(g, xm, y, z, t) - base, eo_index(g, x, ym, z, t) - base,
+                                eo_index(g, x, y, zm, t) - base, eo_index(g, x, y, z, 0)};
+            float2 acc[R][12];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < 12; ++k) acc[r][k] = f2(0.f, 0.f);
+#define WD_ST_DIR(D, SLOT)                                                                         \
+            {                                                                                      \
+                cx<float> u[9];                                                                    \
+                LIO<G>::load((const char *)A.gauge + (size_t)(D) * 9 * Vh * LIO<G>::ELEM, Vh, s, u); \
+                float2 psi[R][12];                                                                 \
+                _Pragma("unroll") for (int r = 0; r < R; ++r)                                      \
+                    if (r < nr) load_smem_f2<SIn>((SLOT) + (size_t)r * NCH * Sl * 16, Sl, onb[D], psi[r]); \
+                compute_dir_f2<R, D, DAG>(A, rg, u, psi, acc);                                     \
+                asm volatile("" ::: "memory");                                                     \
+            }
+            WD_ST_DIR(0, s0) WD_ST_DIR(1, s0) WD_ST_DIR(2, s0) WD_ST_DIR(3, sp)
+            WD_ST_DIR(4, s0) WD_ST_DIR(5, s0) WD_ST_DIR(6, s0) WD_ST_DIR(7, sm)
+#undef WD_ST_DIR
+            constexpr int NO = SIO<SOut>::NCH, NW = SIO<SW>::NCH;
+            const float2 a2 = f2((float)A.a, (float)A.a), b2 = f2((float)A.b, (float)A.b), c2 = f2((float)A.c, (float)A.c);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r >= nr) break;
+                const int rhs = r0 + r;
+                float2 o[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[k] = __fmul2_rn(b2, acc[r][k]);
+                if (A.w) {
+                    float2 wv[12];
+                    load_f2<SW>((const uint4 *)A.w + (size_t)rhs * NW * Vh, Vh, s, wv);
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(a2, wv[k], o[k]);
+                }
+                if (A.w2) {
+                    float2 wv[12];
+                    load_f2<SW>((const uint4 *)A.w2 + (size_t)rhs * NW * Vh, Vh, s, wv);
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(c2, wv[k], o[k]);
+                }
+                cx<float> oc[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) oc[k] = cmake(o[k].x, o[k].y);
+                SIO<SOut>::store((uint4 *)A.out + (size_t)rhs * NO * Vh, Vh, s, oc);
+            }
+        }
+        // every thread is done with slot(t-1): order its reads before the async refill
+        __syncthreads();
+        if (threadIdx.x == 0 && t + 3 <= tb) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            st_issue<NCH>(st_smem, slot_bytes, full, s_loads, (const uint4 *)A.in, Vh, Sl, T, ta, t + 3, r0, nr);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) {
+        if (A.err) atomicExch(A.err, 1);
+        // copies already issued must land before the shared memory is released
+        for (int q = 0; q < ST_SLOTS; ++q)
+            if (s_loads[q] > 0) st_wait(&full[q], (s_loads[q] - 1) & 1);
+    }
+}
+
+size_t hop_staged_smem(const HopArgs &A, int R, int nch) {
+    if (A.g.Vh % A.g.T) return 0;
+    return (size_t)ST_SLOTS * R * nch * (A.g.Vh / A.g.T) * 16 + ST_SLOTS * 8;
+}
+
+template <typename SIn, typename SOut, typename SW, typename G>
+cudaError_t launch_hop_staged(const HopArgs &A0, int R, bool dag, cudaStream_t st) {
+    if constexpr (std::is_same<typename RealOf<SIn>::type, double>::value) {
+        return cudaErrorNotSupported;
+    } else {
+        HopArgs A = A0;
+        if (A.nrhs <= 0) return cudaSuccess;
+        if (R != 1 && R != 2 && R != 4) return cudaErrorNotSupported;
+        const size_t smem = hop_staged_smem(A, R, SIO<SIn>::NCH);
+        if (smem == 0 || smem > 200 * 1024 || A.g.T < 2) return cudaErrorNotSupported;
+        A.nrb = (A.nrhs + R - 1) / R;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+        const int target = sms * per_sm * 2;
+        int ncolt = (target + A.nrb - 1) / A.nrb;
+        if (ncolt > A.g.T) ncolt = A.g.T;
+        if (ncolt < 1) ncolt = 1;
+        const int tlen = (A.g.T + ncolt - 1) / ncolt;
+        ncolt = (A.g.T + tlen - 1) / tlen;
+        const unsigned grid = (unsigned)(A.nrb * ncolt);
+        const int Sl = A.g.Vh / A.g.T;
+        const int th = Sl >= 256 ? 256 : ((Sl + 31) / 32) * 32;
+#define WD_ST_CASE(RR)                                                                                   \
+        if (R == RR) {                                                                                   \
+            if (dag) {                                                                                   \
+                cudaFuncSetAttribute(hop_staged_f2<SIn, SOut, SW, G, RR, true>,                          \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+                hop_staged_f2<SIn, SOut, SW, G, RR, true><<<grid, th, smem, st>>>(A, tlen);              \
+            } else {                                                                                     \
+                cudaFuncSetAttribute(hop_staged_f2<SIn, SOut, SW, G, RR, false>,                         \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+                hop_staged_f2<SIn, SOut, SW, G, RR, false><<<grid, th, smem, st>>>(A, tlen);             \
+            }                                                                                            \
+        }
+        WD_ST_CASE(1) WD_ST_CASE(2) WD_ST_CASE(4)
+#undef WD_ST_CASE
+        return cudaGetLastError();
+    }
+}
+
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStream_t st) {
     HopArgs A = A0;
     if (A.nrhs <= 0) return cudaSuccess;
-    // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined (FP32 arithmetic only)
+    // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined; R = 21, 22, 24:
+    // timeslices staged through shared memory (FP32 arithmetic only)
+    if (R > 20) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
     const bool pipe = R > 10;
     if (pipe) R -= 10;
     if (R != 1 && R != 2 && R != 4) R = 1;

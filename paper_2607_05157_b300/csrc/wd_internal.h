@@ -36,6 +36,7 @@ struct HopArgs {
     int p;                 // output parity
     int nrhs, nrb;
     Geom g;
+    int *err;              // error flag of the staged variant (bounded waits); set by hop()
 };
 
 template <typename SIn, typename SOut, typename SW, typename G>
@@ -102,6 +103,7 @@ struct wd_ctx {
     int hop_R[3];                   // default RHS tile per input precision
     int hop_threads[3];
     bool autotune;                  // time the stencil launch shapes on first use
+    int *hop_err;                   // device flag: a staged stencil wait gave up
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
     std::vector<double> last_level2;    // [n2][T][2]
@@ -120,6 +122,8 @@ void prof_end(wd_ctx *c, int slot);
 // for inner precision prec; SIn is the input storage, SOut the output storage.
 int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, const void *w,
         double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0);
+
+int hop_err_check(wd_ctx *c);
 
 // layout conversions between the user layout and the eo layout
 int user_to_eo(wd_ctx *c, const void *user, bool user_double, int prec, void *even, void *odd, int nrhs);

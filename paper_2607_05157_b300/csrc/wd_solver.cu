@@ -238,6 +238,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
             if (!(res <= tol * 1.0000001) && status == WD_OK) status = isfinite(res) ? WD_ENOCONV : WD_EBREAKDOWN;
         }
     }
+    WD_TRY(hop_err_check(c));
     if (iters_out)
         for (int r = 0; r < nrhs; ++r) iters_out[r] = iters[r];
     if (status != WD_OK) set_error("solve: %s", status == WD_ENOCONV ? "not converged within max_iter" : "breakdown");
