@@ -186,6 +186,8 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     int slot;
     prof_begin(c, pin == P64 ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
     cudaError_t e = launch_hop_any(pin, pout, A, R, dag, th, c->st);
+    if (e == cudaErrorNotSupported)   // an overridden variant that does not fit this shape
+        e = launch_hop_any(pin, pout, A, c->hop_R[pin], dag, c->hop_threads[pin], c->st);
     prof_end(c, slot);
     c->launches++;
     if (e != cudaSuccess) { set_error("hop launch: %s", cudaGetErrorString(e)); return WD_ECUDA; }
