@@ -6,10 +6,12 @@ lattice (antiperiodic in t), kappa = 0.125, synthetic SU(3) links
 (Gram-Schmidt projection of I + 0.5 G, seed 1002) standing in for the paper's
 RQCD ensemble; per step and per GPU 256 right-hand sides = 16 Rademacher
 samples x 16 timeslices (time dilution), estimating the disconnected loop
-O(t) = tr[g5 D^{-1}(t,t)] (Eq. 21), each solve to a true FP64 relative
-residual of 1e-10 by FP32 (or BF16) BiCGStab inside FP64 defect correction.
+O(t) = tr[g5 D^{-1}(t,t)] (Eq. 21), plus the pseudoscalar correlator
+C(t) = sum_x |D^{-1}(x,t;0,0)|^2 from 12 point sources, each solve to a true
+FP64 relative residual of 1e-10 by FP32 (or BF16) BiCGStab inside FP64 defect
+correction.
 
-A step = one trace_estimate call: RHS generation on the device, even-odd
+A step = one trace_estimate call plus one wd_point_correlator call: RHS generation on the device, even-odd
 source, 256-RHS batched mixed-precision solve (stencil, BLAS-1, FP64 residual),
 odd-site reconstruction, FP64 per-timeslice contraction, mean and sample
 variance.  `value` = algorithmic stencil bytes moved by all stencil launches
@@ -45,7 +47,8 @@ SAMPLES = 16
 TOL = 1e-10
 BC = (1, 1, 1, -1)
 METRIC = "Dslash GB/s (% HBM peak); trace time at fixed error, mixed+batched vs FP64"
-WORKLOAD = "8^3x16 Wilson-Dirac, kappa 0.125, 256 time-diluted Rademacher RHS, tr[g5 D^-1(t,t)] to 1e-10"
+WORKLOAD = ("8^3x16 Wilson-Dirac, kappa 0.125, 256 time-diluted Rademacher RHS for tr[g5 D^-1(t,t)] + "
+            "12 point sources for C(t), solves to 1e-10")
 
 
 def env_rank():
@@ -300,9 +303,15 @@ def main():
     ctx = wd.Context(DIMS, gauge, KAPPA, BC)
     seed0 = NOISE_SEED + 7919 * rank
 
-    def step(i, p=prec, batch=SAMPLES * T):
+    def trace_only(i, p=prec, batch=SAMPLES * T):
         return api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, SAMPLES, T, seed=seed0 + i, op=1,
                                   prec=p, batch=batch, tol=TOL)
+
+    def step(i, p=prec, batch=SAMPLES * T):
+        # the whole workload: 256 time-diluted RHS for O(t) and 12 point sources for C(t)
+        r = trace_only(i, p, batch)
+        r['C'] = api.wd_point_correlator(ctx.h, (0, 0, 0, 0), T, prec=p, tol=TOL)
+        return r
 
     for i in range(args.warmup):
         step(i)
@@ -378,21 +387,21 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64" if args.prec == 'fp32' else "bf16+f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "kappa": KAPPA,
-                       "rhs_per_step_per_gpu": SAMPLES * T, "inner_precision": args.prec,
+                       "rhs_per_step_per_gpu": SAMPLES * T + 12, "inner_precision": args.prec,
                        "l2": "inputs larger than L2 (each stencil launch streams >100 MB)",
                        "parallelism": f"replicas x{world} (independent samples)"},
             "roofline": roof, "clocks": clk.summary(),
             "e2e": {"value": e_bytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps},
             "gpu_launches": launches,
-            "solves_per_step": results[-1]['n_solves']}
+            "solves_per_step": results[-1]["n_solves"] + 12}
 
     if rank == 0 and not args.no_fp64_compare:
         # trace time at fixed error: same noise (so the same estimate and error)
         # through the plain FP64 single-RHS path
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ref = step(1000, p=wd.WD_FP64, batch=1)
+        ref = trace_only(1000, p=wd.WD_FP64, batch=1)
         torch.cuda.synchronize()
         t_fp64 = time.perf_counter() - t0
         mix = results[0]

@@ -125,6 +125,14 @@ int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, 
                    int op, int prec, int batch, double tol, double *estimate, double *sample_var,
                    int64_t *n_solves_out, double *samples_out);
 
+/* Pseudoscalar correlator from point sources: C(t) = sum_{x in t} sum over the
+ * 12 x 12 spin-colour entries |D^{-1}(x; x0)|^2, from the 12 columns of D^{-1}
+ * with the source at site x0 = src[4] (x, y, z, t), solved as 12 RHS with the
+ * precision / tolerance semantics of wd_solve.  C: host [T], absolute
+ * timeslice index.  The connected observable of Sec. 4 at one source, without
+ * the multilevel splitting. */
+int wd_point_correlator(wd_ctx *ctx, const int src[4], int prec, double tol, double *C);
+
 /* Per-sample level values of the last WD_MLMC2 estimate: level 2 samples
  * [n2][T][2] (host). */
 int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);

@@ -44,6 +44,7 @@ _SIGS = {
     'trace_estimate': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int, c_int,
                                c_double, c_void_p, c_void_p, P(c_int64), c_void_p]),
     'wd_mlmc_level2_samples': (c_int, [c_void_p, c_void_p, c_int]),
+    'wd_point_correlator': (c_int, [c_void_p, P(c_int), c_int, c_double, c_void_p]),
     'wd_last_error': (ctypes.c_char_p, []),
     'wd_mg_setup': (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_uint64]),
     'wd_coarse_apply': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),

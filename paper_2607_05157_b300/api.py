@@ -108,6 +108,13 @@ def trace_estimate(h, method, dilution, N, T, n2=0, d=0, seed=0, op=1, prec=WD_M
     return out
 
 
+def wd_point_correlator(h, src, T, prec=WD_MIXED_FP32, tol=1e-10):
+    """C(t) (numpy, length T) from 12 point sources at site src = (x, y, z, t)."""
+    C = np.zeros(T, np.float64)
+    check(lib.wd_point_correlator(h, _iarr(src), int(prec), float(tol), _host_ptr(C)), 'wd_point_correlator')
+    return C
+
+
 def wd_mlmc_level2_samples(h, n2, T):
     smp = np.zeros((n2, T, 2), np.float64)
     check(lib.wd_mlmc_level2_samples(h, _host_ptr(smp), int(n2)), 'wd_mlmc_level2_samples')
