@@ -183,15 +183,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512)):
+def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 48)):
     """Row a8: tcgen05 coarse 9-point block stencil on the 24^3x48 two-level
     workload (4^4 aggregates, 24 test vectors -> 48x48 blocks, 2592 coarse
     sites), CUDA-event times of the kernel, algorithmic TFLOP/s (8 ncd^2 per
     block, 9 blocks per site and RHS) and block-stream GB/s."""
-    dims = (24, 24, 24, 48)
     ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
     api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=0, seed=3)
-    Vc, ncd = 6 * 6 * 6 * 12, 48
+    Vc, ncd = (dims[0] // 4) * (dims[1] // 4) * (dims[2] // 4) * (dims[3] // 4), 48
     out = []
     for nrhs in rhs_list:
         x = torch.randn((nrhs, Vc, ncd), dtype=torch.complex128, device='cuda')
@@ -210,7 +209,7 @@ def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512)):
                     "block_stream_GB_s": wbytes / (per * 1e-3) / 1e9})
     ctx.close()
     peaks = measured_peaks()
-    return {"workload": "24^3x48, 4^4 aggregates, nv=24 (48x48 blocks), BF16 tcgen05, FP32 accumulate",
+    return {"workload": "x".join(map(str, dims)) + ", 4^4 aggregates, nv=24 (48x48 blocks), BF16 tcgen05, FP32 accumulate",
             "bf16_peak_TFLOP_s": peaks['bf16_tflops'] if peaks else 1800.0, "points": out}
 
 
@@ -276,6 +275,8 @@ def main():
     ap.add_argument('--no-fp64-compare', action='store_true')
     ap.add_argument('--no-secondary', action='store_true', help='skip the coarse / gradient / batched measurements')
     ap.add_argument('--coarse-only', action='store_true', help='only the tensor-core coarse stencil measurement')
+    ap.add_argument('--coarse-lattice', default='24,24,24,48', help='fine lattice of --coarse-only (X,Y,Z,T)')
+    ap.add_argument('--coarse-rhs', default='64,128,256,512', help='RHS counts of --coarse-only')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)
@@ -294,7 +295,9 @@ def main():
 
     if args.coarse_only:
         if rank == 0:
-            print(json.dumps({"coarse_tc": coarse_measure(wd, api, torch, synth, (64, 128, 256, 512))}), flush=True)
+            cd = tuple(int(v) for v in args.coarse_lattice.split(','))
+            cr = tuple(int(v) for v in args.coarse_rhs.split(','))
+            print(json.dumps({"coarse_tc": coarse_measure(wd, api, torch, synth, cr, cd)}), flush=True)
         return
 
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
