@@ -107,11 +107,16 @@ static int rhs_bucket(int nrhs) {
 // (input precision, output precision, RHS bucket).  Not usable during stream
 // capture: the caller must tune (one uncaptured call) before capturing.
 static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, int *R, int *th) {
-    // WD_HOP_R overrides the FP32/BF16 launch shape (R code as below, 128 threads
-    // for the plain variants), for experiments and for tests that pin a variant
+    // WD_HOP_R = "R" or "R:threads" overrides the FP32/BF16 launch shape (R code as
+    // below; 128 threads unless given), for experiments, profiling and tests
     if (pin != P64) {
         const char *ov = getenv("WD_HOP_R");
-        if (ov && atoi(ov) > 0) { *R = atoi(ov); *th = 128; return WD_OK; }
+        if (ov && atoi(ov) > 0) {
+            *R = atoi(ov);
+            const char *colon = strchr(ov, ':');
+            *th = colon && atoi(colon + 1) > 0 ? atoi(colon + 1) : 128;
+            return WD_OK;
+        }
     }
     const int key = (pin * 4 + pout) * 8192 + rhs_bucket(A.nrhs);
     auto it = c->tuned.find(key);
