@@ -116,7 +116,8 @@ def hop_traffic(prec):
     taken on the current stencil source (else None)."""
     try:
         rec = json.load(open(os.path.join(ROOT, 'profiles', 'hop_traffic.json')))
-        src = open(os.path.join(ROOT, 'paper_2607_05157_b300', 'csrc', 'wd_dslash.cu'), 'rb').read()
+        csrc = os.path.join(ROOT, 'paper_2607_05157_b300', 'csrc')
+        src = b''.join(open(os.path.join(csrc, f), 'rb').read() for f in ('wd_dslash.cu', 'wd_spin.cuh'))
         if rec.get('source_sha256') != hashlib.sha256(src).hexdigest():
             return None
         return rec.get(prec, {}).get('dram_bytes_per_launch')
@@ -381,7 +382,9 @@ def main():
                       f"{by_hop / max(n_hop, 1) / 1e6:.1f} MB algorithmic per launch)",
             "peak_source": "measured" if peaks else "fallback",
             "share_of_step": ms_hop / ms if ms else None,
-            "fp64_stencil": {"launches_per_step": n_h64 // max(args.steps, 1),
+            "fp64_stencil": {"arithmetic": "fp64" if os.environ.get('WD_DD') == '0' else
+                             "double-float (FP32 pairs, FP64 fields)",
+                             "launches_per_step": n_h64 // max(args.steps, 1),
                              "GB_s": (by_h64 / (ms_h64 * 1e-3) / 1e9) if ms_h64 else None,
                              "share_of_step": ms_h64 / ms if ms else None}}
 

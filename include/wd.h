@@ -59,7 +59,8 @@ typedef enum {
 typedef enum {
     WD_FP64 = 0,         /* FP64 storage and arithmetic throughout */
     WD_MIXED_FP32 = 1,   /* FP32 inner Krylov solve inside FP64 defect correction */
-    WD_MIXED_BF16 = 2    /* BF16 storage, FP32 arithmetic inner solve, FP64 outer */
+    WD_MIXED_BF16 = 2,   /* BF16 storage, FP32 arithmetic inner solve, FP64 outer */
+    WD_FP64_DD = 3       /* wd_apply only: FP64 fields, double-float arithmetic */
 } wd_prec;
 
 /* trace_estimate methods */
@@ -81,14 +82,20 @@ int wd_destroy(wd_ctx *ctx);
 /* y = D x (dagger = 0) or D^dag x (dagger = 1) on nrhs fields (Sec. 1).
  * in/out: device, complex128 for WD_FP64, complex64 for WD_MIXED_FP32
  * (then the stencil runs in FP32); WD_MIXED_BF16 takes complex64 fields,
- * rounds them and the links to BF16 and accumulates in FP32. */
+ * rounds them and the links to BF16 and accumulates in FP32.  WD_FP64_DD
+ * takes complex128 fields and computes with pairs of FP32 numbers
+ * (double-float: error-free products and sums), agreeing with WD_FP64 to about
+ * 2^-44 normwise; inputs below 2^-103 in magnitude count as zero.  It is the
+ * stencil of the FP64 steps of the mixed-precision solves. */
 int wd_apply(wd_ctx *ctx, const void *in, void *out, int nrhs, int prec, int dagger);
 
 /* x = D^{-1} b for nrhs right-hand sides (the D^{-1} eta products of Sec. 1),
  * even-odd preconditioned BiCGStab.  rhs, x: device complex128.  prec selects
- * the inner arithmetic; for the mixed modes the outer loop is FP64 defect
- * correction, so tol (relative FP64 residual ||b - D x|| / ||b|| per RHS) can be
- * 1e-10 or below.  iters_out[nrhs] (host, nullable): inner iterations summed
+ * the inner arithmetic (WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16); for the mixed
+ * modes the outer loop is defect correction on FP64 fields whose stencil steps
+ * (source, residuals, odd-site reconstruction) use WD_FP64_DD arithmetic, so
+ * tol (relative residual ||b - D x|| / ||b|| per RHS) can be 1e-10 or below;
+ * a tol under 1e-12 runs those steps in FP64 arithmetic instead.  iters_out[nrhs] (host, nullable): inner iterations summed
  * over outer steps; true_resid_out[nrhs] (host, nullable): final FP64 relative
  * residual.  Returns WD_ENOCONV if some RHS missed tol within max_iter inner
  * iterations (x still holds the best iterate). */
@@ -222,7 +229,8 @@ int wd_batch_solve(wd_batch *b, const double *const *rhs, double *const *x, cons
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* The paper has no counterpart to this entry point.
- * Same result as wd_apply (same arguments, same layouts and precisions), but
+ * Same result as wd_apply (same arguments, same layouts; precisions WD_FP64,
+ * WD_MIXED_FP32 and WD_MIXED_BF16), but
  * the call allocates no memory: for callers that cannot allocate device memory
  * while running -- services that reserve their whole device-memory budget at
  * start-up, and frameworks whose caching allocator must own every byte of

@@ -6,7 +6,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, 'libwd.so')
 
 WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA, WD_ENOCONV, WD_EBREAKDOWN, WD_ETIMEOUT, WD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16 = 0, 1, 2
+WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16, WD_FP64_DD = 0, 1, 2, 3
 WD_HUTCH, WD_PROBE, WD_MLMC2 = 0, 1, 2
 WD_TR_DINV, WD_TR_G5_DINV = 0, 1
 WD_DIL_TIME = 0x100

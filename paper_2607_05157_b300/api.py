@@ -8,7 +8,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import lib, check, WD_OK, WD_ENOCONV, WD_EBREAKDOWN, WD_FP64, WD_MIXED_FP32, WDError
+from ._lib import lib, check, WD_OK, WD_ENOCONV, WD_EBREAKDOWN, WD_FP64, WD_MIXED_FP32, WD_FP64_DD, WDError
 
 _ci = ctypes.c_int
 
@@ -61,7 +61,7 @@ def wd_update_gauge(h, gauge, kappa):
 
 def wd_apply(h, x, out, prec=WD_FP64, dagger=False):
     import torch
-    dt = torch.complex128 if prec == WD_FP64 else torch.complex64
+    dt = torch.complex128 if prec in (WD_FP64, WD_FP64_DD) else torch.complex64
     check(lib.wd_apply(h, _dev_ptr(x, dt, 'in'), _dev_ptr(out, dt, 'out'), x.shape[0], int(prec), int(bool(dagger))),
           'wd_apply')
     return out

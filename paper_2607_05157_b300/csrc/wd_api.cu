@@ -90,6 +90,7 @@ static const void *gauge_parity(wd_ctx *c, int prec, int p) {
 }
 
 static cudaError_t launch_hop_any(int pin, int pout, const HopArgs &A, int R, bool dag, int th, cudaStream_t st) {
+    if (pin == PDD) return launch_hop_dd(A, R, dag, th, st);
     if (pin == P64) return launch_hop<double, double, double, double>(A, R, dag, th, st);
     if (pin == P32) return launch_hop<float, float, float, float>(A, R, dag, th, st);
     if (pout == P16) return launch_hop<bf16, bf16, bf16, bf16>(A, R, dag, th, st);
@@ -135,7 +136,8 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     float best = 1e30f;
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 3; ++j) {
-            if (pin == P64 && Rs[i] > 2) continue;          // FP64: plain R = 1, 2 only (R = 4 spills)
+            if ((pin == P64 || pin == PDD) && Rs[i] > 2) continue;   // FP64 fields: R = 1, 2 only (R = 4 spills)
+            if (pin == PDD && Ts[j] > 128) continue;                 // double-float: at most 128 threads
             if (Rs[i] > 20 && j > 0) continue;              // staged: one block size
             {
                 const cudaError_t e = launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st);   // warm
@@ -180,8 +182,13 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
-    // links in the precision of the input field
-    A.gauge = gauge_parity(c, pin, p);
+    // links in the precision of the input field; double-float: FP32 copy + remainder
+    if (pin == PDD) {
+        A.gauge = gauge_parity(c, P32, p);
+        A.gauge_lo = (const char *)c->gauge_lo + (size_t)p * 8 * 9 * c->g.Vh * sizeof(float2);
+    } else {
+        A.gauge = gauge_parity(c, pin, p);
+    }
     int R, th;
     WD_TRY(tune_hop(c, pin, pout, A, dag, &R, &th));
     // algorithmic bytes: nrhs x (in + out [+ w + w2]) spinors + 8 links per output site
@@ -189,7 +196,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     const double bytes = (double)c->g.Vh *
                          (nrhs * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
-    prof_begin(c, pin == P64 ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
+    prof_begin(c, pin == P64 || pin == PDD ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
     cudaError_t e = launch_hop_any(pin, pout, A, R, dag, th, c->st);
     if (e == cudaErrorNotSupported)   // an overridden variant that does not fit this shape
         e = launch_hop_any(pin, pout, A, c->hop_R[pin], dag, c->hop_threads[pin], c->st);
@@ -213,6 +220,15 @@ template <> struct LStore<float> {
 template <> struct LStore<bf16> {
     __device__ static void put(void *base, long idx, double re, double im) {
         ((__nv_bfloat162 *)base)[idx] = __floats2bfloat162_rn((float)re, (float)im);
+    }
+};
+
+// FP32 remainder of an FP64 link: U - (float)U, the low half of the
+// double-float links (the high half is the FP32 copy)
+struct LoTag {};
+template <> struct LStore<LoTag> {
+    __device__ static void put(void *base, long idx, double re, double im) {
+        ((float2 *)base)[idx] = make_float2((float)(re - (double)(float)re), (float)(im - (double)(float)im));
     }
 };
 
@@ -262,7 +278,8 @@ static int ingest_gauge(wd_ctx *c, const double *gauge_host) {
     k_gauge_eo<double><<<blocks, 128, 0, c->st>>>(dU, c->gauge[P64], c->g, bc);
     k_gauge_eo<float><<<blocks, 128, 0, c->st>>>(dU, c->gauge[P32], c->g, bc);
     k_gauge_eo<bf16><<<blocks, 128, 0, c->st>>>(dU, c->gauge[P16], c->g, bc);
-    c->launches += 3;
+    k_gauge_eo<LoTag><<<blocks, 128, 0, c->st>>>(dU, c->gauge_lo, c->g, bc);
+    c->launches += 4;
     WD_CUDA(cudaGetLastError());
     WD_CUDA(cudaStreamSynchronize(c->st));
     return WD_OK;
@@ -295,7 +312,13 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->prof = false;
     c->mg = nullptr;
     c->last_n2 = 0;
-    for (int p = 0; p < 3; ++p) { c->hop_R[p] = p == P64 ? 1 : 2; c->hop_threads[p] = 128; c->gauge[p] = nullptr; }
+    for (int p = 0; p < 4; ++p) { c->hop_R[p] = p == P64 || p == PDD ? 1 : 2; c->hop_threads[p] = 128; }
+    for (int p = 0; p < 3; ++p) c->gauge[p] = nullptr;
+    c->gauge_lo = nullptr;
+    {
+        const char *e = getenv("WD_DD");
+        c->outer = e && atoi(e) == 0 ? P64 : PDD;
+    }
     c->autotune = getenv("WD_NO_AUTOTUNE") == nullptr;
     c->hop_err = nullptr;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
@@ -313,6 +336,12 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
             wd_destroy(c);
             return WD_ENOMEM;
         }
+    }
+    if (cudaMalloc(&c->gauge_lo, nl * 8) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("wd_create: link allocation failed");
+        wd_destroy(c);
+        return WD_ENOMEM;
     }
     int s = ingest_gauge(c, gauge);
     if (s != WD_OK) { wd_destroy(c); return s; }
@@ -333,6 +362,7 @@ extern "C" int wd_destroy(wd_ctx *c) {
     cudaStreamSynchronize(c->st);
     wd_mg_free(c);
     for (int p = 0; p < 3; ++p) if (c->gauge[p]) cudaFree(c->gauge[p]);
+    if (c->gauge_lo) cudaFree(c->gauge_lo);
     if (c->hop_err) cudaFree(c->hop_err);
     for (auto &b : c->bufs) cudaFree(b.second.first);
     for (auto &b : c->hbufs) cudaFreeHost(b.second.first);
@@ -344,23 +374,23 @@ extern "C" int wd_destroy(wd_ctx *c) {
 
 extern "C" int wd_apply(wd_ctx *c, const void *in, void *out, int nrhs, int prec, int dagger) {
     if (!c || (!in && nrhs > 0) || (!out && nrhs > 0) || nrhs < 0) { set_error("wd_apply: bad argument"); return WD_EINVAL; }
-    if (prec < 0 || prec > 2) { set_error("wd_apply: bad precision %d", prec); return WD_EINVAL; }
+    if (prec < 0 || prec > 3) { set_error("wd_apply: bad precision %d", prec); return WD_EINVAL; }
     if (nrhs == 0) return WD_OK;
-    const int pf = prec;               // field storage inside the stencil
-    const int po = prec == P64 ? P64 : P32;
-    const bool udbl = prec == P64;
+    const int pf = prec;               // field storage inside the stencil (PDD: FP64 fields)
+    const int po = prec == P64 || prec == PDD ? prec : P32;
+    const bool udbl = prec == P64 || prec == PDD;
     const size_t fin = field_bytes(c->g, pf, nrhs), fout = field_bytes(c->g, po, nrhs);
     void *ie, *io, *oe, *oo;
     WD_TRY(ws_get(c, "apply.ie", fin, &ie));
     WD_TRY(ws_get(c, "apply.io", fin, &io));
     WD_TRY(ws_get(c, "apply.oe", fout, &oe));
     WD_TRY(ws_get(c, "apply.oo", fout, &oo));
-    WD_TRY(user_to_eo(c, in, udbl, pf, ie, io, nrhs));
+    WD_TRY(user_to_eo(c, in, udbl, pf == PDD ? P64 : pf, ie, io, nrhs));
     // (D x)_e = x_e - k H_eo x_o,  (D x)_o = x_o - k H_oe x_e
     const double k = c->kappa;
     WD_TRY(hop(c, pf, po, 0, oe, io, ie, 1.0, -k, nrhs, dagger != 0));
     WD_TRY(hop(c, pf, po, 1, oo, ie, io, 1.0, -k, nrhs, dagger != 0));
-    WD_TRY(eo_to_user(c, oe, oo, po, out, udbl, nrhs));
+    WD_TRY(eo_to_user(c, oe, oo, po == PDD ? P64 : po, out, udbl, nrhs));
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }

@@ -154,6 +154,8 @@ static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *
     }
     const int n = (int)b->c.size();
     const int pp = prec;
+    // stencil of the FP64 steps, as in solve_eo
+    auto outer_of = [tol](wd_ctx *cc) { return tol < 1e-12 ? (int)P64 : cc->outer; };
     std::vector<Lat> L(n);
     for (int j = 0; j < n; ++j) {
         Lat &l = L[j];
@@ -187,7 +189,7 @@ static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *
         l.last.assign(l.nrhs, 0.0);
         l.iters.assign(l.nrhs, 0);
         // b_hat = b_e + k H_eo b_o; x = 0; r = b_hat
-        WD_TRY(hop(c, P64, P64, 0, l.bhat, l.bo, l.be, 1.0, c->kappa, l.nrhs));
+        WD_TRY(hop(c, outer_of(c), outer_of(c), 0, l.bhat, l.bo, l.be, 1.0, c->kappa, l.nrhs));
         WD_TRY(blas_zero(c, l.xe, f));
         WD_CUDA(cudaMemcpyAsync(l.r64, l.bhat, f, cudaMemcpyDeviceToDevice, c->st));
     }
@@ -254,16 +256,16 @@ static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *
             for (int r = 0; r < l.nrhs; ++r) l.iters[r] += hs[r].iters;
             const Space sp = fine_space(l.c->g);
             WD_TRY(blas_axpy_mixed(l.c, sp, l.xe, P32, l.V.x, l.scale + l.nrhs, l.nrhs));
-            // r = b_hat - D_hat x in FP64
-            WD_TRY(hop(l.c, P64, P64, 1, l.tmp64, l.xe, nullptr, 0.0, 1.0, l.nrhs));
-            WD_TRY(hop(l.c, P64, P64, 0, l.r64, l.tmp64, l.bhat, 1.0, l.c->kappa * l.c->kappa, l.nrhs, false, l.xe, -1.0));
+            // r = b_hat - D_hat x on FP64 fields (double-float stencil unless WD_DD=0 or tol < 1e-12)
+            WD_TRY(hop(l.c, outer_of(l.c), outer_of(l.c), 1, l.tmp64, l.xe, nullptr, 0.0, 1.0, l.nrhs));
+            WD_TRY(hop(l.c, outer_of(l.c), outer_of(l.c), 0, l.r64, l.tmp64, l.bhat, 1.0, l.c->kappa * l.c->kappa, l.nrhs, false, l.xe, -1.0));
         }
     }
     if (exec) cudaGraphExecDestroy(exec);
     int ri = 0;
     for (int j = 0; j < n; ++j) {
         Lat &l = L[j];
-        WD_TRY(hop(l.c, P64, P64, 1, l.xo, l.xe, l.bo, 1.0, l.c->kappa, l.nrhs));
+        WD_TRY(hop(l.c, outer_of(l.c), outer_of(l.c), 1, l.xo, l.xe, l.bo, 1.0, l.c->kappa, l.nrhs));
         WD_TRY(eo_to_user(l.c, l.xe, l.xo, P64, x[j], true, l.nrhs));
         int mx = 0;
         for (int r = 0; r < l.nrhs; ++r) {

@@ -16,40 +16,9 @@
 #include <type_traits>
 
 #include "wd_internal.h"
+#include "wd_spin.cuh"
 
 namespace wd {
-
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void spin_project(const cx<R> psi[12], cx<R> h[6]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cx<R> p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
-        cx<R> a0, a1;   // A_mu (p2, p3)
-        if (MU == 0)      { a0 = times_mi(p3); a1 = times_mi(p2); }          // A = -i s1
-        else if (MU == 1) { a0 = cmake(-p3.re, -p3.im); a1 = p2; }           // A = -i s2
-        else if (MU == 2) { a0 = times_mi(p2); a1 = times_i(p3); }           // A = -i s3
-        else              { a0 = p2; a1 = p3; }                              // A = 1
-        if (SIGN > 0) { h[c] = p0 + a0; h[3 + c] = p1 + a1; }
-        else          { h[c] = p0 - a0; h[3 + c] = p1 - a1; }
-    }
-}
-
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void spin_reconstruct_add(cx<R> acc[12], const cx<R> h[6]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cx<R> h0 = h[c], h1 = h[3 + c];
-        acc[c] = acc[c] + h0;
-        acc[3 + c] = acc[3 + c] + h1;
-        cx<R> b0, b1;   // A_mu^dag (h0, h1)
-        if (MU == 0)      { b0 = times_i(h1); b1 = times_i(h0); }
-        else if (MU == 1) { b0 = h1; b1 = cmake(-h0.re, -h0.im); }
-        else if (MU == 2) { b0 = times_i(h0); b1 = times_mi(h1); }
-        else              { b0 = h0; b1 = h1; }
-        if (SIGN > 0) { acc[6 + c] = acc[6 + c] + b0; acc[9 + c] = acc[9 + c] + b1; }
-        else          { acc[6 + c] = acc[6 + c] - b0; acc[9 + c] = acc[9 + c] - b1; }
-    }
-}
 
 // out[i] = sum_j u[3i+j] in[j] for both half-spinor spins
 template <typename R>

@@ -32,6 +32,7 @@ struct HopArgs {
     const void *w;         // same-parity addend (nullable)
     const void *w2;        // second same-parity addend (nullable)
     const void *gauge;     // links of the output parity: [8][9][Vh]
+    const void *gauge_lo = nullptr;   // FP32 remainders of the FP64 links (double-float stencil)
     double a, b, c;        // out = a*w + c*w2 + b*H(in)
     int p;                 // output parity
     int nrhs, nrb;
@@ -41,6 +42,9 @@ struct HopArgs {
 
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
+
+// FP64 fields, double-float arithmetic (wd_dslash_dd.cu); R = 1, 2
+cudaError_t launch_hop_dd(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
 
 // several lattices' stencils in one persistent launch (FP32 arithmetic only)
 static constexpr int WD_MAX_BATCH = 8;
@@ -52,12 +56,13 @@ struct HopBatch {
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop_batched(HopBatch B, int R, cudaStream_t st);
 
-// Precision tags of the inner solve
-enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+// Precision tags of the inner solve; PDD: FP64 storage, double-float
+// arithmetic (stencil only: the FP64 steps of the mixed-precision solves)
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PDD = 3 };
 
 // Bytes of one site-spinor (12 complex) and one link (9 complex) per storage
-inline int spinor_bytes(int prec) { return prec == P64 ? 192 : prec == P32 ? 96 : 48; }
-inline int link_bytes(int prec) { return prec == P64 ? 144 : prec == P32 ? 72 : 36; }
+inline int spinor_bytes(int prec) { return prec == P64 || prec == PDD ? 192 : prec == P32 ? 96 : 48; }
+inline int link_bytes(int prec) { return prec == P64 || prec == PDD ? 144 : prec == P32 ? 72 : 36; }
 
 // BiCGStab per-RHS state, FP64 scalars
 struct BiState {
@@ -94,14 +99,16 @@ struct wd_ctx {
     wd::Geom g;
     cudaStream_t st;
     void *gauge[3];                 // eo doubled links per precision P64/P32/P16: [2][8][9][Vh]
+    void *gauge_lo;                 // FP64 link minus its FP32 copy, as FP32: [2][8][9][Vh] float2
+    int outer;                      // stencil of the FP64 steps of mixed solves: PDD, or P64 (WD_DD=0)
     std::map<std::string, std::pair<void *, size_t>> bufs;   // named device workspaces
     std::map<std::string, std::pair<void *, size_t>> hbufs;  // named pinned host workspaces
     int64_t launches;
     bool prof;
     std::vector<wd_prof_rec> recs;
     std::vector<cudaEvent_t> event_pool;
-    int hop_R[3];                   // default RHS tile per input precision
-    int hop_threads[3];
+    int hop_R[4];                   // default RHS tile per input precision
+    int hop_threads[4];
     bool autotune;                  // time the stencil launch shapes on first use
     int *hop_err;                   // device flag: a staged stencil wait gave up
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)

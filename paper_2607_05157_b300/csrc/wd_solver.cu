@@ -170,11 +170,12 @@ static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
     return hop(c, S->pin, S->pout, 0, out, S->tmp, in, 1.0, -c->kappa * c->kappa, nrhs);
 }
 
-// r = b - D_hat x = b - x + k^2 H_eo H_oe x, FP64
+// r = b - D_hat x = b - x + k^2 H_eo H_oe x on FP64 fields, with the stencil
+// S->pin (P64, or PDD: double-float arithmetic)
 static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
     SchurArgs *S = (SchurArgs *)u;
-    WD_TRY(hop(c, P64, P64, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
-    return hop(c, P64, P64, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
+    WD_TRY(hop(c, S->pin, S->pin, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
+    return hop(c, S->pin, S->pin, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
 }
 
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
@@ -196,25 +197,30 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     for (int r = 0; r < nrhs; ++r) bnorm2[r] += bnorm2[nrhs + r];
     bnorm2.resize(nrhs);
     WD_CUDA(cudaMemcpyAsync(bn2 + 2 * nrhs, bnorm2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
+    // The FP64 steps (source, residuals, reconstruction) of a mixed solve run
+    // the double-float stencil: FP64 fields, ~2^-44 normwise, well below the
+    // tolerances the outer loop certifies (tol < 1e-12 and the FP64 mode keep
+    // FP64 arithmetic).
+    const int pd = prec == P64 || tol < 1e-12 ? P64 : c->outer;
     // b_hat = b_e + k H_eo b_o                                         (a3)
-    WD_TRY(hop(c, P64, P64, 0, bhat, b_o, b_e, 1.0, k, nrhs));
+    WD_TRY(hop(c, pd, pd, 0, bhat, b_o, b_e, 1.0, k, nrhs));
 
     const int pp = prec == P16 ? P16 : (prec == P32 ? P32 : P64);
     void *tmplo = nullptr;
     if (prec != P64) WD_TRY(ws_get(c, "sol.tmplo", field_bytes(c->g, pp, nrhs), &tmplo));
-    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo};
+    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo}, sres = {pd, pd, tmp64};
     Problem P;
     P.sp = sp;
     P.op64 = schur_op; P.u64 = &s64;
     P.oplo = schur_op; P.ulo = &slo;
-    P.res64 = schur_res64; P.ures = &s64;
+    P.res64 = schur_res64; P.ures = &sres;
     P.tag = "fine";
     std::vector<int> iters;
     std::vector<double> last_rn2;
     int status = dc_solve(c, P, bhat, x_e, nrhs, bn2 + 2 * nrhs, bnorm2, tol, prec, max_iter, iters, last_rn2);
     if (status != WD_OK && status != WD_ENOCONV && status != WD_EBREAKDOWN) return status;
     // x_o = b_o + k H_oe x_e                                             (a7)
-    WD_TRY(hop(c, P64, P64, 1, x_o, x_e, b_o, 1.0, k, nrhs));
+    WD_TRY(hop(c, pd, pd, 1, x_o, x_e, b_o, 1.0, k, nrhs));
     // True FP64 residual of the full system, when asked for.  Without it the
     // last FP64 Schur residual (mixed modes) or the FP64 recursion (FP64 mode)
     // certifies convergence: the full residual of (x_e, x_o) equals the Schur

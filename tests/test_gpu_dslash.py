@@ -11,13 +11,15 @@ pytestmark = pytest.mark.gpu
 
 BC = (1, 1, 1, -1)
 # bounds: FP64 from the benchmark spec's tolerance; FP32 ~ 8 terms of unit size in
-# single precision (eps 6e-8); BF16 storage of links and input (eps 2^-9)
-TOL = {0: 1e-13, 1: 3e-6, 2: 2e-2}
+# single precision (eps 6e-8); BF16 storage of links and input (eps 2^-9);
+# double-float (3): inputs split to 47 bits, every product and sum exact up to
+# terms of 2^-48 relative, ~100 of them per output -> a few 1e-14, bound 1e-12
+TOL = {0: 1e-13, 1: 3e-6, 2: 2e-2, 3: 1e-12}
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 8), (6, 2, 4, 2)])
 @pytest.mark.parametrize("nrhs", [1, 3, 5])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_apply_parity(dims, nrhs, prec, dagger):
     import torch
@@ -26,7 +28,7 @@ def test_apply_parity(dims, nrhs, prec, dagger):
     kappa = 0.125
     psi = synth.spinors(dims, nrhs, 31)
     ctx = Context(dims, U, kappa, BC)
-    dt = torch.complex128 if prec == 0 else torch.complex64
+    dt = torch.complex128 if prec in (0, 3) else torch.complex64
     y = ctx.apply(to_dev(psi, dt), prec=prec, dagger=dagger).cpu().numpy()
     f = wilson.apply_dagger if dagger else wilson.apply
     ref = f(U, psi, kappa, BC)
@@ -34,6 +36,47 @@ def test_apply_parity(dims, nrhs, prec, dagger):
         assert rel(y[r], ref[r]) < TOL[prec], (r, rel(y[r], ref[r]))
     if prec == 0:
         assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
+    if prec == 3:
+        assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e-8, 1.0, 1e25])
+def test_apply_double_float_range(scale):
+    """Double-float stencil over the input range it supports (2^-103 .. 2^127):
+    relative accuracy independent of the scale; exact zeros (time-diluted
+    sources are zero off their timeslice) stay zero."""
+    import torch
+    from paper_2607_05157_b300 import Context, WD_FP64_DD
+    dims = (4, 4, 4, 8)
+    U = synth.gauge_field(dims, 0.5, 1004)
+    psi = synth.spinors(dims, 2, 77) * scale
+    psi[1, 2:] = 0.0          # rhs 1: zero on timeslices 2..7
+    ctx = Context(dims, U, 0.125, BC)
+    y = ctx.apply(to_dev(psi), prec=WD_FP64_DD).cpu().numpy()
+    ref = wilson.apply(U, psi, 0.125, BC)
+    for r in range(2):
+        assert rel(y[r], ref[r]) < TOL[3], (scale, r, rel(y[r], ref[r]))
+    # D = 1 - k H: no output outside timeslices 1..3 for rhs 1 except from t = 0, 1
+    assert np.all(y[1, 3:7] == 0.0)
+    ctx.close()
+
+
+def test_apply_double_float_vs_fp64_and_fp32():
+    """The double-float stencil is at least 10^4 times closer to the FP64
+    result than the FP32 stencil on the same input (8^3 x 16, 16 RHS)."""
+    import torch
+    from paper_2607_05157_b300 import Context, WD_FP64_DD
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 0.5, 1002)
+    psi = synth.spinors(dims, 16, 9)
+    ctx = Context(dims, U, 0.125, BC)
+    y64 = ctx.apply(to_dev(psi), prec=0).cpu().numpy()
+    ydd = ctx.apply(to_dev(psi), prec=WD_FP64_DD).cpu().numpy()
+    y32 = ctx.apply(to_dev(psi, torch.complex64), prec=1).cpu().numpy()
+    e_dd = max(rel(ydd[r], y64[r]) for r in range(16))
+    e_32 = max(rel(y32[r], y64[r]) for r in range(16))
+    assert e_dd < 1e-12 and e_dd * 1e4 < e_32, (e_dd, e_32)
     ctx.close()
 
 

@@ -74,3 +74,27 @@ def test_zero_rhs():
     assert np.all(x[0] == 0) and res[0] == 0
     assert res[1] <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_outer_double_float_vs_fp64(monkeypatch, prec):
+    """Mixed solves whose FP64 steps use the double-float stencil (default)
+    and the FP64 stencil (WD_DD=0): both meet 1e-10 by the oracle's own FP64
+    residual, and their solutions agree to the tolerance."""
+    from paper_2607_05157_b300 import Context
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 0.5, 1002)
+    b = synth.spinors(dims, 4, 41)
+    xs = []
+    for dd in ('1', '0'):
+        monkeypatch.setenv('WD_DD', dd)
+        ctx = Context(dims, U, 0.125, (1, 1, 1, -1))
+        x, it, res = ctx.solve(to_dev(b), tol=1e-10, prec=prec)
+        x = x.cpu().numpy()
+        for r in range(4):
+            rr = b[r] - wilson.apply(U, x[r], 0.125, (1, 1, 1, -1))
+            assert np.linalg.norm(rr) <= 1e-10 * np.linalg.norm(b[r]) * 1.01
+        xs.append(x)
+        ctx.close()
+    for r in range(4):
+        assert rel(xs[0][r], xs[1][r]) < 1e-8
