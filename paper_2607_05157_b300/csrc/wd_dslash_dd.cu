@@ -110,32 +110,39 @@ __device__ __forceinline__ void su3_dd(const cx<dd> u[9], const cx<dd> in[6], cx
         }
 }
 
-template <int R, int D, bool DAG>
-__device__ __forceinline__ void hop_dir_dd(const HopArgs &A, int s, int nb, int rb, cx<dd> acc[][12]) {
-    constexpr int MU = D & 3;
-    constexpr bool FWD = D < 4;
-    constexpr int SIGN = (FWD != DAG) ? -1 : +1;
-    const long Vh = A.g.Vh;
-    cx<dd> u[9];
-    {
-        const float2 *qh = (const float2 *)A.gauge + (size_t)D * 9 * Vh + s;
-        const float2 *ql = (const float2 *)A.gauge_lo + (size_t)D * 9 * Vh + s;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float2 h = __ldg(qh + k * Vh), l = __ldg(ql + k * Vh);
-            u[k] = cmake(dd_make(h.x, l.x), dd_make(h.y, l.y));
-        }
+// The eight directions run as one rolled loop: the SU(3) product and the input
+// conversion (most of the instructions) exist once in the code, only the spin
+// projection and reconstruction are specialised per direction behind a
+// warp-uniform switch.  Unrolled, the directions make ~11k instructions of
+// straight-line double-float code and the kernel stalls on instruction fetch.
+template <bool DAG>
+__device__ __forceinline__ void project_dir(int d, const cx<dd> psi[12], cx<dd> h[6]) {
+    // D uses (1 - g) forward and (1 + g) backward; D^dag swaps them
+    constexpr int F = DAG ? +1 : -1, B = -F;
+    switch (d) {
+        case 0: spin_project<0, F>(psi, h); break;
+        case 1: spin_project<1, F>(psi, h); break;
+        case 2: spin_project<2, F>(psi, h); break;
+        case 3: spin_project<3, F>(psi, h); break;
+        case 4: spin_project<0, B>(psi, h); break;
+        case 5: spin_project<1, B>(psi, h); break;
+        case 6: spin_project<2, B>(psi, h); break;
+        default: spin_project<3, B>(psi, h); break;
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs < A.nrhs) {
-            cx<dd> psi[12], h[6], uh[6];
-            load_dd((const double2 *)A.in + (size_t)rhs * 12 * Vh, Vh, nb, psi);
-            spin_project<MU, SIGN>(psi, h);
-            su3_dd(u, h, uh);
-            spin_reconstruct_add<MU, SIGN>(acc[r], uh);
-        }
+}
+
+template <bool DAG>
+__device__ __forceinline__ void reconstruct_dir(int d, cx<dd> acc[12], const cx<dd> uh[6]) {
+    constexpr int F = DAG ? +1 : -1, B = -F;
+    switch (d) {
+        case 0: spin_reconstruct_add<0, F>(acc, uh); break;
+        case 1: spin_reconstruct_add<1, F>(acc, uh); break;
+        case 2: spin_reconstruct_add<2, F>(acc, uh); break;
+        case 3: spin_reconstruct_add<3, F>(acc, uh); break;
+        case 4: spin_reconstruct_add<0, B>(acc, uh); break;
+        case 5: spin_reconstruct_add<1, B>(acc, uh); break;
+        case 6: spin_reconstruct_add<2, B>(acc, uh); break;
+        default: spin_reconstruct_add<3, B>(acc, uh); break;
     }
 }
 
@@ -147,10 +154,6 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
     const Geom &g = A.g;
     int x, y, z, t;
     eo_coords(g, A.p, s, x, y, z, t);
-    const int xp = x + 1 == g.X ? 0 : x + 1, xm = x == 0 ? g.X - 1 : x - 1;
-    const int yp = y + 1 == g.Y ? 0 : y + 1, ym = y == 0 ? g.Y - 1 : y - 1;
-    const int zp = z + 1 == g.Z ? 0 : z + 1, zm = z == 0 ? g.Z - 1 : z - 1;
-    const int tp = t + 1 == g.T ? 0 : t + 1, tm = t == 0 ? g.T - 1 : t - 1;
 
     cx<dd> acc[R][12];
 #pragma unroll
@@ -158,14 +161,40 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[r][k] = cmake(dd_make(0.f, 0.f), dd_make(0.f, 0.f));
 
-    hop_dir_dd<R, 0, DAG>(A, s, eo_index(g, xp, y, z, t), rb, acc);
-    hop_dir_dd<R, 1, DAG>(A, s, eo_index(g, x, yp, z, t), rb, acc);
-    hop_dir_dd<R, 2, DAG>(A, s, eo_index(g, x, y, zp, t), rb, acc);
-    hop_dir_dd<R, 3, DAG>(A, s, eo_index(g, x, y, z, tp), rb, acc);
-    hop_dir_dd<R, 4, DAG>(A, s, eo_index(g, xm, y, z, t), rb, acc);
-    hop_dir_dd<R, 5, DAG>(A, s, eo_index(g, x, ym, z, t), rb, acc);
-    hop_dir_dd<R, 6, DAG>(A, s, eo_index(g, x, y, zm, t), rb, acc);
-    hop_dir_dd<R, 7, DAG>(A, s, eo_index(g, x, y, z, tm), rb, acc);
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        // neighbour x + mu (d < 4) or x - mu (d >= 4) with periodic wrap (the
+        // boundary factor is folded into the links)
+        const int mu = d & 3;
+        int c[4] = {x, y, z, t};
+        const int L[4] = {g.X, g.Y, g.Z, g.T};
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (m == mu) c[m] = d < 4 ? (c[m] + 1 == L[m] ? 0 : c[m] + 1) : (c[m] == 0 ? L[m] - 1 : c[m] - 1);
+        const int nb = eo_index(g, c[0], c[1], c[2], c[3]);
+        const long Vh = g.Vh;
+        cx<dd> u[9];
+        {
+            const float2 *qh = (const float2 *)A.gauge + (size_t)d * 9 * Vh + s;
+            const float2 *ql = (const float2 *)A.gauge_lo + (size_t)d * 9 * Vh + s;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float2 h = __ldg(qh + k * Vh), l = __ldg(ql + k * Vh);
+                u[k] = cmake(dd_make(h.x, l.x), dd_make(h.y, l.y));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int rhs = rb * R + r;
+            if (rhs < A.nrhs) {
+                cx<dd> psi[12], h[6], uh[6];
+                load_dd((const double2 *)A.in + (size_t)rhs * 12 * Vh, Vh, nb, psi);
+                project_dir<DAG>(d, psi, h);
+                su3_dd(u, h, uh);
+                reconstruct_dir<DAG>(d, acc[r], uh);
+            }
+        }
+    }
 
     const long Vh = g.Vh;
     const dd a = d2dd(A.a), b = d2dd(A.b), c = d2dd(A.c);
