@@ -181,6 +181,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
+    A.act = c->act; A.act_stride = c->act_stride;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
     if (pin == PDD) {
@@ -321,6 +322,8 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     }
     c->autotune = getenv("WD_NO_AUTOTUNE") == nullptr;
     c->hop_err = nullptr;
+    c->act = nullptr;
+    c->act_stride = 0;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("wd_create: allocation failed");

@@ -330,8 +330,10 @@ __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm
 
 // partial sums of conj(a).b (slots 0, 1) and optionally |a|^2 (slot 2)
 template <typename SA, typename SB, bool NORMA, bool FL>
-__global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, int nrhs, int bpr) {
+__global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, int nrhs, int bpr,
+                           const BiState *st) {
     typedef typename RT_of<SA>::type RT;
+    if (st && !st[blockIdx.y].active) return;    // converged RHS: partials unused
     Range R = my_range(Vh);
     cx<RT> acc = cmake(RT(0), RT(0));
     RT nn = 0;
@@ -417,11 +419,17 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
     if (threadIdx.x == 0) *count = cnt;
 }
 
+// The iteration kernels below skip every RHS whose state is inactive
+// (converged or broken down): its x and r keep their final values, and the
+// other fields of that RHS are neither read nor written again in this run.
+// Stencil launches inside the run skip the same RHS (HopArgs::act).
+
 // s = r - alpha v
 template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long Vh, long n) {
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        if (!st[u / Vh].active) continue;
         const double2 a = st[u / Vh].alpha;
         const cx<RT> mal = cmake((RT)-a.x, (RT)-a.y);
         cx<RT> rv[12], vv[12];
@@ -438,6 +446,7 @@ template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const void *t, const void *rh,
                           const BiState *st, double *part, long Vh, int nrhs, int bpr) {
     typedef typename RT_of<SW>::type RT;
+    if (!st[blockIdx.y].active) return;          // converged RHS: x, r stay as they are
     Range R = my_range(Vh);
     const double2 a = st[blockIdx.y].alpha, w = st[blockIdx.y].omega;
     const cx<RT> al = cmake((RT)a.x, (RT)a.y), om = cmake((RT)w.x, (RT)w.y), mom = cmake(-om.re, -om.im);
@@ -473,6 +482,7 @@ __global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *s
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const BiState &S = st[u / Vh];
+        if (!S.active) continue;
         const cx<RT> be = cmake((RT)S.beta.x, (RT)S.beta.y), mom = cmake((RT)-S.omega.x, (RT)-S.omega.y);
         cx<RT> rv[12], pv[12], vv[12];
         ldsite<SW, RT, FL>(r, Vh, u, rv);
@@ -513,7 +523,7 @@ int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr);
+        k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr, V.st);
         k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
     }));
@@ -529,7 +539,7 @@ int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr);
+        k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr, V.st);
         k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_xr<SW, SP, FL><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
         k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);

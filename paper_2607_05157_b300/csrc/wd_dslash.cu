@@ -47,7 +47,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, int s, int nb, int rb,
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int rhs = rb * R + r;
-        if (rhs < A.nrhs) {
+        if (rhs < A.nrhs && rhs_on(A, rhs)) {
             cx<RT> psi[12], h[6], uh[6];
             SIO<SIn>::load((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi);
             spin_project<MU, SIGN>(psi, h);
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     for (int r = 0; r < R; ++r) {
         const int rhs = rb * R + r;
         if (rhs >= A.nrhs) break;
+        if (!rhs_on(A, rhs)) continue;
         cx<RT> o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = b * acc[r][k];
@@ -188,7 +189,7 @@ __device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int rhs = rb * R + r;
-        if (rhs < A.nrhs) {
+        if (rhs < A.nrhs && rhs_on(A, rhs)) {
             float2 psi[12], h[6], hs[6], uh[6];
             load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi);
             proj_f2<MU, SIGN>(psi, h);
@@ -224,7 +225,7 @@ __device__ __forceinline__ void load_dir_f2(const HopArgs &A, int s, int nb, int
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int rhs = rb * R + r;
-        if (rhs < A.nrhs) load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi[r]);
+        if (rhs < A.nrhs && rhs_on(A, rhs)) load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi[r]);
     }
 }
 
@@ -236,7 +237,7 @@ __device__ __forceinline__ void compute_dir_f2(const HopArgs &A, int rb, const c
     constexpr int SIGN = (FWD != DAG) ? -1 : +1;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (rb * R + r < A.nrhs) {
+        if (rb * R + r < A.nrhs && rhs_on(A, rb * R + r)) {
             float2 h[6], hs[6], uh[6];
             proj_f2<MU, SIGN>(psi[r], h);
 #pragma unroll
@@ -319,6 +320,7 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     for (int r = 0; r < R; ++r) {
         const int rhs = rb * R + r;
         if (rhs >= A.nrhs) break;
+        if (!rhs_on(A, rhs)) continue;
         float2 o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = __fmul2_rn(b2, acc[r][k]);

@@ -38,7 +38,15 @@ struct HopArgs {
     int nrhs, nrb;
     Geom g;
     int *err;              // error flag of the staged variant (bounded waits); set by hop()
+    // Krylov activity of each RHS (nullable): RHS r is skipped when
+    // act[r * act_stride] == 0 -- inside a BiCGStab run the converged RHS
+    const int *act = nullptr;
+    int act_stride = 0;
 };
+
+__device__ __forceinline__ bool rhs_on(const HopArgs &A, int rhs) {
+    return A.act == nullptr || __ldg(A.act + (size_t)rhs * A.act_stride) != 0;
+}
 
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
@@ -70,6 +78,7 @@ struct BiState {
     double rr, bb, thr;    // |r|^2, |b|^2, convergence threshold on |r|^2
     int active, flag, iters, pad;
 };
+static_assert(sizeof(BiState) % sizeof(int) == 0, "the activity mask strides BiState in ints");
 
 }  // namespace wd
 
@@ -111,6 +120,8 @@ struct wd_ctx {
     int hop_threads[4];
     bool autotune;                  // time the stencil launch shapes on first use
     int *hop_err;                   // device flag: a staged stencil wait gave up
+    const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)
+    int act_stride;
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
     std::vector<double> last_level2;    // [n2][T][2]

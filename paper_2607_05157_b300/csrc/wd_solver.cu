@@ -37,8 +37,11 @@ int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V
     return WD_OK;
 }
 
-// Run BiCGStab iterations until no RHS is active or max_iter is reached; the
-// host reads the active count every `check` iterations.
+// Run BiCGStab iterations until no RHS is active or max_iter is reached.  The
+// host reads the active count every second iteration; in between, every
+// kernel of an iteration (stencil and BLAS) skips the RHS that have converged
+// (the stencil through the activity mask set here), so an iteration issued
+// after the last RHS converged costs only its launches.
 static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter, int *ran) {
     int *hcount;
     WD_TRY(hws_get(c, "count", sizeof(int), (void **)&hcount));
@@ -46,7 +49,13 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
     WD_CUDA(cudaMemcpyAsync(hcount, V.count, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     WD_CUDA(cudaStreamSynchronize(c->st));
     int active = *hcount;
-    int check = 4;
+    struct MaskGuard {
+        wd_ctx *c;
+        ~MaskGuard() { c->act = nullptr; c->act_stride = 0; }
+    } guard{c};
+    c->act = &V.st[0].active;
+    c->act_stride = (int)(sizeof(BiState) / sizeof(int));
+    const int check = 2;
     while (active > 0 && it < max_iter) {
         int k = check < max_iter - it ? check : max_iter - it;
         for (int i = 0; i < k; ++i) WD_TRY(bicg_iter(c, pw, pp, V, nrhs));
@@ -54,7 +63,6 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
         WD_CUDA(cudaMemcpyAsync(hcount, V.count, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         WD_CUDA(cudaStreamSynchronize(c->st));
         active = *hcount;
-        if (check < 16) check *= 2;
     }
     *ran = it;
     return WD_OK;
