@@ -90,7 +90,7 @@ static const void *gauge_parity(wd_ctx *c, int prec, int p) {
 }
 
 static cudaError_t launch_hop_any(int pin, int pout, const HopArgs &A, int R, bool dag, int th, cudaStream_t st) {
-    if (pin == PDD) return launch_hop_dd(A, R, dag, th, st);
+    if (is_dd(pin)) return launch_hop_dd(A, R, dag, th, pout == PDDL, st);
     if (pin == P64) return launch_hop<double, double, double, double>(A, R, dag, th, st);
     if (pin == P32) return launch_hop<float, float, float, float>(A, R, dag, th, st);
     if (pout == P16) return launch_hop<bf16, bf16, bf16, bf16>(A, R, dag, th, st);
@@ -110,7 +110,18 @@ static int rhs_bucket(int nrhs) {
 static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, int *R, int *th) {
     // WD_HOP_R = "R" or "R:threads" overrides the FP32/BF16 launch shape (R code as
     // below; 128 threads unless given), for experiments, profiling and tests
-    if (pin != P64) {
+    // WD_DD_R = "R[:threads]" does the same for the double-float stencil (R = 1, 2
+    // scalar, 11, 12 packed)
+    if (is_dd(pin)) {
+        const char *ov = getenv("WD_DD_R");
+        if (ov && atoi(ov) > 0) {
+            *R = atoi(ov);
+            const char *colon = strchr(ov, ':');
+            *th = colon && atoi(colon + 1) > 0 ? atoi(colon + 1) : 128;
+            return WD_OK;
+        }
+    }
+    if (pin == P32 || pin == P16) {
         const char *ov = getenv("WD_HOP_R");
         if (ov && atoi(ov) > 0) {
             *R = atoi(ov);
@@ -119,7 +130,7 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
             return WD_OK;
         }
     }
-    const int key = (pin * 4 + pout) * 8192 + rhs_bucket(A.nrhs);
+    const int key = (pin * 8 + pout) * 8192 + rhs_bucket(A.nrhs);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) { *R = it->second.first; *th = it->second.second; return WD_OK; }
     *R = c->hop_R[pin];
@@ -136,8 +147,9 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     float best = 1e30f;
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 3; ++j) {
-            if ((pin == P64 || pin == PDD) && Rs[i] > 2) continue;   // FP64 fields: R = 1, 2 only (R = 4 spills)
-            if (pin == PDD && Ts[j] > 128) continue;                 // double-float: at most 128 threads
+            if (pin == P64 && Rs[i] > 2) continue;                   // FP64: R = 1, 2 only (R = 4 spills)
+            if (is_dd(pin) && Rs[i] != 1 && Rs[i] != 2 && Rs[i] != 11 && Rs[i] != 12) continue;
+            if (is_dd(pin) && Ts[j] > 128) continue;                 // double-float: at most 128 threads
             if (Rs[i] > 20 && j > 0) continue;              // staged: one block size
             {
                 const cudaError_t e = launch_hop_any(pin, pout, A, Rs[i], dag, Ts[j], c->st);   // warm
@@ -184,20 +196,34 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     A.act = c->act; A.act_stride = c->act_stride;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
-    if (pin == PDD) {
+    if (is_dd(pin)) {
         A.gauge = gauge_parity(c, P32, p);
         A.gauge_lo = (const char *)c->gauge_lo + (size_t)p * 8 * 9 * c->g.Vh * sizeof(float2);
     } else {
         A.gauge = gauge_parity(c, pin, p);
     }
-    int R, th;
-    WD_TRY(tune_hop(c, pin, pout, A, dag, &R, &th));
     // algorithmic bytes: nrhs x (in + out [+ w + w2]) spinors + 8 links per output site
     const double sb_in = spinor_bytes(pin), sb_out = spinor_bytes(pout);
     const double bytes = (double)c->g.Vh *
                          (nrhs * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
-    prof_begin(c, pin == P64 || pin == PDD ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
+    prof_begin(c, pin == P64 || is_dd(pin) ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
+    if (pin == PDD) {
+        // FP64 input: split once into the double-float layout (part of this
+        // stencil application's time; its bytes are not algorithmic)
+        void *ddl;
+        const int s = ws_get(c, "dd.in", field_bytes(c->g, P64, nrhs), &ddl);
+        if (s != WD_OK) { prof_end(c, slot); return s; }
+        cudaError_t e = launch_to_ddl(in, ddl, 12L * c->g.Vh * nrhs, c->st);
+        c->launches++;
+        if (e != cudaSuccess) { prof_end(c, slot); set_error("hop: %s", cudaGetErrorString(e)); return WD_ECUDA; }
+        A.in = ddl;
+    }
+    int R, th;
+    {
+        const int s = tune_hop(c, pin, pout, A, dag, &R, &th);
+        if (s != WD_OK) { prof_end(c, slot); return s; }
+    }
     cudaError_t e = launch_hop_any(pin, pout, A, R, dag, th, c->st);
     if (e == cudaErrorNotSupported)   // an overridden variant that does not fit this shape
         e = launch_hop_any(pin, pout, A, c->hop_R[pin], dag, c->hop_threads[pin], c->st);
@@ -313,7 +339,7 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->prof = false;
     c->mg = nullptr;
     c->last_n2 = 0;
-    for (int p = 0; p < 4; ++p) { c->hop_R[p] = p == P64 || p == PDD ? 1 : 2; c->hop_threads[p] = 128; }
+    for (int p = 0; p < 5; ++p) { c->hop_R[p] = p == P64 || is_dd(p) ? 1 : 2; c->hop_threads[p] = 128; }
     for (int p = 0; p < 3; ++p) c->gauge[p] = nullptr;
     c->gauge_lo = nullptr;
     {

@@ -257,8 +257,9 @@ static int batch_solve_impl(wd_batch *b, cudaStream_t bst, const double *const *
             const Space sp = fine_space(l.c->g);
             WD_TRY(blas_axpy_mixed(l.c, sp, l.xe, P32, l.V.x, l.scale + l.nrhs, l.nrhs));
             // r = b_hat - D_hat x on FP64 fields (double-float stencil unless WD_DD=0 or tol < 1e-12)
-            WD_TRY(hop(l.c, outer_of(l.c), outer_of(l.c), 1, l.tmp64, l.xe, nullptr, 0.0, 1.0, l.nrhs));
-            WD_TRY(hop(l.c, outer_of(l.c), outer_of(l.c), 0, l.r64, l.tmp64, l.bhat, 1.0, l.c->kappa * l.c->kappa, l.nrhs, false, l.xe, -1.0));
+            const int od = outer_of(l.c), ot = od == PDD ? PDDL : od;
+            WD_TRY(hop(l.c, od, ot, 1, l.tmp64, l.xe, nullptr, 0.0, 1.0, l.nrhs));
+            WD_TRY(hop(l.c, ot, od, 0, l.r64, l.tmp64, l.bhat, 1.0, l.c->kappa * l.c->kappa, l.nrhs, false, l.xe, -1.0));
         }
     }
     if (exec) cudaGraphExecDestroy(exec);

@@ -51,8 +51,13 @@ __device__ __forceinline__ bool rhs_on(const HopArgs &A, int rhs) {
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
 
-// FP64 fields, double-float arithmetic (wd_dslash_dd.cu); R = 1, 2
-cudaError_t launch_hop_dd(const HopArgs &A, int R, bool dag, int threads, cudaStream_t st);
+// Double-float stencil (wd_dslash_dd.cu): A.in in the double-float layout
+// (FP64 eo layout, each complex as float4 (re.h, im.h, re.l, im.l)), addends
+// FP64, output FP64 or (out_dd) double-float layout.  R = 1, 2 scalar; 11, 12
+// packed f32x2.
+cudaError_t launch_hop_dd(const HopArgs &A, int R, bool dag, int threads, bool out_dd, cudaStream_t st);
+// FP64 eo field -> double-float layout, n complex numbers
+cudaError_t launch_to_ddl(const void *in, void *out, long n, cudaStream_t st);
 
 // several lattices' stencils in one persistent launch (FP32 arithmetic only)
 static constexpr int WD_MAX_BATCH = 8;
@@ -64,13 +69,15 @@ struct HopBatch {
 template <typename SIn, typename SOut, typename SW, typename G>
 cudaError_t launch_hop_batched(HopBatch B, int R, cudaStream_t st);
 
-// Precision tags of the inner solve; PDD: FP64 storage, double-float
-// arithmetic (stencil only: the FP64 steps of the mixed-precision solves)
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PDD = 3 };
+// Precision tags of the inner solve.  Stencil-only tags for the FP64 steps of
+// the mixed-precision solves (double-float arithmetic): PDD = FP64 storage,
+// PDDL = double-float layout (same bytes per site).
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PDD = 3, PDDL = 4 };
+inline bool is_dd(int prec) { return prec == PDD || prec == PDDL; }
 
 // Bytes of one site-spinor (12 complex) and one link (9 complex) per storage
-inline int spinor_bytes(int prec) { return prec == P64 || prec == PDD ? 192 : prec == P32 ? 96 : 48; }
-inline int link_bytes(int prec) { return prec == P64 || prec == PDD ? 144 : prec == P32 ? 72 : 36; }
+inline int spinor_bytes(int prec) { return prec == P64 || is_dd(prec) ? 192 : prec == P32 ? 96 : 48; }
+inline int link_bytes(int prec) { return prec == P64 || is_dd(prec) ? 144 : prec == P32 ? 72 : 36; }
 
 // BiCGStab per-RHS state, FP64 scalars
 struct BiState {
@@ -116,8 +123,8 @@ struct wd_ctx {
     bool prof;
     std::vector<wd_prof_rec> recs;
     std::vector<cudaEvent_t> event_pool;
-    int hop_R[4];                   // default RHS tile per input precision
-    int hop_threads[4];
+    int hop_R[5];                   // default RHS tile per input precision
+    int hop_threads[5];
     bool autotune;                  // time the stencil launch shapes on first use
     int *hop_err;                   // device flag: a staged stencil wait gave up
     const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)

@@ -179,11 +179,13 @@ static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
 }
 
 // r = b - D_hat x = b - x + k^2 H_eo H_oe x on FP64 fields, with the stencil
-// S->pin (P64, or PDD: double-float arithmetic)
+// S->pin (P64, or PDD: double-float arithmetic, the odd intermediate kept in
+// the double-float layout)
 static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
     SchurArgs *S = (SchurArgs *)u;
-    WD_TRY(hop(c, S->pin, S->pin, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
-    return hop(c, S->pin, S->pin, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
+    const int pt = S->pin == PDD ? PDDL : S->pin;
+    WD_TRY(hop(c, S->pin, pt, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
+    return hop(c, pt, S->pin, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
 }
 
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,

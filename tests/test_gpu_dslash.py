@@ -62,6 +62,27 @@ def test_apply_double_float_range(scale):
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", ["1", "2:64", "11", "12:64"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_double_float_variants(monkeypatch, variant, dagger):
+    """Every launch shape of the double-float stencil (scalar R = 1, 2; packed
+    f32x2 R = 1, 2) against the oracle, on a ragged RHS count and lattice."""
+    import torch
+    from paper_2607_05157_b300 import Context, WD_FP64_DD
+    monkeypatch.setenv('WD_DD_R', variant)
+    dims = (2, 4, 6, 8)
+    U = synth.gauge_field(dims, 0.5, 1005)
+    psi = synth.spinors(dims, 5, 78)
+    ctx = Context(dims, U, 0.125, BC)
+    y = ctx.apply(to_dev(psi), prec=WD_FP64_DD, dagger=dagger).cpu().numpy()
+    f = wilson.apply_dagger if dagger else wilson.apply
+    ref = f(U, psi, 0.125, BC)
+    for r in range(5):
+        assert rel(y[r], ref[r]) < TOL[3], (variant, r, rel(y[r], ref[r]))
+    assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+    ctx.close()
+
+
 def test_apply_double_float_vs_fp64_and_fp32():
     """The double-float stencil is at least 10^4 times closer to the FP64
     result than the FP32 stencil on the same input (8^3 x 16, 16 RHS)."""

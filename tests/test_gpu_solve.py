@@ -98,3 +98,22 @@ def test_outer_double_float_vs_fp64(monkeypatch, prec):
         ctx.close()
     for r in range(4):
         assert rel(xs[0][r], xs[1][r]) < 1e-8
+
+
+@pytest.mark.parametrize("variant", ["1", "11"])
+def test_outer_double_float_variants(monkeypatch, variant):
+    """Mixed FP32 solve with the scalar and the packed double-float stencil in
+    the outer loop (the residual's odd intermediate in the double-float
+    layout): 1e-10 by the oracle's FP64 residual."""
+    from paper_2607_05157_b300 import Context
+    monkeypatch.setenv('WD_DD_R', variant)
+    dims = (4, 4, 6, 8)
+    U = synth.gauge_field(dims, 0.5, 1006)
+    b = synth.spinors(dims, 3, 43)
+    ctx = Context(dims, U, 0.125, BC)
+    x, it, res = ctx.solve(to_dev(b), tol=1e-10, prec=1)
+    x = x.cpu().numpy()
+    for r in range(3):
+        rr = b[r] - wilson.apply(U, x[r], 0.125, BC)
+        assert np.linalg.norm(rr) <= 1e-10 * np.linalg.norm(b[r]) * 1.01
+    ctx.close()
