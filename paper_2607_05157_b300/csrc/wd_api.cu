@@ -195,9 +195,9 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
     A.act = c->act; A.act_stride = c->act_stride;
-    // fused reductions: FP32 arithmetic stencil, D (not D^dag), with the addend w
-    const bool fuse = dot && dot->mode == 2 && (pin == P32 || pin == P16) && w != nullptr && !dag;
-    if (fuse) { A.dot_mode = dot->mode; A.dot_part = dot->part; }
+    // fused reductions: FP32 arithmetic stencil with a same-parity addend only
+    const bool fuse = dot && (pin == P32 || pin == P16) && w != nullptr;
+    if (fuse) { A.dot_mode = dot->mode; A.dot_a = dot->a; A.dot_part = dot->part; }
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
     if (is_dd(pin)) {

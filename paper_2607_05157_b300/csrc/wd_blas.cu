@@ -592,16 +592,17 @@ int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int fused_bps) 
     return WD_OK;
 }
 
-// The operator may fuse the reductions of t = A s into its last stencil
-// launch (c->pending_dot; bps > 0 on return when it did): (t, s) and |t|^2
-// come from values that launch holds anyway.  (rh, v) stays a separate
-// kernel: fused, it would add a field read to the latency-bound stencil.
+// The operator may fuse the step's reductions into its last stencil launch
+// (c->pending_dot; bps > 0 on return when it did).
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
-    HopDot dt = {2, V.fpart, 0};
-    WD_TRY(V.op(c, V.p, V.v, nrhs, V.op_user));       // v = A p
-    WD_TRY(bicg_after_v(c, pw, pp, V, nrhs));
+    HopDot dv = {1, V.rh, V.fpart, 0}, dt = {2, nullptr, V.fpart, 0};
+    c->pending_dot = V.fpart ? &dv : nullptr;
+    int s = V.op(c, V.p, V.v, nrhs, V.op_user);        // v = A p   [+ (rh, v)]
+    c->pending_dot = nullptr;
+    WD_TRY(s);
+    WD_TRY(bicg_after_v(c, pw, pp, V, nrhs, dv.bps));
     c->pending_dot = V.fpart ? &dt : nullptr;
-    int s = V.op(c, V.s, V.t, nrhs, V.op_user);        // t = A s   [+ (t, s), |t|^2]
+    s = V.op(c, V.s, V.t, nrhs, V.op_user);            // t = A s   [+ (t, s), |t|^2]
     c->pending_dot = nullptr;
     WD_TRY(s);
     return bicg_after_t(c, pw, pp, V, nrhs, dt.bps);

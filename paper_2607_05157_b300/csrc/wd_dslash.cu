@@ -340,9 +340,18 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s, flo
 #pragma unroll
         for (int k = 0; k < 12; ++k) oc[k] = cmake(o[k].x, o[k].y);
         SIO<SOut>::store((uint4 *)A.out + (size_t)rhs * NO * Vh, Vh, s, oc);
-        // fused BiCGStab reductions of this site (block-reduced by the caller):
-        // conj(out) . w and |out|^2, from values already in registers
-        if (dots && A.dot_mode == 2) {
+        // fused BiCGStab reductions of this site (block-reduced by the caller)
+        if (dots && A.dot_mode == 1) {          // conj(a) . out
+            float2 av[12];
+            load_f2<SOut>((const uint4 *)A.dot_a + (size_t)rhs * NO * Vh, Vh, s, av);
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                re = fmaf(av[k].x, o[k].x, fmaf(av[k].y, o[k].y, re));
+                im = fmaf(av[k].x, o[k].y, fmaf(-av[k].y, o[k].x, im));
+            }
+            dots[r][0] = re; dots[r][1] = im;
+        } else if (dots && A.dot_mode == 2) {   // conj(out) . w and |out|^2
             float re = 0.f, im = 0.f, nn = 0.f;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
@@ -386,21 +395,19 @@ __device__ __forceinline__ void hop_dot_partials(const HopArgs &A, int rb, float
     }
 }
 
-// DOT: the variant with the fused reductions of HopArgs::dot_mode (a separate
-// instantiation, so that the plain stencil keeps its code size)
-template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE, bool DOT = false>
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE>
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if constexpr (!DOT) {
+    if (A.dot_mode == 0) {
         if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s);
-    } else {
-        float dots[R][3];
-#pragma unroll
-        for (int r = 0; r < R; ++r) dots[r][0] = dots[r][1] = dots[r][2] = 0.f;
-        if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s, dots);
-        hop_dot_partials<R>(A, rb, dots);   // every thread of the block takes part
+        return;
     }
+    float dots[R][3];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dots[r][0] = dots[r][1] = dots[r][2] = 0.f;
+    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s, dots);
+    hop_dot_partials<R>(A, rb, dots);
 }
 
 // Persistent batched stencil over several lattices (row a11): one launch walks
@@ -696,10 +703,7 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
 #define WD_HOP_CASE(RR)                                                                                \
     if (R == RR) {                                                                                     \
         if constexpr (PACKED) {                                                                        \
-            if (A.dot_mode) {                                                                          \
-                if (pipe) hop_kernel_f2<SIn, SOut, SW, G, RR, false, true, true><<<grid, threads, 0, st>>>(A); \
-                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, false, true><<<grid, threads, 0, st>>>(A); \
-            } else if (pipe) {                                                                         \
+            if (pipe) {                                                                                \
                 if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, true><<<grid, threads, 0, st>>>(A); \
                 else hop_kernel_f2<SIn, SOut, SW, G, RR, false, true><<<grid, threads, 0, st>>>(A);    \
             } else {                                                                                   \

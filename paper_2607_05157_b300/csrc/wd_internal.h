@@ -43,15 +43,17 @@ struct HopArgs {
     const int *act = nullptr;
     int act_stride = 0;
     // fused BiCGStab reductions in the FP32/BF16 stencil epilogue (0: none;
-    // 2: conj(out) . w and |out|^2), block partials to
+    // 1: conj(dot_a) . out; 2: conj(out) . w and |out|^2), block partials to
     // dot_part[(q * nrhs + rhs) * bps + site block], bps = site blocks
     int dot_mode = 0;
+    const void *dot_a = nullptr;
     double *dot_part = nullptr;
 };
 
 // A fused-reduction request for one stencil launch; hop() fills bps
 struct HopDot {
     int mode;
+    const void *a;
     double *part;
     int bps;
 };
