@@ -188,16 +188,12 @@ int hop_err_check(wd_ctx *c) {
 }
 
 int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const void *w, double a, double b,
-        int nrhs, bool dag, const void *w2, double cc, HopDot *dot) {
-    if (dot) dot->bps = 0;                 // 0: not fused (the caller reduces separately)
+        int nrhs, bool dag, const void *w2, double cc) {
     if (nrhs <= 0) return WD_OK;
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
     A.act = c->act; A.act_stride = c->act_stride;
-    // fused reductions: FP32 arithmetic stencil with a same-parity addend only
-    const bool fuse = dot && (pin == P32 || pin == P16) && w != nullptr;
-    if (fuse) { A.dot_mode = dot->mode; A.dot_a = dot->a; A.dot_part = dot->part; }
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
     if (is_dd(pin)) {
@@ -229,14 +225,11 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
         if (s != WD_OK) { prof_end(c, slot); return s; }
     }
     cudaError_t e = launch_hop_any(pin, pout, A, R, dag, th, c->st);
-    if (e == cudaErrorNotSupported) {  // an overridden variant that does not fit this shape
-        th = c->hop_threads[pin];
-        e = launch_hop_any(pin, pout, A, c->hop_R[pin], dag, th, c->st);
-    }
+    if (e == cudaErrorNotSupported)   // an overridden variant that does not fit this shape
+        e = launch_hop_any(pin, pout, A, c->hop_R[pin], dag, c->hop_threads[pin], c->st);
     prof_end(c, slot);
     c->launches++;
     if (e != cudaSuccess) { set_error("hop launch: %s", cudaGetErrorString(e)); return WD_ECUDA; }
-    if (fuse) dot->bps = (c->g.Vh + th - 1) / th;   // one partial per site block
     return WD_OK;
 }
 
@@ -357,7 +350,6 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->hop_err = nullptr;
     c->act = nullptr;
     c->act_stride = 0;
-    c->pending_dot = nullptr;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("wd_create: allocation failed");

@@ -516,96 +516,45 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
     return WD_OK;
 }
 
-// rows[i] = sum of in[i*bps .. i*bps + bps) (fixed tree per row), one block per row
-__global__ void k_fold_rows(const double *in, double *out, int bps) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < bps; i += blockDim.x) a += in[(size_t)blockIdx.x * bps + i];
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (threadIdx.x == 0) out[blockIdx.x] = a;
-    }
-}
-
-// Partials of a reduction fused into the stencil (fused_bps site blocks per
-// RHS in V.fpart): returns the buffer and blocks per RHS the scalar kernels
-// read, folding long rows first so that one thread per RHS sums few values.
-static int fused_partials(wd_ctx *c, BiVecs &V, int nrhs, int nq, int fused_bps, const double **part, int *bpr) {
-    if (fused_bps <= 64) { *part = V.fpart; *bpr = fused_bps; return WD_OK; }
-    k_fold_rows<<<nq * nrhs, 128, 0, c->st>>>(V.fpart, V.part, fused_bps);
-    c->launches++;
-    WD_CUDA(cudaGetLastError());
-    *part = V.part;
-    *bpr = 1;
-    return WD_OK;
-}
-
-// BLAS half after v = A p: alpha = rho / (rh, v), s = r - alpha v.
-// fused_bps > 0: (rh, v) was reduced by the stencil epilogue into V.fpart.
-int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int fused_bps) {
+// BLAS half after v = A p: alpha = rho / (rh, v), s = r - alpha v
+int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
-    const double *part = V.part;
-    int bpr = V.bpr;
-    if (fused_bps > 0) WD_TRY(fused_partials(c, V, nrhs, 2, fused_bps, &part, &bpr));
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        if (fused_bps == 0) {
-            k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr, V.st);
-            c->launches++;
-        }
-        k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, part, nrhs, bpr);
+        k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr, V.st);
+        k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
     }));
-    c->launches += 2;
+    c->launches += 3;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-// BLAS half after t = A s: omega, x and r updates, rho and beta, p update.
-// fused_bps > 0: (t, s) and |t|^2 were reduced by the stencil epilogue.
-int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int fused_bps) {
+// BLAS half after t = A s: omega, x and r updates, rho and beta, p update
+int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     const int sb = (nrhs + 127) / 128;
-    const double *part = V.part;
-    int bpr = V.bpr;
-    if (fused_bps > 0) WD_TRY(fused_partials(c, V, nrhs, 3, fused_bps, &part, &bpr));
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        if (fused_bps == 0) {
-            k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr, V.st);
-            c->launches++;
-        }
-        k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, part, nrhs, bpr);
+        k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr, V.st);
+        k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_xr<SW, SP, FL><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
         k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
         k_bicg_p<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
     }));
-    c->launches += 4;
+    c->launches += 5;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-// The operator may fuse the step's reductions into its last stencil launch
-// (c->pending_dot; bps > 0 on return when it did).
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
-    HopDot dv = {1, V.rh, V.fpart, 0}, dt = {2, nullptr, V.fpart, 0};
-    c->pending_dot = V.fpart ? &dv : nullptr;
-    int s = V.op(c, V.p, V.v, nrhs, V.op_user);        // v = A p   [+ (rh, v)]
-    c->pending_dot = nullptr;
-    WD_TRY(s);
-    WD_TRY(bicg_after_v(c, pw, pp, V, nrhs, dv.bps));
-    c->pending_dot = V.fpart ? &dt : nullptr;
-    s = V.op(c, V.s, V.t, nrhs, V.op_user);            // t = A s   [+ (t, s), |t|^2]
-    c->pending_dot = nullptr;
-    WD_TRY(s);
-    return bicg_after_t(c, pw, pp, V, nrhs, dt.bps);
+    WD_TRY(V.op(c, V.p, V.v, nrhs, V.op_user));       // v = A p
+    WD_TRY(bicg_after_v(c, pw, pp, V, nrhs));
+    WD_TRY(V.op(c, V.s, V.t, nrhs, V.op_user));       // t = A s
+    return bicg_after_t(c, pw, pp, V, nrhs);
 }
 
 }  // namespace wd

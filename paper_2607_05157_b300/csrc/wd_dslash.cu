@@ -285,7 +285,7 @@ __device__ __forceinline__ void hop_dirs_pipelined(const HopArgs &A, int s, int 
 
 // one output site s for RHS tile rb
 template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE = false>
-__device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s, float dots[][3] = nullptr) {
+__device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     const Geom &g = A.g;
     int x, y, z, t;
     eo_coords(g, A.p, s, x, y, z, t);
@@ -324,74 +324,22 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s, flo
         float2 o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = __fmul2_rn(b2, acc[r][k]);
-        float2 wv[12];
         if (A.w) {
+            float2 wv[12];
             load_f2<SW>((const uint4 *)A.w + (size_t)rhs * NW * Vh, Vh, s, wv);
 #pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(a2, wv[k], o[k]);
         }
         if (A.w2) {
-            float2 w2v[12];
-            load_f2<SW>((const uint4 *)A.w2 + (size_t)rhs * NW * Vh, Vh, s, w2v);
+            float2 wv[12];
+            load_f2<SW>((const uint4 *)A.w2 + (size_t)rhs * NW * Vh, Vh, s, wv);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(c2, w2v[k], o[k]);
+            for (int k = 0; k < 12; ++k) o[k] = __ffma2_rn(c2, wv[k], o[k]);
         }
         cx<float> oc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) oc[k] = cmake(o[k].x, o[k].y);
         SIO<SOut>::store((uint4 *)A.out + (size_t)rhs * NO * Vh, Vh, s, oc);
-        // fused BiCGStab reductions of this site (block-reduced by the caller)
-        if (dots && A.dot_mode == 1) {          // conj(a) . out
-            float2 av[12];
-            load_f2<SOut>((const uint4 *)A.dot_a + (size_t)rhs * NO * Vh, Vh, s, av);
-            float re = 0.f, im = 0.f;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                re = fmaf(av[k].x, o[k].x, fmaf(av[k].y, o[k].y, re));
-                im = fmaf(av[k].x, o[k].y, fmaf(-av[k].y, o[k].x, im));
-            }
-            dots[r][0] = re; dots[r][1] = im;
-        } else if (dots && A.dot_mode == 2) {   // conj(out) . w and |out|^2
-            float re = 0.f, im = 0.f, nn = 0.f;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                re = fmaf(o[k].x, wv[k].x, fmaf(o[k].y, wv[k].y, re));
-                im = fmaf(o[k].x, wv[k].y, fmaf(-o[k].y, wv[k].x, im));
-                nn = fmaf(o[k].x, o[k].x, fmaf(o[k].y, o[k].y, nn));
-            }
-            dots[r][0] = re; dots[r][1] = im; dots[r][2] = nn;
-        }
-    }
-}
-
-// Block reduction of the fused dot products: part[(q * nrhs + rhs) * bps + sb],
-// sb the site block, bps = gridDim.x / nrb.  Fixed tree: deterministic.
-template <int R>
-__device__ __forceinline__ void hop_dot_partials(const HopArgs &A, int rb, float dots[][3]) {
-    __shared__ double sh[3 * R][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            double v = (double)dots[r][q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[3 * r + q][wid] = v;
-        }
-    __syncthreads();
-    if (wid == 0) {
-        const int sb = blockIdx.x / A.nrb, bps = gridDim.x / A.nrb;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                double v = lane < nw ? sh[3 * r + q][lane] : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                const int rhs = rb * R + r;
-                if (lane == 0 && rhs < A.nrhs) A.dot_part[((size_t)q * A.nrhs + rhs) * bps + sb] = v;
-            }
     }
 }
 
@@ -399,15 +347,7 @@ template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG,
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (A.dot_mode == 0) {
-        if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s);
-        return;
-    }
-    float dots[R][3];
-#pragma unroll
-    for (int r = 0; r < R; ++r) dots[r][0] = dots[r][1] = dots[r][2] = 0.f;
-    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s, dots);
-    hop_dot_partials<R>(A, rb, dots);
+    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s);
 }
 
 // Persistent batched stencil over several lattices (row a11): one launch walks
@@ -691,7 +631,6 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     if (A.nrhs <= 0) return cudaSuccess;
     // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined; R = 21, 22, 24:
     // timeslices staged through shared memory (FP32 arithmetic only)
-    if (R > 20 && A.dot_mode) R = 2;   // the staged variant has no fused reductions
     if (R > 20) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
     const bool pipe = R > 10;
     if (pipe) R -= 10;

@@ -42,20 +42,6 @@ struct HopArgs {
     // act[r * act_stride] == 0 -- inside a BiCGStab run the converged RHS
     const int *act = nullptr;
     int act_stride = 0;
-    // fused BiCGStab reductions in the FP32/BF16 stencil epilogue (0: none;
-    // 1: conj(dot_a) . out; 2: conj(out) . w and |out|^2), block partials to
-    // dot_part[(q * nrhs + rhs) * bps + site block], bps = site blocks
-    int dot_mode = 0;
-    const void *dot_a = nullptr;
-    double *dot_part = nullptr;
-};
-
-// A fused-reduction request for one stencil launch; hop() fills bps
-struct HopDot {
-    int mode;
-    const void *a;
-    double *part;
-    int bps;
 };
 
 __device__ __forceinline__ bool rhs_on(const HopArgs &A, int rhs) {
@@ -143,7 +129,6 @@ struct wd_ctx {
     int *hop_err;                   // device flag: a staged stencil wait gave up
     const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)
     int act_stride;
-    wd::HopDot *pending_dot;        // reduction a BiCGStab step asks the operator to fuse (nullable)
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
     std::vector<double> last_level2;    // [n2][T][2]
@@ -161,8 +146,7 @@ void prof_end(wd_ctx *c, int slot);
 // Launch one hop on the context's links: out(parity p) = a*w + c*w2 + b*H(in)
 // for inner precision prec; SIn is the input storage, SOut the output storage.
 int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, const void *w,
-        double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0,
-        HopDot *dot = nullptr);
+        double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0);
 
 int hop_err_check(wd_ctx *c);
 
@@ -203,8 +187,6 @@ struct BiVecs {
     void *p, *s;                // operator-input precision (SP)
     BiState *st;
     double *part;               // reduction partials
-    double *fpart;              // partials of reductions fused into the stencil
-    int fpart_bps;              // capacity: site blocks per RHS
     int *count;                 // active count (device)
     int bpr;                    // reduction blocks per RHS
     Space sp;
@@ -214,8 +196,8 @@ struct BiVecs {
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev);
 int bicg_iter(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
-int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int fused_bps = 0);
-int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int fused_bps = 0);
+int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
+int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs);
 int reduction_bpr(long units, int nrhs);
 int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V, const std::string &tag);
 

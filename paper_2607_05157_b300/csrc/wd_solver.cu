@@ -33,15 +33,6 @@ int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V
     V.sp = sp;
     V.bpr = reduction_bpr(sp.units, nrhs);
     WD_TRY(ws_get(c, (t + ".part").c_str(), sizeof(double) * 3 * V.bpr * nrhs, (void **)&V.part));
-    // partials of reductions fused into the fine stencil: one per site block of
-    // at least 64 sites
-    V.fpart = nullptr;
-    V.fpart_bps = 0;
-    if (!sp.flat && pw != P64) {
-        V.fpart_bps = (int)((sp.units + 63) / 64);
-        WD_TRY(ws_get(c, (t + ".fpart").c_str(), sizeof(double) * 3 * (size_t)V.fpart_bps * nrhs,
-                      (void **)&V.fpart));
-    }
     WD_TRY(ws_get(c, (t + ".count").c_str(), sizeof(int), (void **)&V.count));
     return WD_OK;
 }
@@ -181,13 +172,10 @@ struct SchurArgs {
     void *tmp;      // odd-parity field in precision pin
 };
 
-// The second hop carries the reduction a BiCGStab step asked for
-// (c->pending_dot), fused into its epilogue where the stencil supports it.
 static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
     SchurArgs *S = (SchurArgs *)u;
     WD_TRY(hop(c, S->pin, S->pin, 1, S->tmp, in, nullptr, 0.0, 1.0, nrhs));
-    return hop(c, S->pin, S->pout, 0, out, S->tmp, in, 1.0, -c->kappa * c->kappa, nrhs, false, nullptr, 0.0,
-               c->pending_dot);
+    return hop(c, S->pin, S->pout, 0, out, S->tmp, in, 1.0, -c->kappa * c->kappa, nrhs);
 }
 
 // r = b - D_hat x = b - x + k^2 H_eo H_oe x on FP64 fields, with the stencil
