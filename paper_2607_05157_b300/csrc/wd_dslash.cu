@@ -174,8 +174,38 @@ template <typename S> __device__ __forceinline__ void load_f2(const void *p, lon
     for (int k = 0; k < 12; ++k) v[k] = make_float2(t[k].re, t[k].im);
 }
 
-template <typename SIn, typename G, int R, int D, bool DAG>
-__device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int rb, float2 acc[][12]) {
+// Prefetch of the next direction's link and neighbour spinors (PF = 1: into
+// L1, PF = 2: into L2): the loads of direction d+1 are in flight while
+// direction d computes, without holding registers for them.
+template <int PF> __device__ __forceinline__ void prefetch_line(const void *p) {
+    if constexpr (PF == 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    else if constexpr (PF == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <typename SIn, typename G, int R, int D, int PF>
+__device__ __forceinline__ void prefetch_dir(const HopArgs &A, int s, int nb, int rb) {
+    if constexpr (PF != 0 && D < 8) {
+        const long Vh = A.g.Vh;
+        const char *ub = (const char *)A.gauge + ((size_t)D * 9 * Vh + s) * LIO<G>::ELEM;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) prefetch_line<PF>(ub + (size_t)k * Vh * LIO<G>::ELEM);
+        constexpr int NCH = SIO<SIn>::NCH;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int rhs = rb * R + r;
+            if (rhs < A.nrhs) {
+                const uint4 *q = (const uint4 *)A.in + (size_t)rhs * NCH * Vh + nb;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) prefetch_line<PF>(q + (size_t)k * Vh);
+            }
+        }
+    }
+}
+
+template <typename SIn, typename G, int R, int D, bool DAG, int PF = 0>
+__device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int rb, float2 acc[][12],
+                                           int nb_next = 0) {
+    prefetch_dir<SIn, G, R, D + 1, PF>(A, s, nb_next, rb);
     constexpr int MU = D & 3;
     constexpr bool FWD = D < 4;
     constexpr int SIGN = (FWD != DAG) ? -1 : +1;
@@ -284,7 +314,7 @@ __device__ __forceinline__ void hop_dirs_pipelined(const HopArgs &A, int s, int 
 }
 
 // one output site s for RHS tile rb
-template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE = false>
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE = false, int PF = 0>
 __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     const Geom &g = A.g;
     int x, y, z, t;
@@ -303,6 +333,19 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
                            eo_index(g, x, y, z, tp), eo_index(g, xm, y, z, t), eo_index(g, x, ym, z, t),
                            eo_index(g, x, y, zm, t), eo_index(g, x, y, z, tm)};
         hop_dirs_pipelined<SIn, G, R, DAG>(A, s, rb, nb, acc);
+    } else if constexpr (PF != 0) {
+        const int nb[8] = {eo_index(g, xp, y, z, t), eo_index(g, x, yp, z, t), eo_index(g, x, y, zp, t),
+                           eo_index(g, x, y, z, tp), eo_index(g, xm, y, z, t), eo_index(g, x, ym, z, t),
+                           eo_index(g, x, y, zm, t), eo_index(g, x, y, z, tm)};
+        prefetch_dir<SIn, G, R, 0, PF>(A, s, nb[0], rb);
+        hop_dir_f2<SIn, G, R, 0, DAG, PF>(A, s, nb[0], rb, acc, nb[1]);
+        hop_dir_f2<SIn, G, R, 1, DAG, PF>(A, s, nb[1], rb, acc, nb[2]);
+        hop_dir_f2<SIn, G, R, 2, DAG, PF>(A, s, nb[2], rb, acc, nb[3]);
+        hop_dir_f2<SIn, G, R, 3, DAG, PF>(A, s, nb[3], rb, acc, nb[4]);
+        hop_dir_f2<SIn, G, R, 4, DAG, PF>(A, s, nb[4], rb, acc, nb[5]);
+        hop_dir_f2<SIn, G, R, 5, DAG, PF>(A, s, nb[5], rb, acc, nb[6]);
+        hop_dir_f2<SIn, G, R, 6, DAG, PF>(A, s, nb[6], rb, acc, nb[7]);
+        hop_dir_f2<SIn, G, R, 7, DAG, PF>(A, s, nb[7], rb, acc);
     } else {
         hop_dir_f2<SIn, G, R, 0, DAG>(A, s, eo_index(g, xp, y, z, t), rb, acc);
         hop_dir_f2<SIn, G, R, 1, DAG>(A, s, eo_index(g, x, yp, z, t), rb, acc);
@@ -343,11 +386,11 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     }
 }
 
-template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE>
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE, int PF = 0>
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE>(A, rb, s);
+    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE, PF>(A, rb, s);
 }
 
 // Persistent batched stencil over several lattices (row a11): one launch walks
@@ -630,19 +673,32 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     HopArgs A = A0;
     if (A.nrhs <= 0) return cudaSuccess;
     // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined; R = 21, 22, 24:
-    // timeslices staged through shared memory (FP32 arithmetic only)
-    if (R > 20) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
+    // timeslices staged through shared memory (FP32 arithmetic only); R = 31,
+    // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2
+    constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
+    if (R > 20 && R < 30) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
+    int pf = 0;
+    if (R > 30) {
+        if (!PACKED) return cudaErrorNotSupported;
+        pf = R > 40 ? 2 : 1;
+        R -= pf == 2 ? 40 : 30;
+    }
     const bool pipe = R > 10;
     if (pipe) R -= 10;
     if (R != 1 && R != 2 && R != 4) R = 1;
     A.nrb = (A.nrhs + R - 1) / R;
     const int sblocks = (A.g.Vh + threads - 1) / threads;
     dim3 grid((unsigned)(sblocks * A.nrb));
-    constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
 #define WD_HOP_CASE(RR)                                                                                \
     if (R == RR) {                                                                                     \
         if constexpr (PACKED) {                                                                        \
-            if (pipe) {                                                                                \
+            if (pf == 1) {                                                                             \
+                if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, false, 1><<<grid, threads, 0, st>>>(A); \
+                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, false, 1><<<grid, threads, 0, st>>>(A); \
+            } else if (pf == 2) {                                                                      \
+                if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, false, 2><<<grid, threads, 0, st>>>(A); \
+                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, false, 2><<<grid, threads, 0, st>>>(A); \
+            } else if (pipe) {                                                                         \
                 if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, true><<<grid, threads, 0, st>>>(A); \
                 else hop_kernel_f2<SIn, SOut, SW, G, RR, false, true><<<grid, threads, 0, st>>>(A);    \
             } else {                                                                                   \
