@@ -190,12 +190,13 @@ int hop_err_check(wd_ctx *c) {
 }
 
 int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const void *w, double a, double b,
-        int nrhs, bool dag, const void *w2, double cc) {
+        int nrhs, bool dag, const void *w2, double cc, const int *tsup) {
     if (nrhs <= 0) return WD_OK;
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
     A.act = c->act; A.act_stride = c->act_stride;
+    if (is_dd(pin)) A.tsup = tsup;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
     if (is_dd(pin)) {

@@ -11,13 +11,16 @@
 
 namespace wd {
 
-// b_k = unit vector on dof (x0, k), k = 0..11, as FP64 eo fields (zeroed by the caller)
-__global__ void k_point_sources(double *be, double *bo, Geom g, int site0) {
+// b_k = unit vector on dof (x0, k), k = 0..11, as FP64 eo fields (zeroed by the
+// caller); tsup[k] = the source timeslice (the Schur-source stencil skips the
+// timeslices the source cannot reach)
+__global__ void k_point_sources(double *be, double *bo, Geom g, int site0, int *tsup) {
     const int k = threadIdx.x;
     if (k >= 12) return;
     int x = site0 % g.X, r = site0 / g.X;
     int y = r % g.Y; r /= g.Y;
     int z = r % g.Z, t = r / g.Z;
+    tsup[k] = t;
     const int p = (x + y + z + t) & 1, s = site0 >> 1;
     double2 *f = (double2 *)(p ? bo : be) + (size_t)k * 12 * g.Vh;
     f[(size_t)k * g.Vh + s] = make_double2(1.0, 0.0);
@@ -72,6 +75,8 @@ extern "C" int wd_point_correlator(wd_ctx *c, const int src[4], int prec, double
     const int nr = 12;
     const size_t f = field_bytes(g, P64, nr);
     double *be, *bo, *xe, *xo, *part, *Cd;
+    int *tsup;
+    WD_TRY(ws_get(c, "pc.tsup", sizeof(int) * nr, (void **)&tsup));
     WD_TRY(ws_get(c, "pc.be", f, (void **)&be));
     WD_TRY(ws_get(c, "pc.bo", f, (void **)&bo));
     WD_TRY(ws_get(c, "pc.xe", f, (void **)&xe));
@@ -82,10 +87,10 @@ extern "C" int wd_point_correlator(wd_ctx *c, const int src[4], int prec, double
     WD_TRY(ws_get(c, "pc.C", sizeof(double) * g.T, (void **)&Cd));
     WD_TRY(blas_zero(c, be, f));
     WD_TRY(blas_zero(c, bo, f));
-    k_point_sources<<<1, 32, 0, c->st>>>(be, bo, g, site0);
+    k_point_sources<<<1, 32, 0, c->st>>>(be, bo, g, site0, tsup);
     c->launches++;
     WD_CUDA(cudaGetLastError());
-    int s = solve_eo(c, be, bo, xe, xo, nr, tol, prec, 100000, nullptr, nullptr);
+    int s = solve_eo(c, be, bo, xe, xo, nr, tol, prec, 100000, nullptr, nullptr, tsup);
     if (s != WD_OK) return s;
     k_norm_timeslice<<<dim3(bps, nr, g.T), 256, 0, c->st>>>(g, xe, xo, part, bps);
     k_sum_correlator<<<(g.T + 127) / 128, 128, 0, c->st>>>(part, nr, g.T, bps, Cd);

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int rhs = rb * R + r;
-            if (rhs < A.nrhs && rhs_on(A, rhs)) {
+            if (rhs < A.nrhs && rhs_on(A, rhs) && hop_reaches(A, rhs, t)) {
                 cx<dd> psi[12], h[6], uh[6];
                 load_dd((const double2 *)A.in + (size_t)rhs * 12 * Vh, Vh, nb, psi);
                 project_dir<DAG>(d, psi, h);
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(128) hop_kernel_ddz(HopArgs A) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int rhs = rb * R + r;
-            if (rhs < A.nrhs && rhs_on(A, rhs)) {
+            if (rhs < A.nrhs && rhs_on(A, rhs) && hop_reaches(A, rhs, t)) {
                 zdd psi[12], h[6], uh[6];
                 const float4 *q = (const float4 *)A.in + (size_t)rhs * 12 * Vh + nb;
 #pragma unroll

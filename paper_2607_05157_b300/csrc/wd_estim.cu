@@ -149,6 +149,97 @@ __global__ void k_contract(EstParams P, Geom g, const double *xe, const double *
     }
 }
 
+// Support timeslice of each RHS of the batch (-1: all timeslices), for the
+// stencil of the Schur source
+__global__ void k_tsup(EstParams P, int *tsup) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < P.nrhs) tsup[r] = describe(P, P.g0 + r).tslice;
+}
+
+// B = gamma5 with time dilution: every RHS eta lives on one timeslice t0 and
+// X(t0) = eta^dag g5 x over both parities.  With x_o = eta_o + k H_oe x_e and
+// the gamma5-hermiticity H_oe^dag g5 = g5 H_eo of the hop,
+//   eta_o^dag g5 x_o = eta_o^dag g5 eta_o + k (H_eo eta_o)^dag g5 x_e,
+// and k H_eo eta_o = bhat_e - eta_e, so
+//   X(t0) = bhat_e^dag g5 x_e + eta_o^dag g5 eta_o
+// (exact algebra: the odd solution is never formed).  bhat_e lives on the
+// timeslices t0 - 1, t0, t0 + 1.  grid (bps, nrhs, 3), z = t - t0 + 1;
+// part[((rhs*3 + z)*bps + bx)*2 + {re,im}]
+__global__ void k_contract_schur(EstParams P, Geom g, const double *bhat, const double *xe, double *part, int bps) {
+    const int r = blockIdx.y, z3 = blockIdx.z;
+    const RhsDesc d = describe(P, P.g0 + r);
+    const int T = g.T;
+    const int t = (d.tslice + z3 - 1 + T) % T;
+    const int slice = g.Vh / T;            // half-sites per timeslice and parity
+    double are = 0.0, aim = 0.0;
+    if (!(T == 2 && z3 == 2)) {            // T = 2: t0 - 1 and t0 + 1 coincide
+        const int chunk = (slice + bps - 1) / bps;
+        const int u0 = blockIdx.x * chunk, u1 = min(u0 + chunk, slice);
+        for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+            const int s = t * slice + u;
+            cx<double> bv[12], xv[12];
+            SIO<double>::load((const uint4 *)bhat + (size_t)r * 12 * g.Vh, g.Vh, s, bv);
+            SIO<double>::load((const uint4 *)xe + (size_t)r * 12 * g.Vh, g.Vh, s, xv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const double sg = k >= 6 ? -1.0 : 1.0;
+                are += sg * (bv[k].re * xv[k].re + bv[k].im * xv[k].im);
+                aim += sg * (bv[k].re * xv[k].im - bv[k].im * xv[k].re);
+            }
+            if (z3 == 1) {                 // eta_o^dag g5 eta_o on the odd sites of t0
+                int x, y, zz, tt;
+                eo_coords(g, 1, s, x, y, zz, tt);
+                cx<double> v[12];
+                if (site_noise(P, g, d, x, y, zz, tt, v)) {
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) are += (k >= 6 ? -1.0 : 1.0) * v[k].re * v[k].re;
+                }
+            }
+        }
+    }
+    __shared__ double sh[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_xor_sync(0xffffffffu, are, o);
+        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { sh[0][wid] = are; sh[1][wid] = aim; }
+    __syncthreads();
+    if (wid == 0) {
+        are = lane < nw ? sh[0][lane] : 0.0;
+        aim = lane < nw ? sh[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            are += __shfl_xor_sync(0xffffffffu, are, o);
+            aim += __shfl_xor_sync(0xffffffffu, aim, o);
+        }
+        if (lane == 0) {
+            double *q = part + (((size_t)r * 3 + z3) * bps + blockIdx.x) * 2;
+            q[0] = are;
+            q[1] = aim;
+        }
+    }
+}
+
+// X[sample][t] += sum over this batch's RHS of that sample on timeslice t of
+// their k_contract_schur partials (fixed order)
+__global__ void k_accumulate_schur(EstParams P, int T, const double *part, int bps, double *X, int first_sample,
+                                   int nsamples) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nsamples * T) return;
+    const int si = first_sample + idx / T, t = idx % T;
+    const int a = max(P.g0, si * P.m), b = min(P.g0 + P.nrhs, (si + 1) * P.m);
+    double re = 0.0, im = 0.0;
+    for (int gidx = a; gidx < b; ++gidx) {
+        if (describe(P, gidx).tslice != t) continue;
+        const double *q = part + (size_t)(gidx - P.g0) * 3 * bps * 2;
+        for (int k = 0; k < 3 * bps; ++k) { re += q[2 * k]; im += q[2 * k + 1]; }
+    }
+    X[((size_t)si * T + t) * 2] += re;
+    X[((size_t)si * T + t) * 2 + 1] += im;
+}
+
 // X[sample][t] += sum over this batch's RHS of that sample (fixed order)
 __global__ void k_accumulate(EstParams P, int T, const double *part, int bps, double *X, int first_sample,
                              int nsamples) {
@@ -208,17 +299,35 @@ int estimate_rhs_range(wd_ctx *c, EstParams P, int total, int batch, double tol,
         const int slice2 = 2 * (g.Vh / T);
         int bps = (slice2 + 1023) / 1024;
         if (bps < 1) bps = 1;
-        WD_TRY(ws_get(c, "est.part", sizeof(double) * 2 * (size_t)nb * T * bps, (void **)&part));
+        WD_TRY(ws_get(c, "est.part", sizeof(double) * 2 * (size_t)nb * (T > 3 ? T : 3) * bps, (void **)&part));
         const long n = (long)g.V * nb;
         k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, g, be, bo);
         c->launches++;
         WD_CUDA(cudaGetLastError());
-        int s = solve_eo(c, be, bo, xe, xo, nb, tol, prec, 100000, nullptr, nullptr);
+        // time dilution: each source lives on one timeslice (the Schur-source
+        // stencil skips the sites it cannot reach); with B = gamma5 the
+        // contraction uses bhat and the even solution only (k_contract_schur)
+        int *tsup = nullptr;
+        if (P.TT > 1) {
+            WD_TRY(ws_get(c, "est.tsup", sizeof(int) * (size_t)nb, (void **)&tsup));
+            k_tsup<<<(nb + 127) / 128, 128, 0, c->st>>>(P, tsup);
+            c->launches++;
+            WD_CUDA(cudaGetLastError());
+        }
+        const bool schur = P.TT > 1 && P.gamma5;
+        const double *bhat = nullptr;
+        int s = solve_eo(c, be, bo, xe, schur ? nullptr : xo, nb, tol, prec, 100000, nullptr, nullptr, tsup, &bhat);
         if (s != WD_OK) return s;
-        k_contract<<<dim3(bps, nb, T), 256, 0, c->st>>>(P, g, xe, xo, part, bps);
         const int s_first = g0 / P.m, s_last = (g0 + nb - 1) / P.m;
         const int ns = s_last - s_first + 1;
-        k_accumulate<<<(ns * T + 127) / 128, 128, 0, c->st>>>(P, T, part, bps, X, s_first, ns);
+        if (schur) {
+            const int bps1 = ((g.Vh / T) + 1023) / 1024;
+            k_contract_schur<<<dim3(bps1, nb, 3), 256, 0, c->st>>>(P, g, bhat, xe, part, bps1);
+            k_accumulate_schur<<<(ns * T + 127) / 128, 128, 0, c->st>>>(P, T, part, bps1, X, s_first, ns);
+        } else {
+            k_contract<<<dim3(bps, nb, T), 256, 0, c->st>>>(P, g, xe, xo, part, bps);
+            k_accumulate<<<(ns * T + 127) / 128, 128, 0, c->st>>>(P, T, part, bps, X, s_first, ns);
+        }
         c->launches += 2;
         WD_CUDA(cudaGetLastError());
         *nsolves += nb;

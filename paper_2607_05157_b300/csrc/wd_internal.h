@@ -42,7 +42,20 @@ struct HopArgs {
     // act[r * act_stride] == 0 -- inside a BiCGStab run the converged RHS
     const int *act = nullptr;
     int act_stride = 0;
+    // timeslice that holds the whole input of each RHS (nullable; entry -1:
+    // anywhere): output sites more than one timeslice away get no hop term
+    // (double-float stencil only; time-diluted and point sources)
+    const int *tsup = nullptr;
 };
+
+// true if the hop can reach output timeslice t from RHS rhs's input support
+__device__ __forceinline__ bool hop_reaches(const HopArgs &A, int rhs, int t) {
+    if (A.tsup == nullptr) return true;
+    const int t0 = __ldg(A.tsup + rhs);
+    if (t0 < 0) return true;
+    const int dt = t > t0 ? t - t0 : t0 - t;
+    return dt <= 1 || dt == A.g.T - 1;
+}
 
 __device__ __forceinline__ bool rhs_on(const HopArgs &A, int rhs) {
     return A.act == nullptr || __ldg(A.act + (size_t)rhs * A.act_stride) != 0;
@@ -146,7 +159,8 @@ void prof_end(wd_ctx *c, int slot);
 // Launch one hop on the context's links: out(parity p) = a*w + c*w2 + b*H(in)
 // for inner precision prec; SIn is the input storage, SOut the output storage.
 int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, const void *w,
-        double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0);
+        double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0,
+        const int *tsup = nullptr);
 
 int hop_err_check(wd_ctx *c);
 
@@ -155,8 +169,13 @@ int user_to_eo(wd_ctx *c, const void *user, bool user_double, int prec, void *ev
 int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *user, bool user_double, int nrhs);
 
 // Solver core on eo fields (wd_solver.cu).  b: FP64 eo [2 parities] fields.
+// src_tsup (device [nrhs], nullable): timeslice holding each RHS's source
+// (-1: anywhere).  x_odd nullable: no odd-site reconstruction (then
+// resid_out must be null); bhat_out: the Schur source b_e + k H_eo b_o
+// (a workspace of the context, valid until the next solve).
 int solve_eo(wd_ctx *c, const double *b_even, const double *b_odd, double *x_even, double *x_odd, int nrhs,
-             double tol, int prec, int max_iter, int *iters_out, double *resid_out);
+             double tol, int prec, int max_iter, int *iters_out, double *resid_out, const int *src_tsup = nullptr,
+             const double **bhat_out = nullptr);
 
 // blas (wd_blas.cu)
 // A vector space for BLAS-1: `units` 12-complex units per right-hand side, in

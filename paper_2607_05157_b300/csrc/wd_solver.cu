@@ -189,8 +189,10 @@ static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, i
 }
 
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
-             int prec, int max_iter, int *iters_out, double *resid_out) {
+             int prec, int max_iter, int *iters_out, double *resid_out, const int *src_tsup,
+             const double **bhat_out) {
     if (nrhs <= 0) return WD_OK;
+    if (!x_o && resid_out) { set_error("solve: the true residual needs the odd sites"); return WD_EINVAL; }
     const double k = c->kappa;
     const Space sp = fine_space(c->g);
     const size_t f64 = field_bytes(c->g, P64, nrhs);
@@ -213,7 +215,8 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     // FP64 arithmetic).
     const int pd = prec == P64 || tol < 1e-12 ? P64 : c->outer;
     // b_hat = b_e + k H_eo b_o                                         (a3)
-    WD_TRY(hop(c, pd, pd, 0, bhat, b_o, b_e, 1.0, k, nrhs));
+    WD_TRY(hop(c, pd, pd, 0, bhat, b_o, b_e, 1.0, k, nrhs, false, nullptr, 0.0, src_tsup));
+    if (bhat_out) *bhat_out = bhat;
 
     const int pp = prec == P16 ? P16 : (prec == P32 ? P32 : P64);
     void *tmplo = nullptr;
@@ -230,7 +233,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     int status = dc_solve(c, P, bhat, x_e, nrhs, bn2 + 2 * nrhs, bnorm2, tol, prec, max_iter, iters, last_rn2);
     if (status != WD_OK && status != WD_ENOCONV && status != WD_EBREAKDOWN) return status;
     // x_o = b_o + k H_oe x_e                                             (a7)
-    WD_TRY(hop(c, pd, pd, 1, x_o, x_e, b_o, 1.0, k, nrhs));
+    if (x_o) WD_TRY(hop(c, pd, pd, 1, x_o, x_e, b_o, 1.0, k, nrhs));
     // True FP64 residual of the full system, when asked for.  Without it the
     // last FP64 Schur residual (mixed modes) or the FP64 recursion (FP64 mode)
     // certifies convergence: the full residual of (x_e, x_o) equals the Schur

@@ -121,3 +121,50 @@ def test_probing_16x16x16x32_full_size():
     ref = estimators.probing(_oracle_solve(U, 0.13, shape), dims, 2003, 1, True, col, nc, 1)
     _close(r['samples'], ref)
     ctx.close()
+
+
+def _diluted_reference(Dinv, dims, seed, N, gamma5, col, nc, dil):
+    """X_i(t) of time dilution combined with colour x spin-colour dilution,
+    composed from the oracle's noise, masks and contraction: the RHS of
+    sample i are eta_i masked to (colour, component, timeslice t0)."""
+    from oracle import noise
+    n = 12 * int(np.prod(dims))
+    ts = wilson.timeslice_of_dof(dims)
+    masks = estimators.probing_masks(col, nc, dil)
+    out = np.zeros((N, dims[3]), np.complex128)
+    for i in range(N):
+        eta = noise.rademacher(seed, i, n)
+        for m in masks:
+            for t0 in range(dims[3]):
+                v = np.where(m & (ts == t0), eta, 0).astype(complex)
+                out[i] += estimators.contract(v, Dinv @ v, dims, gamma5)
+    return out
+
+
+@pytest.mark.parametrize("dims,method,d,dil,op", [
+    ((2, 4, 4, 2), 0, 0, 1, 1),      # T = 2: the Schur source reaches both timeslices
+    ((4, 4, 4, 4), 1, 1, 12, 1),     # probing x spin-colour x time dilution, gamma5
+    ((2, 4, 6, 4), 1, 2, 1, 0),      # B = 1: the full contraction with the odd solution
+    ((4, 2, 2, 6), 0, 0, 12, 1),     # Hutchinson x spin-colour x time dilution
+])
+def test_time_diluted_variants(dims, method, d, dil, op):
+    """Time dilution in every combination the estimator supports. With
+    B = gamma5 the contraction uses the Schur source and the even solution
+    only (X(t0) = bhat^dag g5 x_e + eta_o^dag g5 eta_o); the Schur-source
+    stencil skips timeslices the source cannot reach. Per-sample values
+    against the oracle's dense inverse."""
+    from paper_2607_05157_b300 import Context, trace_estimate, WD_DIL_TIME
+    U = synth.gauge_field(dims, 0.5, 31)
+    Dinv = solver.dense_inverse(wilson.sparse_matrix(U, 0.125, BC))
+    if method == 1:
+        nc, sigma = coloring.search(dims, d)
+        col = coloring.colors(dims, sigma, nc)
+    else:
+        nc, col = 1, np.zeros(int(np.prod(dims)), np.int64)
+    ctx = Context(dims, U, 0.125, BC)
+    r = trace_estimate(ctx.h, method, dil | WD_DIL_TIME, 2, dims[3], d=d, seed=55, op=op, prec=1, tol=1e-12,
+                       batch=13, with_samples=True)
+    ref = _diluted_reference(Dinv, dims, 55, 2, bool(op), col, nc, dil)
+    _close(r['samples'], ref)
+    assert r['n_solves'] == 2 * nc * dil * dims[3]
+    ctx.close()
