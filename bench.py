@@ -111,16 +111,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def hop_traffic(prec):
-    """DRAM bytes per stencil launch from the committed ncu summary, if it was
-    taken on the current stencil source (else None)."""
+def hop_traffic(prec, alg_bytes_per_launch):
+    """DRAM bytes per stencil launch: the committed ncu summary's DRAM bytes per
+    algorithmic byte (taken on 256-RHS launches of the same workload) times this
+    run's algorithmic bytes per launch, if the summary was taken on the current
+    stencil source (else None)."""
     try:
         rec = json.load(open(os.path.join(ROOT, 'profiles', 'hop_traffic.json')))
         csrc = os.path.join(ROOT, 'paper_2607_05157_b300', 'csrc')
         src = b''.join(open(os.path.join(csrc, f), 'rb').read() for f in ('wd_dslash.cu', 'wd_spin.cuh'))
         if rec.get('source_sha256') != hashlib.sha256(src).hexdigest():
             return None
-        return rec.get(prec, {}).get('dram_bytes_per_launch')
+        r = rec.get(prec, {}).get('dram_bytes_per_algorithmic_byte')
+        return r * alg_bytes_per_launch if r is not None else None
     except Exception:
         return None
 
@@ -377,7 +380,7 @@ def main():
     peak = peaks['hbm_gbs'] if peaks else 6400.0
     achieved = (by_hop / n_hop) / (ms_hop / n_hop * 1e-3) / 1e9 if n_hop else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": hop_traffic(args.prec),
+            "frac": achieved / peak if achieved else None, "traffic": hop_traffic(args.prec, by_hop / max(n_hop, 1)),
             "kernel": f"hop_kernel ({args.prec} storage, {n_hop // max(args.steps, 1)} launches/step, "
                       f"{by_hop / max(n_hop, 1) / 1e6:.1f} MB algorithmic per launch)",
             "peak_source": "measured" if peaks else "fallback",
