@@ -353,6 +353,9 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->hop_err = nullptr;
     c->act = nullptr;
     c->act_stride = 0;
+    c->gst = nullptr;
+    c->loop_dev = nullptr;
+    c->graph_off = false;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("wd_create: allocation failed");
@@ -388,11 +391,13 @@ extern "C" int wd_update_gauge(wd_ctx *c, const double *gauge, double kappa) {
 }
 
 void wd_mg_free(wd_ctx *c);
+namespace wd { void wd_loops_free(wd_ctx *c); }
 
 extern "C" int wd_destroy(wd_ctx *c) {
     if (!c) return WD_OK;
     cudaStreamSynchronize(c->st);
     wd_mg_free(c);
+    wd_loops_free(c);
     for (int p = 0; p < 3; ++p) if (c->gauge[p]) cudaFree(c->gauge[p]);
     if (c->gauge_lo) cudaFree(c->gauge_lo);
     if (c->hop_err) cudaFree(c->hop_err);

@@ -109,6 +109,15 @@ struct wd_prof_rec {
     double bytes;
 };
 
+// A BiCGStab loop captured as a CUDA graph (wd_solver.cu): a conditional
+// while node around two iterations, keyed by everything its kernels see
+struct wd_loop_graph {
+    std::vector<uintptr_t> key;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int kernels;                    // kernel launches per body (two iterations + condition)
+};
+
 // multigrid state (wd_mg.cu)
 struct wd_mg {
     int nv, ncd;
@@ -142,6 +151,10 @@ struct wd_ctx {
     int *hop_err;                   // device flag: a staged stencil wait gave up
     const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)
     int act_stride;
+    std::vector<wd_loop_graph> loops;   // captured BiCGStab loops (most recent last)
+    cudaStream_t gst;               // capture stream of those graphs
+    int *loop_dev;                  // [iterations run, iteration limit] of a graph launch
+    bool graph_off;                 // a graph call failed: plain loops from then on
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
     std::vector<double> last_level2;    // [n2][T][2]
@@ -211,6 +224,10 @@ struct BiVecs {
     Space sp;
     OpFn op;
     void *op_user;
+    // the operator's launches may be captured in a graph; sig: what of
+    // op_user its kernels see (precisions, workspace), part of the graph key
+    bool graph_ok = false;
+    uintptr_t sig[3] = {0, 0, 0};
 };
 int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, double tol_rel,
               const double *bnorm2_dev);
@@ -228,6 +245,8 @@ struct Problem {
     OpFn oplo;  void *ulo;      // inner operator, inputs in pp, outputs in pw
     ResFn res64; void *ures;    // FP64 residual
     const char *tag;            // workspace name prefix
+    bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
+    uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};
 };
 int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
              const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,

@@ -14,6 +14,9 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
+#include <functional>
+#include <string>
 #include <vector>
 
 #include "wd_internal.h"
@@ -37,11 +40,135 @@ int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V
     return WD_OK;
 }
 
-// Run BiCGStab iterations until no RHS is active or max_iter is reached.  The
-// host reads the active count every second iteration; in between, every
-// kernel of an iteration (stencil and BLAS) skips the RHS that have converged
-// (the stencil through the activity mask set here), so an iteration issued
-// after the last RHS converged costs only its launches.
+// ---- the BiCGStab loop on the device: a CUDA graph with a while node ------
+// The body is two iterations (every kernel skips converged RHS) and a one-
+// thread kernel that counts them and keeps the loop going while some RHS is
+// active and the iteration limit is not reached.  The host launches the graph
+// once per inner solve and reads the count back once; no launch latency and
+// no host round trip per iteration.  The loop always ends: the count grows by
+// two per body and the limit is finite.
+__global__ void k_bicg_while(cudaGraphConditionalHandle h, const int *count, int *loop) {
+    const int it = loop[0] + 2;
+    loop[0] = it;
+    cudaGraphSetConditional(h, (*count > 0 && it + 2 <= loop[1]) ? 1u : 0u);
+}
+
+static std::vector<uintptr_t> loop_key(wd_ctx *c, int pw, int pp, const BiVecs &V, int nrhs) {
+    uint64_t kb;
+    memcpy(&kb, &c->kappa, sizeof(kb));
+    const char *ov = getenv("WD_HOP_R");
+    return {(uintptr_t)V.x, (uintptr_t)V.r, (uintptr_t)V.rh, (uintptr_t)V.v, (uintptr_t)V.t, (uintptr_t)V.p,
+            (uintptr_t)V.s, (uintptr_t)V.st, (uintptr_t)V.part, (uintptr_t)V.count, (uintptr_t)V.op,
+            V.sig[0], V.sig[1], V.sig[2], (uintptr_t)nrhs, (uintptr_t)pw, (uintptr_t)pp, (uintptr_t)V.bpr,
+            (uintptr_t)V.sp.units, (uintptr_t)kb, (uintptr_t)std::hash<std::string>()(ov ? ov : "")};
+}
+
+static void loop_graph_free(wd_loop_graph &L) {
+    if (L.exec) cudaGraphExecDestroy(L.exec);
+    if (L.graph) cudaGraphDestroy(L.graph);
+    L.exec = nullptr;
+    L.graph = nullptr;
+}
+
+void wd_loops_free(wd_ctx *c) {
+    for (auto &L : c->loops) loop_graph_free(L);
+    c->loops.clear();
+    if (c->gst) cudaStreamDestroy(c->gst);
+    if (c->loop_dev) cudaFree(c->loop_dev);
+    c->gst = nullptr;
+    c->loop_dev = nullptr;
+}
+
+// Capture two iterations of V's loop into a while-node graph.  Returns false
+// (and switches graphs off for this context) if the runtime refuses any step.
+static bool loop_graph_build(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, wd_loop_graph &L) {
+    L.graph = nullptr;
+    L.exec = nullptr;
+    bool ok = true;
+    if (!c->gst) ok = cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && !c->loop_dev) ok = cudaMalloc(&c->loop_dev, 2 * sizeof(int)) == cudaSuccess;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraph_t body = nullptr;
+    if (ok) ok = cudaGraphCreate(&L.graph, 0) == cudaSuccess;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, L.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, L.graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+        if (ok) body = np.conditional.phGraph_out[0];
+    }
+    if (ok) ok = cudaStreamBeginCaptureToGraph(c->gst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+                 cudaSuccess;
+    if (ok) {
+        cudaStream_t saved = c->st;
+        const int64_t l0 = c->launches;
+        c->st = c->gst;
+        int s = bicg_iter(c, pw, pp, V, nrhs);
+        if (s == WD_OK) s = bicg_iter(c, pw, pp, V, nrhs);
+        if (s == WD_OK) k_bicg_while<<<1, 1, 0, c->gst>>>(h, V.count, c->loop_dev);
+        c->st = saved;
+        L.kernels = (int)(c->launches - l0) + 1;
+        c->launches = l0;                 // captured, not run
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->gst, &out);
+        ok = s == WD_OK && e == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&L.exec, L.graph, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        loop_graph_free(L);
+        c->graph_off = true;
+        if (getenv("WD_VERBOSE")) fprintf(stderr, "[wd] BiCGStab loop graph refused: plain loops from now on\n");
+    }
+    return ok;
+}
+
+// Run up to max_more iterations (an even number, >= 2) on the device; *done =
+// iterations run.  *used = false if graphs are unavailable (nothing ran).
+static int loop_graph_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_more, int *done, bool *used) {
+    *used = false;
+    *done = 0;
+    const std::vector<uintptr_t> key = loop_key(c, pw, pp, V, nrhs);
+    wd_loop_graph *L = nullptr;
+    for (auto &g : c->loops)
+        if (g.key == key) L = &g;
+    if (!L) {
+        wd_loop_graph G;
+        if (!loop_graph_build(c, pw, pp, V, nrhs, G)) return WD_OK;
+        G.key = key;
+        if (c->loops.size() >= 16) {      // keep the cache small
+            loop_graph_free(c->loops.front());
+            c->loops.erase(c->loops.begin());
+        }
+        c->loops.push_back(G);
+        L = &c->loops.back();
+    }
+    int *h;
+    WD_TRY(hws_get(c, "loop", 2 * sizeof(int), (void **)&h));
+    h[0] = 0;
+    h[1] = max_more;
+    WD_CUDA(cudaMemcpyAsync(c->loop_dev, h, 2 * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    WD_CUDA(cudaGraphLaunch(L->exec, c->st));
+    WD_CUDA(cudaMemcpyAsync(h, c->loop_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    *done = h[0];
+    *used = true;
+    c->launches += (int64_t)L->kernels * (h[0] / 2) + 1;
+    return WD_OK;
+}
+
+// Run BiCGStab iterations until no RHS is active or max_iter is reached.
+// Every kernel of an iteration (stencil and BLAS) skips the RHS that have
+// converged (the stencil through the activity mask set here).  The first two
+// iterations run as plain launches (they tune the stencil shapes and touch
+// every workspace); the rest run inside a captured graph whose while node
+// checks convergence on the device, or -- when profiling with per-launch
+// events, with WD_NO_GRAPH set, or if the runtime refuses the graph -- as
+// plain launches with the host reading the active count every second
+// iteration.
 static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter, int *ran) {
     int *hcount;
     WD_TRY(hws_get(c, "count", sizeof(int), (void **)&hcount));
@@ -55,8 +182,24 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
     } guard{c};
     c->act = &V.st[0].active;
     c->act_stride = (int)(sizeof(BiState) / sizeof(int));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->st, &cs);
+    const bool graphs = V.graph_ok && !c->prof && !c->graph_off && cs == cudaStreamCaptureStatusNone &&
+                        getenv("WD_NO_GRAPH") == nullptr;
     const int check = 2;
     while (active > 0 && it < max_iter) {
+        if (graphs && it >= 2 && max_iter - it >= 2 && !c->graph_off) {
+            int done = 0;
+            bool used = false;
+            WD_TRY(loop_graph_run(c, pw, pp, V, nrhs, (max_iter - it) & ~1, &done, &used));
+            if (used) {
+                it += done;
+                WD_CUDA(cudaMemcpyAsync(hcount, V.count, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+                WD_CUDA(cudaStreamSynchronize(c->st));
+                active = *hcount;
+                continue;
+            }
+        }
         int k = check < max_iter - it ? check : max_iter - it;
         for (int i = 0; i < k; ++i) WD_TRY(bicg_iter(c, pw, pp, V, nrhs));
         it += k;
@@ -89,6 +232,8 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
         WD_TRY(alloc_bivecs(c, P.sp, P64, P64, nrhs, V, tag + ".bi64"));
         V.op = P.op64;
         V.op_user = P.u64;
+        V.graph_ok = P.graph_ok;
+        for (int q = 0; q < 3; ++q) V.sig[q] = P.sig64[q];
         // the recursive residual drifts from the true one: aim at half the tolerance
         WD_TRY(bicg_init(c, P64, P64, V, b, nrhs, 0.5 * tol, bnorm2_dev));
         int ran = 0;
@@ -110,6 +255,8 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
     WD_TRY(alloc_bivecs(c, P.sp, pw, pp, nrhs, V, tag + (prec == P32 ? ".bi32" : ".bi16")));
     V.op = P.oplo;
     V.op_user = P.ulo;
+    V.graph_ok = P.graph_ok;
+    for (int q = 0; q < 3; ++q) V.sig[q] = P.siglo[q];
     double *r64, *scale_d, *rn2_d, *blo, *hsc;
     WD_TRY(ws_get(c, (tag + ".r64").c_str(), f64, (void **)&r64));
     WD_TRY(ws_get(c, (tag + ".blo").c_str(), space_bytes(P.sp, pw, nrhs), (void **)&blo));
@@ -228,6 +375,10 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     P.oplo = schur_op; P.ulo = &slo;
     P.res64 = schur_res64; P.ures = &sres;
     P.tag = "fine";
+    // the Schur operator's launches see the precisions and the odd workspace
+    P.graph_ok = true;
+    P.sig64[0] = s64.pin; P.sig64[1] = s64.pout; P.sig64[2] = (uintptr_t)s64.tmp;
+    P.siglo[0] = slo.pin; P.siglo[1] = slo.pout; P.siglo[2] = (uintptr_t)slo.tmp;
     std::vector<int> iters;
     std::vector<double> last_rn2;
     int status = dc_solve(c, P, bhat, x_e, nrhs, bn2 + 2 * nrhs, bnorm2, tol, prec, max_iter, iters, last_rn2);
