@@ -205,10 +205,13 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     } else {
         A.gauge = gauge_parity(c, pin, p);
     }
-    // algorithmic bytes: nrhs x (in + out [+ w + w2]) spinors + 8 links per output site
+    // algorithmic bytes: (in + out [+ w + w2]) spinors per RHS that does work
+    // (inside a BiCGStab run: the RHS active at the last host check) + 8 links
+    // per output site
     const double sb_in = spinor_bytes(pin), sb_out = spinor_bytes(pout);
+    const int nwork = c->act && c->act_count >= 0 && c->act_count < nrhs ? c->act_count : nrhs;
     const double bytes = (double)c->g.Vh *
-                         (nrhs * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
+                         (nwork * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
     prof_begin(c, pin == P64 || is_dd(pin) ? WD_K_HOP64 : WD_K_HOP, bytes, &slot);
     if (pin == PDD) {
@@ -356,6 +359,7 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->gst = nullptr;
     c->loop_dev = nullptr;
     c->graph_off = false;
+    c->act_count = -1;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("wd_create: allocation failed");

@@ -151,6 +151,7 @@ struct wd_ctx {
     int *hop_err;                   // device flag: a staged stencil wait gave up
     const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)
     int act_stride;
+    int act_count;                  // RHS active at the last host check (-1: unknown), for profiled bytes
     std::vector<wd_loop_graph> loops;   // captured BiCGStab loops (most recent last)
     cudaStream_t gst;               // capture stream of those graphs
     int *loop_dev;                  // [iterations run, iteration limit] of a graph launch

@@ -178,15 +178,18 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
     int active = *hcount;
     struct MaskGuard {
         wd_ctx *c;
-        ~MaskGuard() { c->act = nullptr; c->act_stride = 0; }
+        ~MaskGuard() { c->act = nullptr; c->act_stride = 0; c->act_count = -1; }
     } guard{c};
     c->act = &V.st[0].active;
     c->act_stride = (int)(sizeof(BiState) / sizeof(int));
+    c->act_count = active;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(c->st, &cs);
     const bool graphs = V.graph_ok && !c->prof && !c->graph_off && cs == cudaStreamCaptureStatusNone &&
                         getenv("WD_NO_GRAPH") == nullptr;
-    const int check = 2;
+    // profiling: check after every iteration, so that the stencil's recorded
+    // bytes count exactly the RHS that still work
+    const int check = c->prof ? 1 : 2;
     while (active > 0 && it < max_iter) {
         if (graphs && it >= 2 && max_iter - it >= 2 && !c->graph_off) {
             int done = 0;
@@ -206,6 +209,7 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
         WD_CUDA(cudaMemcpyAsync(hcount, V.count, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         WD_CUDA(cudaStreamSynchronize(c->st));
         active = *hcount;
+        c->act_count = active;
     }
     *ran = it;
     return WD_OK;
