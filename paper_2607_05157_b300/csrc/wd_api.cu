@@ -195,7 +195,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
-    A.act = c->act; A.act_stride = c->act_stride;
+    A.alist = c->alist; A.acount = c->acount;
     if (is_dd(pin)) A.tsup = tsup;
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
@@ -209,7 +209,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     // (inside a BiCGStab run: the RHS active at the last host check) + 8 links
     // per output site
     const double sb_in = spinor_bytes(pin), sb_out = spinor_bytes(pout);
-    const int nwork = c->act && c->act_count >= 0 && c->act_count < nrhs ? c->act_count : nrhs;
+    const int nwork = c->alist && c->act_count >= 0 && c->act_count < nrhs ? c->act_count : nrhs;
     const double bytes = (double)c->g.Vh *
                          (nwork * (sb_in + sb_out + (w ? sb_in : 0) + (w2 ? sb_in : 0)) + 8.0 * link_bytes(pin));
     int slot;
@@ -354,8 +354,8 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     }
     c->autotune = getenv("WD_NO_AUTOTUNE") == nullptr;
     c->hop_err = nullptr;
-    c->act = nullptr;
-    c->act_stride = 0;
+    c->alist = nullptr;
+    c->acount = nullptr;
     c->gst = nullptr;
     c->loop_dev = nullptr;
     c->graph_off = false;

@@ -422,7 +422,35 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
 // The iteration kernels below skip every RHS whose state is inactive
 // (converged or broken down): its x and r keep their final values, and the
 // other fields of that RHS are neither read nor written again in this run.
-// Stencil launches inside the run skip the same RHS (HopArgs::act).
+// Stencil launches inside the run walk the list of the active RHS that
+// k_active_list builds after every update of the states (HopArgs::alist).
+
+// list[0 .. count) = the active RHS in ascending order (count: the number
+// k_scal_init / k_scal_beta stored); one block, fixed order
+__global__ void k_active_list(const BiState *st, int nrhs, int *list) {
+    __shared__ int wc[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nrhs; c0 += blockDim.x) {
+        const int r = c0 + threadIdx.x;
+        const bool a = r < nrhs && st[r].active;
+        const unsigned m = __ballot_sync(0xffffffffu, a);
+        if (lane == 0) wc[wid] = __popc(m);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < wid; ++w) off += wc[w];
+        if (a) list[off + __popc(m & ((1u << lane) - 1u))] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < nw; ++w) tot += wc[w];
+            base += tot;
+        }
+        __syncthreads();
+    }
+}
 
 // s = r - alpha v
 template <typename SW, typename SP, bool FL>
@@ -511,7 +539,8 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP,
         k_bicg_init<SW, SP, FL><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, Vh, nrhs, V.bpr)));
     k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count);
-    c->launches += 2;
+    k_active_list<<<1, 256, 0, c->st>>>(V.st, nrhs, V.alist);
+    c->launches += 3;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -543,9 +572,10 @@ int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
         k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_xr<SW, SP, FL><<<grid, 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part, Vh, nrhs, V.bpr);
         k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
+        k_active_list<<<1, 256, 0, c->st>>>(V.st, nrhs, V.alist);
         k_bicg_p<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
     }));
-    c->launches += 5;
+    c->launches += 6;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }

@@ -46,8 +46,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, int s, int nb, int rb,
     constexpr int NCH = SIO<SIn>::NCH;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs < A.nrhs && rhs_on(A, rhs)) {
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs >= 0) {
             cx<RT> psi[12], h[6], uh[6];
             SIO<SIn>::load((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi);
             spin_project<MU, SIGN>(psi, h);
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     typedef typename RealOf<SIn>::type RT;
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s >= A.g.Vh) return;
+    if (s >= A.g.Vh || tile_rhs(A, rb, 0, R) < 0) return;   // no site, or a tile with no working RHS
     const Geom &g = A.g;
     int x, y, z, t;
     eo_coords(g, A.p, s, x, y, z, t);
@@ -91,9 +91,8 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     const RT a = (RT)A.a, b = (RT)A.b, c = (RT)A.c;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs >= A.nrhs) break;
-        if (!rhs_on(A, rhs)) continue;
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs < 0) break;
         cx<RT> o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = b * acc[r][k];
@@ -192,8 +191,8 @@ __device__ __forceinline__ void prefetch_dir(const HopArgs &A, int s, int nb, in
         constexpr int NCH = SIO<SIn>::NCH;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int rhs = rb * R + r;
-            if (rhs < A.nrhs) {
+            const int rhs = tile_rhs(A, rb, r, R);
+            if (rhs >= 0) {
                 const uint4 *q = (const uint4 *)A.in + (size_t)rhs * NCH * Vh + nb;
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) prefetch_line<PF>(q + (size_t)k * Vh);
@@ -218,8 +217,8 @@ __device__ __forceinline__ void hop_dir_f2(const HopArgs &A, int s, int nb, int 
     constexpr int NCH = SIO<SIn>::NCH;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs < A.nrhs && rhs_on(A, rhs)) {
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs >= 0) {
             float2 psi[12], h[6], hs[6], uh[6];
             load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi);
             proj_f2<MU, SIGN>(psi, h);
@@ -254,8 +253,8 @@ __device__ __forceinline__ void load_dir_f2(const HopArgs &A, int s, int nb, int
     constexpr int NCH = SIO<SIn>::NCH;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs < A.nrhs && rhs_on(A, rhs)) load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi[r]);
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs >= 0) load_f2<SIn>((const uint4 *)A.in + (size_t)rhs * NCH * Vh, Vh, nb, psi[r]);
     }
 }
 
@@ -267,7 +266,7 @@ __device__ __forceinline__ void compute_dir_f2(const HopArgs &A, int rb, const c
     constexpr int SIGN = (FWD != DAG) ? -1 : +1;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (rb * R + r < A.nrhs && rhs_on(A, rb * R + r)) {
+        if (tile_rhs(A, rb, r, R) >= 0) {
             float2 h[6], hs[6], uh[6];
             proj_f2<MU, SIGN>(psi[r], h);
 #pragma unroll
@@ -361,9 +360,8 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
     const float2 a2 = f2((float)A.a, (float)A.a), b2 = f2((float)A.b, (float)A.b), c2 = f2((float)A.c, (float)A.c);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs >= A.nrhs) break;
-        if (!rhs_on(A, rhs)) continue;
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs < 0) break;
         float2 o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = __fmul2_rn(b2, acc[r][k]);
@@ -390,7 +388,7 @@ template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG,
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s < A.g.Vh) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE, PF>(A, rb, s);
+    if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE, PF>(A, rb, s);
 }
 
 // Persistent batched stencil over several lattices (row a11): one launch walks

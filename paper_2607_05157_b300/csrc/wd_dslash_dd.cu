@@ -180,7 +180,7 @@ template <int R, bool DAG, bool OUTDD>
 __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s >= A.g.Vh) return;
+    if (s >= A.g.Vh || tile_rhs(A, rb, 0, R) < 0) return;
     const Geom &g = A.g;
     int x, y, z, t;
     eo_coords(g, A.p, s, x, y, z, t);
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int rhs = rb * R + r;
-            if (rhs < A.nrhs && rhs_on(A, rhs) && hop_reaches(A, rhs, t)) {
+            const int rhs = tile_rhs(A, rb, r, R);
+            if (rhs >= 0 && hop_reaches(A, rhs, t)) {
                 cx<dd> psi[12], h[6], uh[6];
                 load_dd((const double2 *)A.in + (size_t)rhs * 12 * Vh, Vh, nb, psi);
                 project_dir<DAG>(d, psi, h);
@@ -230,9 +230,8 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
     const dd a = d2dd(A.a), b = d2dd(A.b), c = d2dd(A.c);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs >= A.nrhs) break;
-        if (!rhs_on(A, rhs)) continue;
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs < 0) break;
         cx<dd> o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = cmake(dd_mul(b, acc[r][k].re), dd_mul(b, acc[r][k].im));
@@ -420,7 +419,7 @@ template <int R, bool DAG, bool OUTDD>
 __global__ void __launch_bounds__(128) hop_kernel_ddz(HopArgs A) {
     const int rb = blockIdx.x % A.nrb;
     const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
-    if (s >= A.g.Vh) return;
+    if (s >= A.g.Vh || tile_rhs(A, rb, 0, R) < 0) return;
     const Geom &g = A.g;
     int x, y, z, t;
     eo_coords(g, A.p, s, x, y, z, t);
@@ -453,8 +452,8 @@ __global__ void __launch_bounds__(128) hop_kernel_ddz(HopArgs A) {
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int rhs = rb * R + r;
-            if (rhs < A.nrhs && rhs_on(A, rhs) && hop_reaches(A, rhs, t)) {
+            const int rhs = tile_rhs(A, rb, r, R);
+            if (rhs >= 0 && hop_reaches(A, rhs, t)) {
                 zdd psi[12], h[6], uh[6];
                 const float4 *q = (const float4 *)A.in + (size_t)rhs * 12 * Vh + nb;
 #pragma unroll
@@ -475,9 +474,8 @@ __global__ void __launch_bounds__(128) hop_kernel_ddz(HopArgs A) {
     const float2 ch = mk2(c.h, c.h), cl = mk2(c.l, c.l);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int rhs = rb * R + r;
-        if (rhs >= A.nrhs) break;
-        if (!rhs_on(A, rhs)) continue;
+        const int rhs = tile_rhs(A, rb, r, R);
+        if (rhs < 0) break;
         zdd o[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = zmul(bh, bl, acc[r][k].h, neg2(acc[r][k].h), acc[r][k].l);

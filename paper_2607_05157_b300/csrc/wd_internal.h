@@ -38,10 +38,11 @@ struct HopArgs {
     int nrhs, nrb;
     Geom g;
     int *err;              // error flag of the staged variant (bounded waits); set by hop()
-    // Krylov activity of each RHS (nullable): RHS r is skipped when
-    // act[r * act_stride] == 0 -- inside a BiCGStab run the converged RHS
-    const int *act = nullptr;
-    int act_stride = 0;
+    // Inside a BiCGStab run: the RHS still working, ascending (alist[0 ..
+    // *acount)); RHS tiles walk this list, so converged RHS cost nothing.
+    // Null: all nrhs RHS.
+    const int *alist = nullptr;
+    const int *acount = nullptr;
     // timeslice that holds the whole input of each RHS (nullable; entry -1:
     // anywhere): output sites more than one timeslice away get no hop term
     // (double-float stencil only; time-diluted and point sources)
@@ -57,8 +58,11 @@ __device__ __forceinline__ bool hop_reaches(const HopArgs &A, int rhs, int t) {
     return dt <= 1 || dt == A.g.T - 1;
 }
 
-__device__ __forceinline__ bool rhs_on(const HopArgs &A, int rhs) {
-    return A.act == nullptr || __ldg(A.act + (size_t)rhs * A.act_stride) != 0;
+// RHS handled by slot r of RHS tile rb (R slots per tile), or -1 if none
+__device__ __forceinline__ int tile_rhs(const HopArgs &A, int rb, int r, int R) {
+    const int k = rb * R + r;
+    if (A.alist == nullptr) return k < A.nrhs ? k : -1;
+    return k < __ldg(A.acount) ? __ldg(A.alist + k) : -1;
 }
 
 template <typename SIn, typename SOut, typename SW, typename G>
@@ -149,8 +153,8 @@ struct wd_ctx {
     int hop_threads[5];
     bool autotune;                  // time the stencil launch shapes on first use
     int *hop_err;                   // device flag: a staged stencil wait gave up
-    const int *act;                 // Krylov activity mask passed to every stencil launch (nullable)
-    int act_stride;
+    const int *alist;               // active-RHS list of the running BiCGStab (nullable)
+    const int *acount;              // its length (device)
     int act_count;                  // RHS active at the last host check (-1: unknown), for profiled bytes
     std::vector<wd_loop_graph> loops;   // captured BiCGStab loops (most recent last)
     cudaStream_t gst;               // capture stream of those graphs
@@ -221,6 +225,7 @@ struct BiVecs {
     BiState *st;
     double *part;               // reduction partials
     int *count;                 // active count (device)
+    int *alist;                 // active RHS, ascending (device, count entries)
     int bpr;                    // reduction blocks per RHS
     Space sp;
     OpFn op;

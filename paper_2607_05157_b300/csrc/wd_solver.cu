@@ -37,6 +37,7 @@ int alloc_bivecs(wd_ctx *c, const Space &sp, int pw, int pp, int nrhs, BiVecs &V
     V.bpr = reduction_bpr(sp.units, nrhs);
     WD_TRY(ws_get(c, (t + ".part").c_str(), sizeof(double) * 3 * V.bpr * nrhs, (void **)&V.part));
     WD_TRY(ws_get(c, (t + ".count").c_str(), sizeof(int), (void **)&V.count));
+    WD_TRY(ws_get(c, (t + ".alist").c_str(), sizeof(int) * (size_t)nrhs, (void **)&V.alist));
     return WD_OK;
 }
 
@@ -58,7 +59,7 @@ static std::vector<uintptr_t> loop_key(wd_ctx *c, int pw, int pp, const BiVecs &
     memcpy(&kb, &c->kappa, sizeof(kb));
     const char *ov = getenv("WD_HOP_R");
     return {(uintptr_t)V.x, (uintptr_t)V.r, (uintptr_t)V.rh, (uintptr_t)V.v, (uintptr_t)V.t, (uintptr_t)V.p,
-            (uintptr_t)V.s, (uintptr_t)V.st, (uintptr_t)V.part, (uintptr_t)V.count, (uintptr_t)V.op,
+            (uintptr_t)V.s, (uintptr_t)V.st, (uintptr_t)V.part, (uintptr_t)V.count, (uintptr_t)V.alist, (uintptr_t)V.op,
             V.sig[0], V.sig[1], V.sig[2], (uintptr_t)nrhs, (uintptr_t)pw, (uintptr_t)pp, (uintptr_t)V.bpr,
             (uintptr_t)V.sp.units, (uintptr_t)kb, (uintptr_t)std::hash<std::string>()(ov ? ov : "")};
 }
@@ -162,7 +163,7 @@ static int loop_graph_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int ma
 
 // Run BiCGStab iterations until no RHS is active or max_iter is reached.
 // Every kernel of an iteration (stencil and BLAS) skips the RHS that have
-// converged (the stencil through the activity mask set here).  The first two
+// converged (the stencil walks the active-RHS list set here).  The first two
 // iterations run as plain launches (they tune the stencil shapes and touch
 // every workspace); the rest run inside a captured graph whose while node
 // checks convergence on the device, or -- when profiling with per-launch
@@ -178,10 +179,10 @@ static int bicg_run(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs, int max_iter
     int active = *hcount;
     struct MaskGuard {
         wd_ctx *c;
-        ~MaskGuard() { c->act = nullptr; c->act_stride = 0; c->act_count = -1; }
+        ~MaskGuard() { c->alist = nullptr; c->acount = nullptr; c->act_count = -1; }
     } guard{c};
-    c->act = &V.st[0].active;
-    c->act_stride = (int)(sizeof(BiState) / sizeof(int));
+    c->alist = V.alist;
+    c->acount = V.count;
     c->act_count = active;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(c->st, &cs);
