@@ -17,6 +17,12 @@ the dofs of timeslice t:  X(t) = sum_{j in t} conj(v_j) (B D^{-1} v)_j.
                X_1 = eta^dag B (D^{-1} - P D_c^{-1} P^dag) eta  on fine noise,
                X_2 = (P xi)^dag B (P D_c^{-1} xi)             on coarse noise,
                the second being tr(B P D_c^{-1} P^dag) = tr(P^dag B P D_c^{-1}).
+  mlmc2_probe  the combination the paper proposes in its outlook (Sec. 6):
+               the level-1 term tr(B M_1) of Eq. 12 estimated with the probing
+               x dilution vectors of Eqs. 13-14 (optionally one timeslice per
+               vector) instead of plain Rademacher vectors; level 2 as mlmc2.
+  mlmc_allocation  Eq. 6: the number of samples per level that minimises the
+               total cost sum_l N_l C_l for a target variance eps^2.
 
 `solve(v)` is any callable returning D^{-1} v for a flat length-12V vector.
 """
@@ -99,6 +105,39 @@ def mlmc2(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, sample0=0):
         xi = rademacher(seed, (sample0 + i) | COARSE_STREAM, ncd).astype(np.complex128)
         X2[i] = contract(P @ xi, P @ solve_coarse(xi), dims, gamma5)
     return X1, X2
+
+
+def mlmc2_probe(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, col, nc, dilution, time_dilution=False,
+                sample0=0):
+    """Per-sample level values (X1 (N1, T), X2 (N2, T)) of the two-level
+    estimator with probing on level 1 (Sec. 6 outlook; Eqs. 12-14): for sample
+    i, X1_i = sum over the probing x dilution (x timeslice) vectors v of eta_i
+    of v^dag B (D^{-1} v - P D_c^{-1} P^dag v); X2 as in mlmc2."""
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    masks = probing_masks(col, nc, dilution)
+    if time_dilution:
+        ts = timeslice_of_dof(dims)
+        masks = [m & (ts == t) for m in masks for t in range(T)]
+    X1 = np.zeros((N1, T), np.complex128)
+    for i in range(N1):
+        eta = rademacher(seed, sample0 + i, n)
+        for m in masks:
+            v = np.where(m, eta, 0).astype(np.complex128)
+            X1[i] += contract(v, solve(v) - P @ solve_coarse(P.conj().T @ v), dims, gamma5)
+    _, X2 = mlmc2(solve, solve_coarse, P, dims, seed, 0, N2, gamma5, sample0)
+    return X1, X2
+
+
+def mlmc_allocation(V, C, eps):
+    """Eq. 6: N_l = eps^-2 sqrt(V_l / C_l) sum_i sqrt(V_i C_i), the minimiser
+    of sum_l N_l C_l subject to sum_l V_l / N_l = eps^2 (real N_l).  Returns
+    (continuous N_l, integer N_l = ceil, at least 1)."""
+    V = np.asarray(V, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    s = np.sum(np.sqrt(V * C))
+    Nc = np.sqrt(V / C) * s / eps ** 2
+    return Nc, np.maximum(np.ceil(Nc - 1e-9 * Nc), 1).astype(np.int64)
 
 
 def mean_and_variance(samples):

@@ -99,3 +99,108 @@ def test_mlmc_unbiased_and_level_variances(mg):
     assert 0.6 < v1 / V1 < 1.4 and 0.7 < v2 / V2 < 1.3
     total = m1 + m2
     assert abs(total - np.trace(Dinv)) < 5 * np.sqrt(V1 / N1 + V2 / N2)
+
+
+# ---- MLMC combined with probing (Sec. 6 outlook) and the N_l allocation (Eq. 6)
+
+def test_mlmc_allocation_hand_example_and_brute_force():
+    """Eq. 6 on V = (4, 1), C = (1, 4), eps = 1: sum sqrt(V C) = 4, so
+    N = (sqrt(4) * 4, sqrt(1/4) * 4) = (8, 2); variance 4/8 + 1/2 = 1 = eps^2.
+    Brute force over integer pairs finds the same minimum cost 16."""
+    Nc, Ni = estimators.mlmc_allocation([4.0, 1.0], [1.0, 4.0], 1.0)
+    assert np.allclose(Nc, [8.0, 2.0], rtol=0, atol=1e-12) and list(Ni) == [8, 2]
+    best = min((n1 + 4 * n2, n1, n2) for n1 in range(1, 60) for n2 in range(1, 60) if 4 / n1 + 1 / n2 <= 1)
+    assert best == (16, 8, 2)
+
+
+def test_mlmc_allocation_is_the_constrained_minimum():
+    """The continuous N_l meet the variance target exactly, and every other
+    point on the constraint surface sum V_l / N_l = eps^2 costs more."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        L = int(rng.integers(2, 5))
+        V = rng.uniform(0.1, 10.0, L)
+        C = rng.uniform(0.1, 10.0, L)
+        eps = float(rng.uniform(0.05, 1.0))
+        Nc, Ni = estimators.mlmc_allocation(V, C, eps)
+        assert abs(np.sum(V / Nc) - eps ** 2) < 1e-12 * eps ** 2
+        cost = np.sum(Nc * C)
+        for _ in range(50):
+            # another feasible point: scale a random positive vector onto the constraint
+            N = Nc * np.exp(rng.normal(0, 0.3, L))
+            N *= np.sum(V / N) / eps ** 2
+            assert abs(np.sum(V / N) - eps ** 2) < 1e-9 * eps ** 2
+            assert np.sum(N * C) >= cost * (1 - 1e-12)
+        # rounding up keeps the variance within the target
+        assert np.sum(V / Ni) <= eps ** 2 * (1 + 1e-12) and np.all(Ni >= 1)
+
+
+@pytest.fixture(scope='module')
+def mg_probe():
+    dims, agg, nv = (2, 2, 2, 4), (2, 2, 2, 2), 3
+    U = synth.gauge_field(dims, 0.4, 1010)
+    D = wilson.sparse_matrix(U, 0.12, BC_AP)
+    P = multigrid.prolongator(synth.test_vectors(dims, nv, 5), dims, agg)
+    Dinv = solver.dense_inverse(D)
+    Dcinv = solver.dense_inverse(multigrid.coarse_operator(D, P))
+    return dims, U, D, P, Dinv, Dcinv
+
+
+@pytest.mark.parametrize("time_dilution", [False, True])
+def test_mlmc2_probe_level1_is_difference_of_probing(mg_probe, time_dilution):
+    """Level 1 of the combined estimator is linear in the operator: each
+    sample equals the probing sample of D^{-1} minus the probing sample of
+    P D_c^{-1} P^dag on the same vectors (probing pinned separately)."""
+    from oracle import coloring
+    dims, U, D, P, Dinv, Dcinv = mg_probe
+    Pd = P.toarray()
+    nc, sigma = coloring.search(dims, 1)
+    col = coloring.colors(dims, sigma, nc)
+    X1, X2 = estimators.mlmc2_probe(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 7, 3, 4, True, col, nc,
+                                    12, time_dilution)
+    coarse = Pd @ Dcinv @ Pd.conj().T
+    if time_dilution:
+        # each timeslice's vectors form their own probing set: sum over t of
+        # probing with the masks restricted to t
+        ts = wilson.timeslice_of_dof(dims)
+        ref = np.zeros_like(X1)
+        from oracle import noise
+        for i in range(3):
+            eta = noise.rademacher(7, i, 12 * int(np.prod(dims)))
+            for m in estimators.probing_masks(col, nc, 12):
+                for t in range(dims[3]):
+                    v = np.where(m & (ts == t), eta, 0).astype(complex)
+                    ref[i] += estimators.contract(v, Dinv @ v - coarse @ v, dims, True)
+    else:
+        ref = (estimators.probing(lambda v: Dinv @ v, dims, 7, 3, True, col, nc, 12) -
+               estimators.probing(lambda v: coarse @ v, dims, 7, 3, True, col, nc, 12))
+    assert np.abs(X1 - ref).max() < 1e-12 * np.abs(ref).max()
+    _, R2 = estimators.mlmc2(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 7, 0, 4, True)
+    assert np.array_equal(X2, R2)
+
+
+@pytest.mark.parametrize("time_dilution", [False, True])
+def test_mlmc2_probe_exact_when_every_dof_is_its_own_vector(time_dilution):
+    """With a colouring that gives every site its own colour (distance 4 on
+    a 2^4 torus) and full spin-colour dilution, every probing vector has one
+    nonzero entry, so level 1 equals tr[B M_1(t, t)] exactly for any noise
+    (Eq. 10: M_1 = D^{-1} - P D_c^{-1} P^dag)."""
+    from oracle import coloring
+    dims = (2, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.4, 1011)
+    D = wilson.sparse_matrix(U, 0.12, BC_AP)
+    P = multigrid.prolongator(synth.test_vectors(dims, 2, 6), dims, (2, 2, 2, 2))
+    Dinv = solver.dense_inverse(D)
+    Dcinv = solver.dense_inverse(multigrid.coarse_operator(D, P))
+    nc, sigma = coloring.search(dims, 4)
+    assert nc == 16
+    col = coloring.colors(dims, sigma, nc)
+    X1, _ = estimators.mlmc2_probe(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 11, 2, 1, True, col, nc,
+                                   12, time_dilution)
+    Pd = P.toarray()
+    M = Dinv - Pd @ Dcinv @ Pd.conj().T
+    d = wilson.gamma5_full(int(np.prod(dims))) * np.diag(M)
+    ts = wilson.timeslice_of_dof(dims)
+    exact = np.array([d[ts == t].sum() for t in range(dims[3])])
+    for i in range(2):
+        assert np.abs(X1[i] - exact).max() < 1e-12 * np.abs(exact).max()
