@@ -64,7 +64,7 @@ typedef enum {
 } wd_prec;
 
 /* trace_estimate methods */
-enum { WD_HUTCH = 0, WD_PROBE = 1, WD_MLMC2 = 2 };
+enum { WD_HUTCH = 0, WD_PROBE = 1, WD_MLMC2 = 2, WD_MLMC2_PROBE = 3 };
 /* trace_estimate operators B in tr[B D^{-1}(t,t)] */
 enum { WD_TR_DINV = 0, WD_TR_G5_DINV = 1 };
 /* dilution flags: low byte = spin-colour dilution (1 or 12); OR in
@@ -118,16 +118,21 @@ int probe_color(const int *dims, int nD, int d, int *n_colors, int *sigma, int32
  *             distance-d torus colouring (Eq. 15), times the dilution.
  *   WD_MLMC2: two-level multigrid MLMC (Eqs. 9-12, L = 2); needs wd_mg_setup.
  *             N is the level-1 sample count, n2 the level-2 count.
+ *   WD_MLMC2_PROBE: WD_MLMC2 with the level-1 term tr(B M_1) estimated by the
+ *             probing x dilution vectors of WD_PROBE (d, dilution) -- the
+ *             combination of both methods the paper proposes in its outlook
+ *             (Sec. 6); level 2 as WD_MLMC2.  N level-1 samples (each N *
+ *             n_c * dilution fine and as many coarse solves), n2 level-2.
  * Noise: entry j of sample i is 1 - 2*(top bit of splitmix64(seed ^ (i<<40) ^ j)),
  * j = 12*site + 3*spin + colour; coarse noise uses sample | 2^23.
  * dilution: 1 or 12, optionally | WD_DIL_TIME.  batch: RHS solved together
  * (0 = automatic).  prec, tol: as wd_solve.
  * Outputs (host): estimate[2*(T+1)] complex mean per timeslice then the total;
  * sample_var[T+1] sample variance sum |X_i - mean|^2 / (N-1) of the per-sample
- * values (for WD_MLMC2: the variance of the two-level estimate itself,
- * s_1^2/N + s_2^2/n2, per timeslice and total); n_solves_out: number of fine
- * plus coarse solves; samples_out (nullable): [N][T][2] per-sample values
- * (the level-1 values for WD_MLMC2). */
+ * values (for WD_MLMC2 / WD_MLMC2_PROBE: the variance of the two-level
+ * estimate itself, s_1^2/N + s_2^2/n2, per timeslice and total);
+ * n_solves_out: number of fine plus coarse solves; samples_out (nullable):
+ * [N][T][2] per-sample values (the level-1 values for the MLMC methods). */
 int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, uint64_t seed,
                    int op, int prec, int batch, double tol, double *estimate, double *sample_var,
                    int64_t *n_solves_out, double *samples_out);
@@ -140,9 +145,17 @@ int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, 
  * the multilevel splitting. */
 int wd_point_correlator(wd_ctx *ctx, const int src[4], int prec, double tol, double *C);
 
-/* Per-sample level values of the last WD_MLMC2 estimate: level 2 samples
- * [n2][T][2] (host). */
+/* Per-sample level values of the last WD_MLMC2 / WD_MLMC2_PROBE estimate:
+ * level 2 samples [n2][T][2] (host). */
 int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);
+
+/* Samples per level of a multilevel estimator (Sec. 2, Eq. 6): the N_l that
+ * minimise the total cost sum_l N_l C_l for a target variance eps^2 of the
+ * estimate, N_l = eps^-2 sqrt(V_l / C_l) sum_i sqrt(V_i C_i), rounded up (at
+ * least 1), so that sum_l V_l / N_l <= eps^2.  V[L]: per-sample variance of
+ * level l (>= 0), C[L]: cost of one level-l sample (> 0), eps > 0; N_out[L]
+ * (host).  Host only.  WD_EINVAL for bad arguments or a count beyond 2^62. */
+int mlmc_allocate(int L, const double *V, const double *C, double eps, int64_t *N_out);
 
 const char *wd_last_error(void);
 

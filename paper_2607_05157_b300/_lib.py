@@ -7,7 +7,7 @@ LIB_PATH = os.path.join(_HERE, 'libwd.so')
 
 WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA, WD_ENOCONV, WD_EBREAKDOWN, WD_ETIMEOUT, WD_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16, WD_FP64_DD = 0, 1, 2, 3
-WD_HUTCH, WD_PROBE, WD_MLMC2 = 0, 1, 2
+WD_HUTCH, WD_PROBE, WD_MLMC2, WD_MLMC2_PROBE = 0, 1, 2, 3
 WD_TR_DINV, WD_TR_G5_DINV = 0, 1
 WD_DIL_TIME = 0x100
 WD_K_HOP, WD_K_BLAS, WD_K_COARSE, WD_K_FORCE, WD_K_HOP64, WD_K_COUNT = 0, 1, 2, 3, 4, 5
@@ -44,6 +44,7 @@ _SIGS = {
     'trace_estimate': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int, c_int,
                                c_double, c_void_p, c_void_p, P(c_int64), c_void_p]),
     'wd_mlmc_level2_samples': (c_int, [c_void_p, c_void_p, c_int]),
+    'mlmc_allocate': (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p]),
     'wd_point_correlator': (c_int, [c_void_p, P(c_int), c_int, c_double, c_void_p]),
     'wd_last_error': (ctypes.c_char_p, []),
     'wd_mg_setup': (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_uint64]),

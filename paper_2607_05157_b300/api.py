@@ -115,6 +115,18 @@ def wd_point_correlator(h, src, T, prec=WD_MIXED_FP32, tol=1e-10):
     return C
 
 
+def mlmc_allocate(V, C, eps):
+    """Samples per level (int64 array) for variances V, costs C and a target
+    standard error eps (host computation in libwd)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    if V.shape != C.shape or V.ndim != 1:
+        raise ValueError('V and C must be 1-D arrays of the same length')
+    N = np.zeros(V.shape[0], np.int64)
+    check(lib.mlmc_allocate(int(V.shape[0]), _host_ptr(V), _host_ptr(C), float(eps), _host_ptr(N)), 'mlmc_allocate')
+    return N
+
+
 def wd_mlmc_level2_samples(h, n2, T):
     smp = np.zeros((n2, T, 2), np.float64)
     check(lib.wd_mlmc_level2_samples(h, _host_ptr(smp), int(n2)), 'wd_mlmc_level2_samples')

@@ -362,7 +362,75 @@ int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double 
 }
 
 int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
-                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out);
+                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out,
+                   int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *) = nullptr,
+                   void *level1_user = nullptr);
+int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
+int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
+int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
+                 double *resid_out);
+
+__global__ void k_sub_fields(double *z, const double *w, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] -= w[i];
+}
+
+// Level 1 of the two-level estimator with probing (WD_MLMC2_PROBE, Sec. 6
+// outlook): for the probing x dilution (x timeslice) vectors v of N1 noise
+// samples, X1(t) += sum_{x in t} conj(v) B (D^{-1} v - P D_c^{-1} P^dag v),
+// v regenerated by the contraction from the counter hash.  u: EstParams.
+static int level1_probe(wd_ctx *c, void *u, int N1, int batch, double tol, int prec, double *X1, int64_t *ns) {
+    EstParams P = *(const EstParams *)u;
+    const Geom &g = c->g;
+    const int T = g.T;
+    const long total = (long)N1 * P.m;
+    const long ncoarse = (long)c->mg->Vc * c->mg->ncd;
+    const int B = batch > 0 ? (int)(batch < total ? batch : total) : auto_batch(c, (int)total);
+    for (long g0 = 0; g0 < total; g0 += B) {
+        const int nb = (int)(total - g0 < B ? total - g0 : B);
+        P.g0 = (int)g0;
+        P.nrhs = nb;
+        const size_t f = field_bytes(g, P64, nb);
+        double *be, *bo, *ze, *zo, *we, *wo, *bc, *yc, *part;
+        WD_TRY(ws_get(c, "mlp.be", f, (void **)&be));
+        WD_TRY(ws_get(c, "mlp.bo", f, (void **)&bo));
+        WD_TRY(ws_get(c, "mlp.ze", f, (void **)&ze));
+        WD_TRY(ws_get(c, "mlp.zo", f, (void **)&zo));
+        WD_TRY(ws_get(c, "mlp.we", f, (void **)&we));
+        WD_TRY(ws_get(c, "mlp.wo", f, (void **)&wo));
+        WD_TRY(ws_get(c, "mlp.bc", sizeof(double2) * ncoarse * nb, (void **)&bc));
+        WD_TRY(ws_get(c, "mlp.yc", sizeof(double2) * ncoarse * nb, (void **)&yc));
+        int bps = (2 * (g.Vh / T) + 1023) / 1024;
+        if (bps < 1) bps = 1;
+        WD_TRY(ws_get(c, "mlp.part", sizeof(double) * 2 * (size_t)nb * T * bps, (void **)&part));
+        const long n = (long)g.V * nb;
+        k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, g, be, bo);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
+        int *tsup = nullptr;
+        if (P.TT > 1) {
+            WD_TRY(ws_get(c, "mlp.tsup", sizeof(int) * (size_t)nb, (void **)&tsup));
+            k_tsup<<<(nb + 127) / 128, 128, 0, c->st>>>(P, tsup);
+            c->launches++;
+        }
+        int s = solve_eo(c, be, bo, ze, zo, nb, tol, prec, 100000, nullptr, nullptr, tsup);
+        if (s != WD_OK) return s;
+        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb));
+        s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
+        if (s != WD_OK) return s;
+        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb));
+        const long nf = (long)nb * 24 * g.Vh;
+        k_sub_fields<<<1184, 256, 0, c->st>>>(ze, we, nf);
+        k_sub_fields<<<1184, 256, 0, c->st>>>(zo, wo, nf);
+        const int s_first = (int)(g0 / P.m), s_last = (int)((g0 + nb - 1) / P.m);
+        const int nsamp = s_last - s_first + 1;
+        k_contract<<<dim3(bps, nb, T), 256, 0, c->st>>>(P, g, ze, zo, part, bps);
+        k_accumulate<<<(nsamp * T + 127) / 128, 128, 0, c->st>>>(P, T, part, bps, X1, s_first, nsamp);
+        c->launches += 4;
+        WD_CUDA(cudaGetLastError());
+        *ns += 2 * (int64_t)nb;
+    }
+    return WD_OK;
+}
 
 // Rademacher noise of samples [sample0, sample0 + nrhs) (no masks) into FP64 eo fields
 int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, double *bo) {
@@ -449,9 +517,19 @@ extern "C" int trace_estimate(wd_ctx *c, int method, int dilution, int N, int n2
         return WD_EINVAL;
     }
     int64_t ns = 0;
-    if (method == WD_MLMC2) {
+    if (method == WD_MLMC2 || method == WD_MLMC2_PROBE) {
         if (n2 < 1) { set_error("trace_estimate: MLMC2 needs n2 >= 1"); return WD_EINVAL; }
-        int s = mlmc2_estimate(c, N, n2, seed, op, prec, batch, tol, estimate, sample_var, &ns, samples_out);
+        if (!c->mg) { set_error("trace_estimate: MLMC2 needs wd_mg_setup"); return WD_EINVAL; }
+        int s;
+        if (method == WD_MLMC2_PROBE) {
+            EstParams P;
+            WD_TRY(est_params(c, WD_PROBE, dilution, d, seed, op == WD_TR_G5_DINV, P));
+            if ((long)N * P.m > (1L << 30)) { set_error("trace_estimate: too many right-hand sides"); return WD_EINVAL; }
+            s = mlmc2_estimate(c, N, n2, seed, op, prec, batch, tol, estimate, sample_var, &ns, samples_out,
+                               level1_probe, &P);
+        } else {
+            s = mlmc2_estimate(c, N, n2, seed, op, prec, batch, tol, estimate, sample_var, &ns, samples_out);
+        }
         if (n_solves_out) *n_solves_out = ns;
         return s;
     }

@@ -132,8 +132,11 @@ static int contract_fields(wd_ctx *c, const double *ae, const double *ao, const 
 
 static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double *var);
 
+// level1 (nullable): fills X1 [N1][T][2] and adds its solves to *ns in place
+// of the plain Rademacher level 1 (WD_MLMC2_PROBE passes the probing one)
 int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
-                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out) {
+                   double *estimate, double *sample_var, int64_t *nsolves, double *samples_out,
+                   int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *), void *level1_user) {
     if (!c->mg) { set_error("trace_estimate: MLMC2 needs wd_mg_setup"); return WD_EINVAL; }
     const Geom &g = c->g;
     const int T = g.T;
@@ -146,7 +149,8 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
     WD_CUDA(cudaMemsetAsync(X2, 0, sizeof(double) * 2 * (size_t)N2 * T, c->st));
     int64_t ns = 0;
     // ---- level 1: eta^dag B (D^{-1} - P D_c^{-1} P^dag) eta
-    for (int s0 = 0; s0 < N1; s0 += B) {
+    if (level1) WD_TRY(level1(c, level1_user, N1, batch, tol, prec, X1, &ns));
+    for (int s0 = 0; s0 < (level1 ? 0 : N1); s0 += B) {
         const int nb = N1 - s0 < B ? N1 - s0 : B;
         const size_t f = field_bytes(g, P64, nb);
         double *be, *bo, *ze, *zo, *we, *wo, *bc, *yc;

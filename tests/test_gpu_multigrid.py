@@ -100,6 +100,38 @@ def test_mlmc2_per_sample(gamma5):
     ctx.close()
 
 
+@pytest.mark.parametrize("gamma5,dil,time_dil,d", [(1, 12, False, 1), (0, 1, False, 2), (1, 1, True, 1)])
+def test_mlmc2_probe_per_sample(gamma5, dil, time_dil, d):
+    """Two-level MLMC with probing on level 1 (the combination of the
+    paper's outlook): per-sample level-1 values (probing x dilution [x time]
+    vectors, fine minus coarse-corrected solves) and level-2 values against
+    the oracle with the same prolongator, element by element."""
+    from paper_2607_05157_b300 import trace_estimate, wd_mlmc_level2_samples, WD_MLMC2_PROBE, WD_DIL_TIME
+    from oracle import coloring
+    dims, agg, nv = (4, 4, 4, 4), (2, 2, 2, 2), 6
+    ctx, U, D, P = _setup(dims, agg, nv, kappa=0.12, seed=1001)
+    nc, sigma = coloring.search(dims, d)
+    col = coloring.colors(dims, sigma, nc)
+    N1, N2 = 2, 6
+    flags = dil | (WD_DIL_TIME if time_dil else 0)
+    r = trace_estimate(ctx.h, WD_MLMC2_PROBE, flags, N1, dims[3], n2=N2, d=d, seed=2014, op=gamma5, prec=1,
+                       tol=1e-12, batch=37, with_samples=True)
+    X2 = wd_mlmc_level2_samples(ctx.h, N2, dims[3])
+    Dinv = solver.dense_inverse(D)
+    Dcinv = solver.dense_inverse(multigrid.coarse_operator(D, P))
+    R1, R2 = estimators.mlmc2_probe(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 2014, N1, N2, bool(gamma5),
+                                    col, nc, dil, time_dil)
+    for got, ref in ((r['samples'], R1), (X2, R2)):
+        scale = max(np.abs(ref).max(), np.abs(ref).sum(1).mean())
+        assert np.abs(got - ref).max() <= 1e-8 * scale
+    m1, v1, mt1, vt1 = estimators.mean_and_variance(R1)
+    m2, v2, mt2, vt2 = estimators.mean_and_variance(R2)
+    assert abs(r['total'] - (mt1 + mt2)) <= 1e-8 * (np.abs(R1).sum(1).mean() + np.abs(R2).sum(1).mean())
+    m = nc * dil * (dims[3] if time_dil else 1)
+    assert r['n_solves'] == 2 * N1 * m + N2
+    ctx.close()
+
+
 def test_gpu_test_vectors_give_orthonormal_prolongator():
     """Test vectors from inverse iterations on the GPU (no host input):
     P^dag P = I holds, seen as restrict(prolong(y)) = y."""

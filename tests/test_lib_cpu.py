@@ -49,3 +49,25 @@ def test_probe_color_bit_exact_vs_oracle(dims, d):
     onc, osig = coloring.search(dims, d, max_nc=4096)
     assert (nc, sigma) == (onc, osig)
     assert np.array_equal(cols, coloring.colors(dims, osig, onc))
+
+
+def test_mlmc_allocate_matches_oracle():
+    """Eq. 6 in libwd (host code, no GPU) against the oracle: identical
+    integer sample counts, and bad arguments rejected."""
+    import numpy as np
+    from oracle import estimators
+    from paper_2607_05157_b300 import mlmc_allocate, WDError
+    assert list(mlmc_allocate([4.0, 1.0], [1.0, 4.0], 1.0)) == [8, 2]
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        L = int(rng.integers(1, 6))
+        V = rng.uniform(0.0, 50.0, L) * (rng.uniform(size=L) > 0.1)
+        C = rng.uniform(0.01, 20.0, L)
+        eps = float(rng.uniform(0.01, 2.0))
+        _, ref = estimators.mlmc_allocation(V, C, eps)
+        got = mlmc_allocate(V, C, eps)
+        assert np.array_equal(got, ref), (V, C, eps, got, ref)
+        assert np.sum(V / got) <= eps ** 2 * (1 + 1e-12)
+    for V, C, eps in (([1.0], [0.0], 1.0), ([-1.0], [1.0], 1.0), ([1.0], [1.0], 0.0), ([1e30], [1e-30], 1e-20)):
+        with pytest.raises(WDError):
+            mlmc_allocate(V, C, eps)
