@@ -59,29 +59,48 @@ def level_operators(Dinv, Pd, Dcinv):
     return Dinv - B2, B2
 
 
+# noise samples of the separately sampled (2,2) term: i | LEVEL2_STREAM
+LEVEL2_STREAM = 1 << 21
+
+
 def samples(solve, solve_coarse, P, dims, seed, N1, N2):
     """Per-sample estimates of G_ij(t) from time-diluted Rademacher noise:
-    returns (S1 (N1, 3, T) for (i, j) = (1,1), (1,2), (2,1), and
-    S2 (N2, T) for (2, 2)).  Sample i uses noise sample i on every source
-    timeslice t'; level 2 needs only coarse solves, so it may use more
-    samples (N2 >= N1)."""
+    returns (S1 (N1, 3, T) for (i, j) = (1,1), (1,2), (2,1) from noise samples
+    0 .. N1-1, and S2 (N2, T) for (2, 2) from the independent noise samples
+    i | LEVEL2_STREAM).  Each sample puts the noise on every source timeslice
+    t' in turn.  The (2, 2) term needs only coarse solves, so it is sampled
+    on its own (N2 samples, typically more than N1); the estimate of G is
+    mean(S11 + S12 + S21) + mean(S22), with variance
+    var(S11 + S12 + S21) / N1 + var(S22) / N2."""
     X, Y, Z, T = dims
     n = 12 * X * Y * Z * T
     ts = timeslice_of_dof(dims)
     S1 = np.zeros((N1, 3, T), np.complex128)
     S2 = np.zeros((N2, T), np.complex128)
-    for i in range(max(N1, N2)):
-        eta = rademacher(seed, i, n)
-        for tp in range(T):
-            v = np.where(ts == tp, eta, 0).astype(np.complex128)
-            y2 = P @ solve_coarse(P.conj().T @ v)
-            y1 = solve(v) - y2 if i < N1 else None
-            for t in range(T):
-                m = ts == (t + tp) % T
-                if i < N2:
-                    S2[i, t] += np.vdot(y2[m], y2[m]) / T
-                if i < N1:
-                    S1[i, 0, t] += np.vdot(y1[m], y1[m]) / T
-                    S1[i, 1, t] += np.vdot(y2[m], y1[m]) / T       # (1,2): y_2^dag y_1
-                    S1[i, 2, t] += np.vdot(y1[m], y2[m]) / T       # (2,1): y_1^dag y_2
+    for level, N in ((1, N1), (2, N2)):
+        for i in range(N):
+            eta = rademacher(seed, i if level == 1 else i | LEVEL2_STREAM, n)
+            for tp in range(T):
+                v = np.where(ts == tp, eta, 0).astype(np.complex128)
+                y2 = P @ solve_coarse(P.conj().T @ v)
+                y1 = solve(v) - y2 if level == 1 else None
+                for t in range(T):
+                    m = ts == (t + tp) % T
+                    if level == 2:
+                        S2[i, t] += np.vdot(y2[m], y2[m]) / T
+                    else:
+                        S1[i, 0, t] += np.vdot(y1[m], y1[m]) / T
+                        S1[i, 1, t] += np.vdot(y2[m], y1[m]) / T   # (1,2): y_2^dag y_1
+                        S1[i, 2, t] += np.vdot(y1[m], y2[m]) / T   # (2,1): y_1^dag y_2
     return S1, S2
+
+
+def estimate(S1, S2):
+    """(G (5, T): means of (1,1), (1,2), (2,1), (2,2) and of the total;
+    var (5, T): variances of those means)."""
+    N1, N2 = S1.shape[0], S2.shape[0]
+    G = np.stack([S1[:, 0].mean(0), S1[:, 1].mean(0), S1[:, 2].mean(0), S2.mean(0),
+                  S1.sum(1).mean(0) + S2.mean(0)])
+    v = lambda a: np.sum(np.abs(a - a.mean(0)) ** 2, axis=0) / (a.shape[0] - 1) / a.shape[0]
+    var = np.stack([v(S1[:, 0]), v(S1[:, 1]), v(S1[:, 2]), v(S2), v(S1.sum(1)) + v(S2)])
+    return G, var

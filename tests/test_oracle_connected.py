@@ -90,3 +90,18 @@ def test_estimator_expectation_is_exact(setup):
     assert np.all(np.abs(S2.mean(0) - G22) < 5 * sd2 + 1e-12)
     # (2,1) is the conjugate of (1,2) sample by sample
     assert np.abs(S1[:, 2] - S1[:, 1].conj()).max() < 1e-14 * np.abs(S1).max()
+
+
+def test_estimate_combines_pinned_means_and_variances(setup):
+    """estimate(): the pair means and variances are the pinned sample mean and
+    variance of the mean; the total's variance adds the independent levels."""
+    from oracle import estimators
+    dims, D, P, Dinv, Dcinv = setup
+    S1, S2 = connected.samples(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 9, 5, 7)
+    G, var = connected.estimate(S1, S2)
+    for k, S in enumerate((S1[:, 0], S1[:, 1], S1[:, 2], S2)):
+        m, v, _, _ = estimators.mean_and_variance(S)
+        assert np.allclose(G[k], m, rtol=1e-14, atol=0) and np.allclose(var[k], v / S.shape[0], rtol=1e-12)
+    m1, v1, _, _ = estimators.mean_and_variance(S1.sum(1))
+    m2, v2, _, _ = estimators.mean_and_variance(S2)
+    assert np.allclose(G[4], m1 + m2, rtol=1e-14) and np.allclose(var[4], v1 / 5 + v2 / 7, rtol=1e-12)
