@@ -149,6 +149,23 @@ int wd_point_correlator(wd_ctx *ctx, const int src[4], int prec, double tol, dou
  * level 2 samples [n2][T][2] (host). */
 int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);
 
+/* Connected pseudoscalar two-point function with the two-level multigrid
+ * decomposition (Sec. 4, Eqs. 16-20, L = 2; needs wd_mg_setup):
+ * G(t) = (1/T) sum_t' tr[D^{-1}(t+t',t') g5 D^{-1}(t',t+t') g5] = sum_ij G_ij(t)
+ * with B_1 = D^{-1} - P D_c^{-1} P^dag and B_2 = P D_c^{-1} P^dag.  Estimated
+ * with time-diluted Rademacher noise eta on each source timeslice t' and
+ * y_k = B_k eta: sample_ij(t) = (1/T) sum_t' sum_{x in t+t'} y_j(x)^dag y_i(x).
+ * Level 1: N1 samples (noise samples 0..N1-1; T fine and T coarse solves
+ * each) give (1,1), (1,2), (2,1); the (2,2) term takes N2 samples of its own
+ * (noise samples i | 2^21; T coarse solves each).  N1, N2 >= 2.
+ * Outputs (host): G[5][T][2] complex means of (1,1), (1,2), (2,1), (2,2) and
+ * the total; var[5][T] variances of those means (total: var of the level-1
+ * sum / N1 + var(2,2) / N2); samples1 (nullable) [N1][3][T][2];
+ * samples2 (nullable) [N2][T][2]; n_solves_out (nullable): fine + coarse
+ * solves.  prec, tol, batch as trace_estimate. */
+int wd_connected_mlmc(wd_ctx *ctx, int N1, int N2, uint64_t seed, int prec, double tol, int batch, double *G,
+                      double *var, double *samples1, double *samples2, int64_t *n_solves_out);
+
 /* Samples per level of a multilevel estimator (Sec. 2, Eq. 6): the N_l that
  * minimise the total cost sum_l N_l C_l for a target variance eps^2 of the
  * estimate, N_l = eps^-2 sqrt(V_l / C_l) sum_i sqrt(V_i C_i), rounded up (at

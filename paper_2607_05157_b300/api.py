@@ -115,6 +115,25 @@ def wd_point_correlator(h, src, T, prec=WD_MIXED_FP32, tol=1e-10):
     return C
 
 
+def wd_connected_mlmc(h, N1, N2, T, seed=0, prec=WD_MIXED_FP32, tol=1e-10, batch=0, with_samples=False):
+    """Connected G(t) with the two-level decomposition.  Returns dict(G (5, T)
+    complex: (1,1), (1,2), (2,1), (2,2), total; var (5, T); samples1 (N1, 3, T)
+    and samples2 (N2, T) or None; n_solves)."""
+    G = np.zeros((5, T, 2), np.float64)
+    var = np.zeros((5, T), np.float64)
+    s1 = np.zeros((N1, 3, T, 2), np.float64) if with_samples else None
+    s2 = np.zeros((N2, T, 2), np.float64) if with_samples else None
+    ns = ctypes.c_int64()
+    check(lib.wd_connected_mlmc(h, int(N1), int(N2), ctypes.c_uint64(seed), int(prec), float(tol), int(batch),
+                                _host_ptr(G), _host_ptr(var), _host_ptr(s1) if with_samples else None,
+                                _host_ptr(s2) if with_samples else None, ctypes.byref(ns)), 'wd_connected_mlmc')
+    out = dict(G=G[..., 0] + 1j * G[..., 1], var=var, n_solves=ns.value, samples1=None, samples2=None)
+    if with_samples:
+        out['samples1'] = s1[..., 0] + 1j * s1[..., 1]
+        out['samples2'] = s2[..., 0] + 1j * s2[..., 1]
+    return out
+
+
 def mlmc_allocate(V, C, eps):
     """Samples per level (int64 array) for variances V, costs C and a target
     standard error eps (host computation in libwd)."""

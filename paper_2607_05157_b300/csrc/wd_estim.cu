@@ -32,7 +32,7 @@ struct EstParams {
     int g0;         // global index of the first RHS of the batch
     int nrhs;       // RHS in this batch
     int gamma5;     // B = gamma5 (1) or 1 (0)
-    int stream_hi;  // coarse-noise stream bit (0 here)
+    int stream_hi;  // OR-ed into the noise sample index (separate noise streams; 0: the main one)
 };
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
@@ -75,7 +75,8 @@ __device__ __forceinline__ bool site_noise(const EstParams &P, const Geom &g, co
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
         double e = 0.0;
-        if (on && (d.comp < 0 || d.comp == k)) e = rademacher(P.seed, (unsigned long long)d.sample, 12ULL * site + k);
+        if (on && (d.comp < 0 || d.comp == k))
+            e = rademacher(P.seed, (unsigned long long)(d.sample | P.stream_hi), 12ULL * site + k);
         v[k] = cmake(e, 0.0);
     }
     return on;
@@ -458,6 +459,21 @@ int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma
     WD_TRY(ws_get(c, "est.part", sizeof(double) * 2 * (size_t)nrhs * g.T * bps, (void **)&part));
     k_contract<<<dim3(bps, nrhs, g.T), 256, 0, c->st>>>(P, g, ye, yo, part, bps);
     k_accumulate<<<(nrhs * g.T + 127) / 128, 128, 0, c->st>>>(P, g.T, part, bps, X, sample0, nrhs);
+    c->launches += 2;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// Time-diluted Rademacher sources: RHS g = T * i + t' (g0 <= g < g0 + nb) is
+// noise sample i | stream on timeslice t' only, into FP64 eo fields; tsup[r]
+// = t' (device, nb entries) for the Schur-source stencil
+int gen_time_diluted_eo(wd_ctx *c, uint64_t seed, int stream, int g0, int nb, double *be, double *bo, int *tsup) {
+    EstParams P;
+    memset(&P, 0, sizeof(P));
+    P.seed = seed; P.nc = 1; P.dil = 1; P.TT = c->g.T; P.m = c->g.T; P.g0 = g0; P.nrhs = nb; P.stream_hi = stream;
+    const long n = (long)c->g.V * nb;
+    k_gen_rhs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, c->g, be, bo);
+    k_tsup<<<(nb + 127) / 128, 128, 0, c->st>>>(P, tsup);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
