@@ -68,8 +68,10 @@ enum { WD_HUTCH = 0, WD_PROBE = 1, WD_MLMC2 = 2, WD_MLMC2_PROBE = 3 };
 /* trace_estimate operators B in tr[B D^{-1}(t,t)] */
 enum { WD_TR_DINV = 0, WD_TR_G5_DINV = 1 };
 /* dilution flags: low byte = spin-colour dilution (1 or 12); OR in
-   WD_DIL_TIME to also dilute in time (one timeslice per right-hand side) */
-enum { WD_DIL_TIME = 0x100 };
+   WD_DIL_TIME to also dilute in time (one timeslice per right-hand side);
+   OR in WD_COLOR_3D (with WD_DIL_TIME) to probe with the 3D colouring of
+   one timeslice (Eq. 15 with n_D = 3: c(x) = sum_{j<3} sigma_j x_j mod n_c) */
+enum { WD_DIL_TIME = 0x100, WD_COLOR_3D = 0x200 };
 
 /* Create a context: uploads the gauge field (a1), folds the boundary factors
  * into the wrap-around links and builds FP64/FP32/BF16 even-odd copies.

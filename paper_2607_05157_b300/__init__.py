@@ -11,7 +11,7 @@ package fails if libwd.so is missing, and every call raises WDError on a
 non-zero status.
 """
 from ._lib import (WDError, lib, WD_OK, WD_ENOCONV, WD_EBREAKDOWN, WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16, WD_FP64_DD,
-                   WD_HUTCH, WD_PROBE, WD_MLMC2, WD_MLMC2_PROBE, WD_TR_DINV, WD_TR_G5_DINV, WD_DIL_TIME,
+                   WD_HUTCH, WD_PROBE, WD_MLMC2, WD_MLMC2_PROBE, WD_TR_DINV, WD_TR_G5_DINV, WD_DIL_TIME, WD_COLOR_3D,
                    WD_K_HOP, WD_K_BLAS, WD_K_COARSE, WD_K_FORCE, WD_K_HOP64)
 from .api import (Context, Batch, wd_create, wd_destroy, wd_apply, wd_solve, probe_color, trace_estimate,
                   wd_mg_setup, wd_coarse_apply, wd_restrict, wd_prolong, wd_coarse_solve, wd_link_force,

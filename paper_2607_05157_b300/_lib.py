@@ -9,7 +9,7 @@ WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA, WD_ENOCONV, WD_EBREAKDOWN, WD_ETIMEOUT, W
 WD_FP64, WD_MIXED_FP32, WD_MIXED_BF16, WD_FP64_DD = 0, 1, 2, 3
 WD_HUTCH, WD_PROBE, WD_MLMC2, WD_MLMC2_PROBE = 0, 1, 2, 3
 WD_TR_DINV, WD_TR_G5_DINV = 0, 1
-WD_DIL_TIME = 0x100
+WD_DIL_TIME, WD_COLOR_3D = 0x100, 0x200
 WD_K_HOP, WD_K_BLAS, WD_K_COARSE, WD_K_FORCE, WD_K_HOP64, WD_K_COUNT = 0, 1, 2, 3, 4, 5
 
 _NAMES = {0: 'WD_OK', -1: 'WD_EINVAL', -2: 'WD_ENOMEM', -3: 'WD_ECUDA', -4: 'WD_ENOCONV',

@@ -490,11 +490,18 @@ int est_params(wd_ctx *c, int method, int dilution, int d, uint64_t seed, int ga
     P.gamma5 = gamma5;
     P.nc = 1;
     if (method == WD_PROBE) {
-        int nc = 0, sig[4];
-        const int s = probe_color(c->dims, 4, d, &nc, sig, nullptr);
+        // 4D colouring, or (WD_COLOR_3D, time-diluted only) the colouring of
+        // one timeslice: sigma_t = 0, every timeslice coloured alike
+        const bool c3 = (dilution & WD_COLOR_3D) != 0;
+        if (c3 && !(dilution & WD_DIL_TIME)) {
+            set_error("WD_COLOR_3D needs time dilution (WD_DIL_TIME)");
+            return WD_EINVAL;
+        }
+        int nc = 0, sig[4] = {0, 0, 0, 0};
+        const int s = probe_color(c->dims, c3 ? 3 : 4, d, &nc, sig, nullptr);
         if (s != WD_OK) { set_error("no torus colouring for distance %d", d); return s; }
         P.nc = nc;
-        for (int j = 0; j < 4; ++j) P.sigma[j] = sig[j];
+        for (int j = 0; j < 4; ++j) P.sigma[j] = j < (c3 ? 3 : 4) ? sig[j] : 0;
     }
     P.m = P.nc * P.dil * P.TT;
     return WD_OK;

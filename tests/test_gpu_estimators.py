@@ -168,3 +168,24 @@ def test_time_diluted_variants(dims, method, d, dil, op):
     _close(r['samples'], ref)
     assert r['n_solves'] == 2 * nc * dil * dims[3]
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,d,dil,op", [((4, 4, 4, 4), 2, 1, 1), ((4, 2, 6, 4), 1, 12, 0)])
+def test_probing_3d_timeslice_colouring(dims, d, dil, op):
+    """Probing with the colouring of one timeslice (Eq. 15 with n_D = 3,
+    WD_COLOR_3D) under time dilution: every timeslice is coloured alike and
+    probed on its own; per-sample values against the oracle."""
+    from paper_2607_05157_b300 import Context, trace_estimate, WD_PROBE, WD_DIL_TIME, WD_COLOR_3D
+    U = synth.gauge_field(dims, 0.5, 32)
+    Dinv = solver.dense_inverse(wilson.sparse_matrix(U, 0.125, BC))
+    nc, sigma = coloring.search(dims[:3], d)
+    col = np.tile(coloring.colors(dims[:3], sigma, nc), dims[3])
+    ctx = Context(dims, U, 0.125, BC)
+    r = trace_estimate(ctx.h, WD_PROBE, dil | WD_DIL_TIME | WD_COLOR_3D, 2, dims[3], d=d, seed=56, op=op, prec=1,
+                       tol=1e-12, batch=29, with_samples=True)
+    ref = _diluted_reference(Dinv, dims, 56, 2, bool(op), col, nc, dil)
+    _close(r['samples'], ref)
+    assert r['n_solves'] == 2 * nc * dil * dims[3]
+    with pytest.raises(Exception):
+        trace_estimate(ctx.h, WD_PROBE, dil | WD_COLOR_3D, 2, dims[3], d=d, seed=56, op=op, prec=1, tol=1e-12)
+    ctx.close()
