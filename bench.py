@@ -234,6 +234,53 @@ def gradient_measure(wd, api, torch, synth):
             "ms": 1e3 * dt}
 
 
+def mlmc_probe_measure(wd, api, torch, synth):
+    """Row f2: two-level MLMC with probing on level 1 (d = 2 x 12 dilution,
+    GPU-built 4^4 aggregates with 24 test vectors) against plain probing on
+    the same level-1 noise, 8^3x16: wall time, solves, variance of the total."""
+    dims = (8, 8, 8, 16)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1006), KAPPA, BC)
+    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=3)
+    kw = dict(d=2, op=1, tol=TOL)
+    api.trace_estimate(ctx.h, wd.WD_MLMC2_PROBE, 12, 2, 16, n2=32, seed=1, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = api.trace_estimate(ctx.h, wd.WD_MLMC2_PROBE, 12, 2, 16, n2=32, seed=2, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    p = api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 2, 16, seed=2, **kw)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx.close()
+    return {"workload": "8^3x16, tr[g5 D^-1(t,t)], level 1: 2 samples x probing d=2 x 12 dilution (384 fine + "
+                        "384 coarse solves), level 2: 32 coarse samples; plain probing: the same 2 samples",
+            "mlmc_probe_ms": 1e3 * (t1 - t0), "mlmc_probe_solves": m["n_solves"],
+            "mlmc_probe_var_total": m["var_total"], "probe_ms": 1e3 * (t2 - t1), "probe_solves": p["n_solves"],
+            "probe_var_total": p["var_total"]}
+
+
+def connected_measure(wd, api, torch, synth):
+    """Row f4: connected pseudoscalar G(t) with the two-level decomposition on
+    8^3x16 (N1 = 4 level-1 samples, N2 = 32 coarse samples): wall time, solves,
+    and the variance of the fine term G_11 against the plain estimator on the
+    same noise (the variance reduction of Sec. 4)."""
+    dims = (8, 8, 8, 16)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1007), KAPPA, BC)
+    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=4)
+    api.wd_connected_mlmc(ctx.h, 4, 32, 16, seed=1, tol=TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = api.wd_connected_mlmc(ctx.h, 4, 32, 16, seed=2, tol=TOL)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    v11, vplain = r["var"][0], r["var"][5]
+    return {"workload": "8^3x16 connected G(t), time-diluted noise, level 1: 4 samples x 16 timeslices (64 fine + "
+                        "64 coarse solves), (2,2): 32 samples x 16 coarse solves",
+            "ms": 1e3 * dt, "n_solves": r["n_solves"],
+            "var_plain_over_var_G11": {str(t): float(vplain[t] / v11[t]) for t in (1, 4, 8)}}
+
+
 def batched_measure(wd, torch, synth):
     """Row a11: 8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16) solved together
     (persistent multi-lattice stencil, CUDA graph) vs one after another."""
@@ -435,7 +482,9 @@ def main():
         # secondary measurements of the other rows, outside the timed region
         line["secondary"] = {"coarse_tc": coarse_measure(wd, api, torch, synth),
                              "gradient": gradient_measure(wd, api, torch, synth),
-                             "batched": batched_measure(wd, torch, synth)}
+                             "batched": batched_measure(wd, torch, synth),
+                             "mlmc_probe": mlmc_probe_measure(wd, api, torch, synth),
+                             "connected": connected_measure(wd, api, torch, synth)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, dt, n = oracle_baseline(3)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",

@@ -159,10 +159,13 @@ int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);
  * y_k = B_k eta: sample_ij(t) = (1/T) sum_t' sum_{x in t+t'} y_j(x)^dag y_i(x).
  * Level 1: N1 samples (noise samples 0..N1-1; T fine and T coarse solves
  * each) give (1,1), (1,2), (2,1); the (2,2) term takes N2 samples of its own
- * (noise samples i | 2^21; T coarse solves each).  N1, N2 >= 2.
- * Outputs (host): G[5][T][2] complex means of (1,1), (1,2), (2,1), (2,2) and
- * the total; var[5][T] variances of those means (total: var of the level-1
- * sum / N1 + var(2,2) / N2); samples1 (nullable) [N1][3][T][2];
+ * (noise samples i | 2^21; T coarse solves each).  N1, N2 >= 2.  The (2,2)
+ * term on the level-1 noise also gives the plain (undecomposed) estimator
+ * |y_1 + y_2|^2 on the same samples, for comparison.
+ * Outputs (host): G[6][T][2] complex means of (1,1), (1,2), (2,1), (2,2), the
+ * total and the plain estimator; var[6][T] variances of those means (total:
+ * var of the level-1 sum / N1 + var(2,2) / N2); samples1 (nullable)
+ * [N1][4][T][2] ((1,1), (1,2), (2,1), (2,2) on the level-1 noise);
  * samples2 (nullable) [N2][T][2]; n_solves_out (nullable): fine + coarse
  * solves.  prec, tol, batch as trace_estimate. */
 int wd_connected_mlmc(wd_ctx *ctx, int N1, int N2, uint64_t seed, int prec, double tol, int batch, double *G,

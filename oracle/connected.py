@@ -65,17 +65,18 @@ LEVEL2_STREAM = 1 << 21
 
 def samples(solve, solve_coarse, P, dims, seed, N1, N2):
     """Per-sample estimates of G_ij(t) from time-diluted Rademacher noise:
-    returns (S1 (N1, 3, T) for (i, j) = (1,1), (1,2), (2,1) from noise samples
-    0 .. N1-1, and S2 (N2, T) for (2, 2) from the independent noise samples
-    i | LEVEL2_STREAM).  Each sample puts the noise on every source timeslice
-    t' in turn.  The (2, 2) term needs only coarse solves, so it is sampled
-    on its own (N2 samples, typically more than N1); the estimate of G is
+    returns (S1 (N1, 4, T) for (i, j) = (1,1), (1,2), (2,1), (2,2) from noise
+    samples 0 .. N1-1, and S2 (N2, T) for (2, 2) from the independent noise
+    samples i | LEVEL2_STREAM).  Each sample puts the noise on every source
+    timeslice t' in turn.  The (2, 2) term needs only coarse solves, so the
+    estimate samples it on its own (N2 samples, typically more than N1): G is
     mean(S11 + S12 + S21) + mean(S22), with variance
-    var(S11 + S12 + S21) / N1 + var(S22) / N2."""
+    var(S11 + S12 + S21) / N1 + var(S22) / N2.  S1's (2, 2) column (same noise
+    as level 1) gives the plain estimator |y_1 + y_2|^2 for comparison."""
     X, Y, Z, T = dims
     n = 12 * X * Y * Z * T
     ts = timeslice_of_dof(dims)
-    S1 = np.zeros((N1, 3, T), np.complex128)
+    S1 = np.zeros((N1, 4, T), np.complex128)
     S2 = np.zeros((N2, T), np.complex128)
     for level, N in ((1, N1), (2, N2)):
         for i in range(N):
@@ -92,15 +93,17 @@ def samples(solve, solve_coarse, P, dims, seed, N1, N2):
                         S1[i, 0, t] += np.vdot(y1[m], y1[m]) / T
                         S1[i, 1, t] += np.vdot(y2[m], y1[m]) / T   # (1,2): y_2^dag y_1
                         S1[i, 2, t] += np.vdot(y1[m], y2[m]) / T   # (2,1): y_1^dag y_2
+                        S1[i, 3, t] += np.vdot(y2[m], y2[m]) / T
     return S1, S2
 
 
 def estimate(S1, S2):
-    """(G (5, T): means of (1,1), (1,2), (2,1), (2,2) and of the total;
-    var (5, T): variances of those means)."""
-    N1, N2 = S1.shape[0], S2.shape[0]
+    """(G (6, T): means of (1,1), (1,2), (2,1), (2,2) [from S2], of the total,
+    and of the plain estimator S11 + S12 + S21 + S22 on the level-1 noise;
+    var (6, T): variances of those means)."""
+    lvl1 = S1[:, :3].sum(1)
     G = np.stack([S1[:, 0].mean(0), S1[:, 1].mean(0), S1[:, 2].mean(0), S2.mean(0),
-                  S1.sum(1).mean(0) + S2.mean(0)])
+                  lvl1.mean(0) + S2.mean(0), S1.sum(1).mean(0)])
     v = lambda a: np.sum(np.abs(a - a.mean(0)) ** 2, axis=0) / (a.shape[0] - 1) / a.shape[0]
-    var = np.stack([v(S1[:, 0]), v(S1[:, 1]), v(S1[:, 2]), v(S2), v(S1.sum(1)) + v(S2)])
+    var = np.stack([v(S1[:, 0]), v(S1[:, 1]), v(S1[:, 2]), v(S2), v(lvl1) + v(S2), v(S1.sum(1))])
     return G, var

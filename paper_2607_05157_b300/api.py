@@ -116,12 +116,12 @@ def wd_point_correlator(h, src, T, prec=WD_MIXED_FP32, tol=1e-10):
 
 
 def wd_connected_mlmc(h, N1, N2, T, seed=0, prec=WD_MIXED_FP32, tol=1e-10, batch=0, with_samples=False):
-    """Connected G(t) with the two-level decomposition.  Returns dict(G (5, T)
-    complex: (1,1), (1,2), (2,1), (2,2), total; var (5, T); samples1 (N1, 3, T)
-    and samples2 (N2, T) or None; n_solves)."""
-    G = np.zeros((5, T, 2), np.float64)
-    var = np.zeros((5, T), np.float64)
-    s1 = np.zeros((N1, 3, T, 2), np.float64) if with_samples else None
+    """Connected G(t) with the two-level decomposition.  Returns dict(G (6, T)
+    complex: (1,1), (1,2), (2,1), (2,2), total, plain; var (6, T);
+    samples1 (N1, 4, T) and samples2 (N2, T) or None; n_solves)."""
+    G = np.zeros((6, T, 2), np.float64)
+    var = np.zeros((6, T), np.float64)
+    s1 = np.zeros((N1, 4, T, 2), np.float64) if with_samples else None
     s2 = np.zeros((N2, T, 2), np.float64) if with_samples else None
     ns = ctypes.c_int64()
     check(lib.wd_connected_mlmc(h, int(N1), int(N2), ctypes.c_uint64(seed), int(prec), float(tol), int(batch),

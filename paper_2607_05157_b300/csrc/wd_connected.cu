@@ -14,7 +14,9 @@
 // y_2 = P D_c^{-1} P^dag eta and the (1,1), (1,2), (2,1) samples.  The (2,2)
 // term needs only coarse solves and is sampled on its own (N2 samples of the
 // independent noise samples i | 2^21), so the variance of the total is
-// var(S11 + S12 + S21)/N1 + var(S22)/N2.
+// var(S11 + S12 + S21)/N1 + var(S22)/N2.  The (2,2) term on the level-1
+// noise comes for free and gives the plain (undecomposed) estimator
+// |y_1 + y_2|^2 on the same samples, for comparison.
 #include <math.h>
 #include <string.h>
 
@@ -81,8 +83,8 @@ __global__ void k_contract_pairs(Geom g, const double *y1e, const double *y1o, c
 }
 
 // S[sample][t] += (1/T) sum over the batch's RHS g = T*sample + t' of the
-// partials at timeslice (t + t') mod T (fixed order).  S1: [N1][3][T][2]
-// (pairs (1,1), (1,2), (2,1)); S2: [N2][T][2].  level 1: S1, else S2.
+// partials at timeslice (t + t') mod T (fixed order).  S1: [N1][4][T][2]
+// (pairs (1,1), (1,2), (2,1), (2,2)); S2: [N2][T][2].  level 1: S1, else S2.
 __global__ void k_accumulate_pairs(const double *part, int bps, int T, int g0, int nb, int level, double *S1,
                                    double *S2, int s_first, int nsamp) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,12 +100,13 @@ __global__ void k_accumulate_pairs(const double *part, int bps, int T, int g0, i
     }
     const double w = 1.0 / T;
     if (level == 1) {
-        double *o = S1 + (size_t)si * 3 * T * 2;
+        double *o = S1 + (size_t)si * 4 * T * 2;
         o[(0 * T + t) * 2] += w * q[0];                      // (1,1): real
         o[(1 * T + t) * 2] += w * q[1];                      // (1,2) = y2^dag y1
         o[(1 * T + t) * 2 + 1] += w * q[2];
         o[(2 * T + t) * 2] += w * q[1];                      // (2,1) = conj(1,2)
         o[(2 * T + t) * 2 + 1] -= w * q[2];
+        o[(3 * T + t) * 2] += w * q[3];                      // (2,2) on the level-1 noise
     } else {
         S2[((size_t)si * T + t) * 2] += w * q[3];
     }
@@ -121,33 +124,43 @@ __device__ void mean_var_of(const double *base, size_t stride, int N, double &mr
     v = v / (N - 1) / N;
 }
 
-// G[5][T][2] and var[5][T]: pairs (1,1), (1,2), (2,1), (2,2) and the total
-// (the level-1 per-sample sum of its three pairs plus the independent (2,2))
+// G[6][T][2] and var[6][T]: pairs (1,1), (1,2), (2,1), (2,2) [from S2], the
+// total (the level-1 per-sample sum of its three pairs plus the independent
+// (2,2)) and the plain estimator (all four pairs on the level-1 noise)
 __global__ void k_connected_stats(const double *S1, const double *S2, int N1, int N2, int T, double *G,
                                   double *var) {
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         for (int k = 0; k < 4; ++k) {
             double mr, mi, v;
-            if (k < 3) mean_var_of(S1 + ((size_t)k * T + t) * 2, (size_t)3 * T * 2, N1, mr, mi, v);
+            if (k < 3) mean_var_of(S1 + ((size_t)k * T + t) * 2, (size_t)4 * T * 2, N1, mr, mi, v);
             else mean_var_of(S2 + (size_t)t * 2, (size_t)T * 2, N2, mr, mi, v);
             G[(k * T + t) * 2] = mr;
             G[(k * T + t) * 2 + 1] = mi;
             var[k * T + t] = v;
         }
-        double sr = 0.0, si = 0.0, v1 = 0.0;
-        for (int pass = 0; pass < 2; ++pass)
-            for (int i = 0; i < N1; ++i) {
-                double xr = 0.0, xi = 0.0;
-                for (int q = 0; q < 3; ++q) {
-                    xr += S1[(((size_t)i * 3 + q) * T + t) * 2];
-                    xi += S1[(((size_t)i * 3 + q) * T + t) * 2 + 1];
+        for (int kind = 0; kind < 2; ++kind) {       // 0: level-1 sum of 3 pairs, 1: plain (4 pairs)
+            const int np = kind == 0 ? 3 : 4;
+            double sr = 0.0, si = 0.0, v1 = 0.0;
+            for (int pass = 0; pass < 2; ++pass)
+                for (int i = 0; i < N1; ++i) {
+                    double xr = 0.0, xi = 0.0;
+                    for (int q = 0; q < np; ++q) {
+                        xr += S1[(((size_t)i * 4 + q) * T + t) * 2];
+                        xi += S1[(((size_t)i * 4 + q) * T + t) * 2 + 1];
+                    }
+                    if (pass == 0) { sr += xr / N1; si += xi / N1; }
+                    else v1 += (xr - sr) * (xr - sr) + (xi - si) * (xi - si);
                 }
-                if (pass == 0) { sr += xr / N1; si += xi / N1; }
-                else v1 += (xr - sr) * (xr - sr) + (xi - si) * (xi - si);
+            if (kind == 0) {
+                G[(4 * T + t) * 2] = sr + G[(3 * T + t) * 2];
+                G[(4 * T + t) * 2 + 1] = si + G[(3 * T + t) * 2 + 1];
+                var[4 * T + t] = v1 / (N1 - 1) / N1 + var[3 * T + t];
+            } else {
+                G[(5 * T + t) * 2] = sr;
+                G[(5 * T + t) * 2 + 1] = si;
+                var[5 * T + t] = v1 / (N1 - 1) / N1;
             }
-        G[(4 * T + t) * 2] = sr + G[(3 * T + t) * 2];
-        G[(4 * T + t) * 2 + 1] = si + G[(3 * T + t) * 2 + 1];
-        var[4 * T + t] = v1 / (N1 - 1) / N1 + var[3 * T + t];
+        }
     }
 }
 
@@ -167,11 +180,11 @@ extern "C" int wd_connected_mlmc(wd_ctx *c, int N1, int N2, uint64_t seed, int p
     if ((long)N1 * T > (1L << 30) || (long)N2 * T > (1L << 30)) { set_error("wd_connected_mlmc: too many samples"); return WD_EINVAL; }
     const long ncoarse = (long)c->mg->Vc * c->mg->ncd;
     double *S1, *S2, *Gd, *vd;
-    WD_TRY(ws_get(c, "con.S1", sizeof(double) * 2 * 3 * (size_t)N1 * T, (void **)&S1));
+    WD_TRY(ws_get(c, "con.S1", sizeof(double) * 2 * 4 * (size_t)N1 * T, (void **)&S1));
     WD_TRY(ws_get(c, "con.S2", sizeof(double) * 2 * (size_t)N2 * T, (void **)&S2));
-    WD_TRY(ws_get(c, "con.G", sizeof(double) * 2 * 5 * T, (void **)&Gd));
-    WD_TRY(ws_get(c, "con.var", sizeof(double) * 5 * T, (void **)&vd));
-    WD_CUDA(cudaMemsetAsync(S1, 0, sizeof(double) * 2 * 3 * (size_t)N1 * T, c->st));
+    WD_TRY(ws_get(c, "con.G", sizeof(double) * 2 * 6 * T, (void **)&Gd));
+    WD_TRY(ws_get(c, "con.var", sizeof(double) * 6 * T, (void **)&vd));
+    WD_CUDA(cudaMemsetAsync(S1, 0, sizeof(double) * 2 * 4 * (size_t)N1 * T, c->st));
     WD_CUDA(cudaMemsetAsync(S2, 0, sizeof(double) * 2 * (size_t)N2 * T, c->st));
     int64_t ns = 0;
     for (int level = 1; level <= 2; ++level) {
@@ -225,10 +238,10 @@ extern "C" int wd_connected_mlmc(wd_ctx *c, int N1, int N2, uint64_t seed, int p
     k_connected_stats<<<1, 128, 0, c->st>>>(S1, S2, N1, N2, T, Gd, vd);
     c->launches++;
     WD_CUDA(cudaGetLastError());
-    WD_CUDA(cudaMemcpyAsync(G, Gd, sizeof(double) * 2 * 5 * T, cudaMemcpyDeviceToHost, c->st));
-    WD_CUDA(cudaMemcpyAsync(var, vd, sizeof(double) * 5 * T, cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaMemcpyAsync(G, Gd, sizeof(double) * 2 * 6 * T, cudaMemcpyDeviceToHost, c->st));
+    WD_CUDA(cudaMemcpyAsync(var, vd, sizeof(double) * 6 * T, cudaMemcpyDeviceToHost, c->st));
     if (samples1)
-        WD_CUDA(cudaMemcpyAsync(samples1, S1, sizeof(double) * 2 * 3 * (size_t)N1 * T, cudaMemcpyDeviceToHost, c->st));
+        WD_CUDA(cudaMemcpyAsync(samples1, S1, sizeof(double) * 2 * 4 * (size_t)N1 * T, cudaMemcpyDeviceToHost, c->st));
     if (samples2)
         WD_CUDA(cudaMemcpyAsync(samples2, S2, sizeof(double) * 2 * (size_t)N2 * T, cudaMemcpyDeviceToHost, c->st));
     WD_CUDA(cudaStreamSynchronize(c->st));

@@ -102,6 +102,27 @@ def test_estimate_combines_pinned_means_and_variances(setup):
     for k, S in enumerate((S1[:, 0], S1[:, 1], S1[:, 2], S2)):
         m, v, _, _ = estimators.mean_and_variance(S)
         assert np.allclose(G[k], m, rtol=1e-14, atol=0) and np.allclose(var[k], v / S.shape[0], rtol=1e-12)
-    m1, v1, _, _ = estimators.mean_and_variance(S1.sum(1))
+    m1, v1, _, _ = estimators.mean_and_variance(S1[:, :3].sum(1))
     m2, v2, _, _ = estimators.mean_and_variance(S2)
     assert np.allclose(G[4], m1 + m2, rtol=1e-14) and np.allclose(var[4], v1 / 5 + v2 / 7, rtol=1e-12)
+    mp, vp, _, _ = estimators.mean_and_variance(S1.sum(1))
+    assert np.allclose(G[5], mp, rtol=1e-14) and np.allclose(var[5], vp / 5, rtol=1e-12)
+
+
+def test_plain_sample_is_the_undecomposed_estimator(setup):
+    """The four level-1 columns sum to |D^{-1} eta|^2 on the source-shifted
+    timeslices: the plain estimator of Eq. 16, sample by sample."""
+    dims, D, P, Dinv, Dcinv = setup
+    T = dims[3]
+    from oracle import noise
+    S1, _ = connected.samples(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 4, 2, 2)
+    ts = wilson.timeslice_of_dof(dims)
+    for i in range(2):
+        eta = noise.rademacher(4, i, Dinv.shape[0])
+        ref = np.zeros(T, np.complex128)
+        for tp in range(T):
+            y = Dinv @ np.where(ts == tp, eta, 0).astype(complex)
+            for t in range(T):
+                m = ts == (t + tp) % T
+                ref[t] += np.vdot(y[m], y[m]) / T
+        assert np.abs(S1[i].sum(0) - ref).max() < 1e-12 * np.abs(ref).max()
