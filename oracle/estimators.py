@@ -108,11 +108,15 @@ def mlmc2(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, sample0=0):
 
 
 def mlmc2_probe(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, col, nc, dilution, time_dilution=False,
-                sample0=0):
+                sample0=0, coarse_col=None, coarse_nc=1, coarse_dil=1):
     """Per-sample level values (X1 (N1, T), X2 (N2, T)) of the two-level
     estimator with probing on level 1 (Sec. 6 outlook; Eqs. 12-14): for sample
     i, X1_i = sum over the probing x dilution (x timeslice) vectors v of eta_i
-    of v^dag B (D^{-1} v - P D_c^{-1} P^dag v); X2 as in mlmc2."""
+    of v^dag B (D^{-1} v - P D_c^{-1} P^dag v).  Level 2 as in mlmc2, or, with
+    coarse_col (per-coarse-site colours of a colouring of the coarse torus),
+    probed as well: X2_i = sum over the coarse probing vectors xi (coarse
+    noise sample i masked to one colour and, for coarse_dil = 2 nv, one
+    coarse dof of the site) of (P xi)^dag B (P D_c^{-1} xi)."""
     X, Y, Z, T = dims
     n = 12 * X * Y * Z * T
     masks = probing_masks(col, nc, dilution)
@@ -125,7 +129,21 @@ def mlmc2_probe(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, col, nc, dil
         for m in masks:
             v = np.where(m, eta, 0).astype(np.complex128)
             X1[i] += contract(v, solve(v) - P @ solve_coarse(P.conj().T @ v), dims, gamma5)
-    _, X2 = mlmc2(solve, solve_coarse, P, dims, seed, 0, N2, gamma5, sample0)
+    if coarse_col is None:
+        _, X2 = mlmc2(solve, solve_coarse, P, dims, seed, 0, N2, gamma5, sample0)
+        return X1, X2
+    ncd = P.shape[1]
+    m = ncd // len(coarse_col)                   # coarse dofs per coarse site
+    site_col = np.repeat(np.asarray(coarse_col), m)
+    comp = np.tile(np.arange(m), len(coarse_col))
+    X2 = np.zeros((N2, T), np.complex128)
+    for i in range(N2):
+        xi = rademacher(seed, (sample0 + i) | COARSE_STREAM, ncd)
+        for c in range(coarse_nc):
+            for k in range(coarse_dil):
+                msk = (site_col == c) & ((comp == k) if coarse_dil > 1 else True)
+                v = np.where(msk, xi, 0).astype(np.complex128)
+                X2[i] += contract(P @ v, P @ solve_coarse(v), dims, gamma5)
     return X1, X2
 
 

@@ -204,3 +204,30 @@ def test_mlmc2_probe_exact_when_every_dof_is_its_own_vector(time_dilution):
     exact = np.array([d[ts == t].sum() for t in range(dims[3])])
     for i in range(2):
         assert np.abs(X1[i] - exact).max() < 1e-12 * np.abs(exact).max()
+
+
+def test_mlmc2_probe_coarse_level_reduces_to_plain_and_exact_limit(mg_probe):
+    """Level 2 with coarse probing: one colour and no dilution is the plain
+    coarse estimator of mlmc2 (pinned separately); every coarse site its own
+    colour with full coarse-dof dilution gives tr[B P D_c^{-1} P^dag (t, t)]
+    exactly for any noise."""
+    from oracle import coloring
+    dims, U, D, P, Dinv, Dcinv = mg_probe
+    cd = multigrid.coarse_dims(dims, (2, 2, 2, 2))
+    Vc = int(np.prod(cd))
+    ncd = P.shape[1]
+    nc, sigma = coloring.search(dims, 1)
+    col = coloring.colors(dims, sigma, nc)
+    solve, solve_c = (lambda v: Dinv @ v), (lambda v: Dcinv @ v)
+    _, X2a = estimators.mlmc2_probe(solve, solve_c, P, dims, 8, 0, 3, True, col, nc, 1,
+                                    coarse_col=np.zeros(Vc, int), coarse_nc=1, coarse_dil=1)
+    _, X2b = estimators.mlmc2(solve, solve_c, P, dims, 8, 0, 3, True)
+    assert np.abs(X2a - X2b).max() < 1e-13 * np.abs(X2b).max()
+    _, X2 = estimators.mlmc2_probe(solve, solve_c, P, dims, 8, 0, 2, True, col, nc, 1,
+                                   coarse_col=np.arange(Vc), coarse_nc=Vc, coarse_dil=ncd // Vc)
+    Pd = P.toarray()
+    d = wilson.gamma5_full(int(np.prod(dims))) * np.diag(Pd @ Dcinv @ Pd.conj().T)
+    ts = wilson.timeslice_of_dof(dims)
+    exact = np.array([d[ts == t].sum() for t in range(dims[3])])
+    for i in range(2):
+        assert np.abs(X2[i] - exact).max() < 1e-12 * np.abs(exact).max()
