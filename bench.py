@@ -251,12 +251,18 @@ def mlmc_probe_measure(wd, api, torch, synth):
     p = api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 2, 16, seed=2, **kw)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    # probing on both levels: coarse colouring d2 = 1 x all 48 coarse dofs of a site
+    b = api.trace_estimate_mlmc_probe(ctx.h, 12, 2, 2, 48, 1, 2, 16, seed=2, op=1, tol=TOL)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     ctx.close()
     return {"workload": "8^3x16, tr[g5 D^-1(t,t)], level 1: 2 samples x probing d=2 x 12 dilution (384 fine + "
-                        "384 coarse solves), level 2: 32 coarse samples; plain probing: the same 2 samples",
+                        "384 coarse solves); level 2: 32 plain coarse samples, or (both-levels) 2 samples x "
+                        "coarse colouring d=1 x 48 coarse dofs; plain probing: the same 2 level-1 samples",
             "mlmc_probe_ms": 1e3 * (t1 - t0), "mlmc_probe_solves": m["n_solves"],
             "mlmc_probe_var_total": m["var_total"], "probe_ms": 1e3 * (t2 - t1), "probe_solves": p["n_solves"],
-            "probe_var_total": p["var_total"]}
+            "probe_var_total": p["var_total"], "both_levels_ms": 1e3 * (t3 - t2),
+            "both_levels_solves": b["n_solves"], "both_levels_var_total": b["var_total"]}
 
 
 def connected_measure(wd, api, torch, synth):

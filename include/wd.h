@@ -147,6 +147,20 @@ int trace_estimate(wd_ctx *ctx, int method, int dilution, int N, int n2, int d, 
  * the multilevel splitting. */
 int wd_point_correlator(wd_ctx *ctx, const int src[4], int prec, double tol, double *C);
 
+/* Two-level MLMC with probing on both levels (the combination of the
+ * outlook, Sec. 6): level 1 as WD_MLMC2_PROBE (fine probing at distance d
+ * with `dilution`); level 2, tr(B P D_c^{-1} P^dag), with probing vectors of
+ * the coarse lattice: the coarse noise of each sample (as WD_MLMC2) masked to
+ * one colour of the distance-d2 torus colouring of the coarse lattice (d2 = 0:
+ * one colour) and, for coarse_dil = 2*nv, to one coarse dof of the site
+ * (coarse_dil = 1: none).  N1 fine samples (N1 * n_c * dilution fine and as
+ * many coarse solves), N2 coarse samples (N2 * n_c2 * coarse_dil coarse
+ * solves).  Outputs as trace_estimate for WD_MLMC2; samples1 [N1][T][2] and
+ * samples2 [N2][T][2] (host, nullable) are the level values per sample. */
+int trace_estimate_mlmc_probe(wd_ctx *ctx, int dilution, int d, int N1, int coarse_dil, int d2, int N2,
+                              uint64_t seed, int op, int prec, int batch, double tol, double *estimate,
+                              double *sample_var, int64_t *n_solves_out, double *samples1, double *samples2);
+
 /* Per-sample level values of the last WD_MLMC2 / WD_MLMC2_PROBE estimate:
  * level 2 samples [n2][T][2] (host). */
 int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);

@@ -45,6 +45,8 @@ _SIGS = {
                                c_double, c_void_p, c_void_p, P(c_int64), c_void_p]),
     'wd_mlmc_level2_samples': (c_int, [c_void_p, c_void_p, c_int]),
     'mlmc_allocate': (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p]),
+    'trace_estimate_mlmc_probe': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int,
+                                          c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     'wd_connected_mlmc': (c_int, [c_void_p, c_int, c_int, c_uint64, c_int, c_double, c_int, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p]),
     'wd_point_correlator': (c_int, [c_void_p, P(c_int), c_int, c_double, c_void_p]),

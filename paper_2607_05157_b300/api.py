@@ -134,6 +134,24 @@ def wd_connected_mlmc(h, N1, N2, T, seed=0, prec=WD_MIXED_FP32, tol=1e-10, batch
     return out
 
 
+def trace_estimate_mlmc_probe(h, dilution, d, N1, coarse_dil, d2, N2, T, seed=0, op=1, prec=WD_MIXED_FP32, batch=0,
+                              tol=1e-10):
+    """Two-level MLMC with probing on both levels.  Returns dict(estimate (T,),
+    total, var (T,), var_total, n_solves, samples1 (N1, T), samples2 (N2, T))."""
+    est = np.zeros(2 * (T + 1), np.float64)
+    var = np.zeros(T + 1, np.float64)
+    ns = ctypes.c_int64()
+    s1 = np.zeros((N1, T, 2), np.float64)
+    s2 = np.zeros((N2, T, 2), np.float64)
+    check(lib.trace_estimate_mlmc_probe(h, int(dilution), int(d), int(N1), int(coarse_dil), int(d2), int(N2),
+                                        ctypes.c_uint64(seed), int(op), int(prec), int(batch), float(tol),
+                                        _host_ptr(est), _host_ptr(var), ctypes.byref(ns), _host_ptr(s1),
+                                        _host_ptr(s2)), 'trace_estimate_mlmc_probe')
+    e = est[0::2] + 1j * est[1::2]
+    return dict(estimate=e[:T], total=e[T], var=var[:T], var_total=var[T], n_solves=ns.value,
+                samples1=s1[..., 0] + 1j * s1[..., 1], samples2=s2[..., 0] + 1j * s2[..., 1])
+
+
 def mlmc_allocate(V, C, eps):
     """Samples per level (int64 array) for variances V, costs C and a target
     standard error eps (host computation in libwd)."""

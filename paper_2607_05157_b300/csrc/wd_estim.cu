@@ -365,7 +365,7 @@ int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double 
 int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
                    double *estimate, double *sample_var, int64_t *nsolves, double *samples_out,
                    int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *) = nullptr,
-                   void *level1_user = nullptr);
+                   void *level1_user = nullptr, const CoarseProbe *cp = nullptr);
 int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
 int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
 int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
@@ -570,4 +570,43 @@ extern "C" int trace_estimate(wd_ctx *c, int method, int dilution, int N, int n2
     if (n_solves_out) *n_solves_out = ns;
     if (s != WD_OK) return s;
     return finish_estimate(c, X, N, estimate, sample_var, samples_out);
+}
+
+extern "C" int trace_estimate_mlmc_probe(wd_ctx *c, int dilution, int d, int N1, int coarse_dil, int d2, int N2,
+                                         uint64_t seed, int op, int prec, int batch, double tol, double *estimate,
+                                         double *sample_var, int64_t *n_solves_out, double *samples1,
+                                         double *samples2) {
+    if (!c || !estimate || !sample_var || N1 < 1 || N2 < 1 || prec < 0 || prec > 2 || !(tol > 0) ||
+        (op != 0 && op != 1) || d2 < 0) {
+        set_error("trace_estimate_mlmc_probe: bad argument");
+        return WD_EINVAL;
+    }
+    if (!c->mg) { set_error("trace_estimate_mlmc_probe: needs wd_mg_setup"); return WD_EINVAL; }
+    const int ncd = c->mg->ncd;
+    if (coarse_dil != 1 && coarse_dil != ncd) {
+        set_error("trace_estimate_mlmc_probe: coarse dilution must be 1 or the %d coarse dofs of a site", ncd);
+        return WD_EINVAL;
+    }
+    EstParams P;
+    WD_TRY(est_params(c, WD_PROBE, dilution, d, seed, op == WD_TR_G5_DINV, P));
+    if ((long)N1 * P.m > (1L << 30)) { set_error("trace_estimate_mlmc_probe: too many right-hand sides"); return WD_EINVAL; }
+    CoarseProbe cp;
+    memset(&cp, 0, sizeof(cp));
+    for (int j = 0; j < 4; ++j) cp.cd[j] = c->mg->cd[j];
+    cp.nc = 1;
+    if (d2 > 0) {
+        int sig[4];
+        WD_TRY(probe_color(c->mg->cd, 4, d2, &cp.nc, sig, nullptr));
+        for (int j = 0; j < 4; ++j) cp.sigma[j] = sig[j];
+    }
+    cp.dil = coarse_dil;
+    cp.m = cp.nc * cp.dil;
+    if ((long)N2 * cp.m > (1L << 30)) { set_error("trace_estimate_mlmc_probe: too many coarse vectors"); return WD_EINVAL; }
+    int64_t ns = 0;
+    const int s = mlmc2_estimate(c, N1, N2, seed, op, prec, batch, tol, estimate, sample_var, &ns, samples1,
+                                 level1_probe, &P, &cp);
+    if (n_solves_out) *n_solves_out = ns;
+    if (s != WD_OK) return s;
+    if (samples2) memcpy(samples2, c->last_level2.data(), sizeof(double) * 2 * (size_t)N2 * c->g.T);
+    return WD_OK;
 }

@@ -122,6 +122,13 @@ struct wd_loop_graph {
     int kernels;                    // kernel launches per body (two iterations + condition)
 };
 
+// Probing on the coarse level (wd_mlmc.cu): colour (sigma . X) mod nc of the
+// coarse site X (coarse extents cd), times dilution over the dil coarse dofs
+// of a site (dil = 1: none); m = nc * dil vectors per noise sample
+struct CoarseProbe {
+    int nc, sigma[4], cd[4], dil, m;
+};
+
 // multigrid state (wd_mg.cu)
 struct wd_mg {
     int nv, ncd;

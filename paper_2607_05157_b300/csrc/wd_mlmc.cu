@@ -46,6 +46,33 @@ __global__ void k_coarse_noise(double2 *xi, unsigned long long seed, int sample0
     xi[i] = make_double2((h >> 63) ? -1.0 : 1.0, 0.0);
 }
 
+// coarse probing noise: RHS g = g0 + r of the sample-major enumeration (m
+// vectors per sample: colour j / dil, coarse dof j % dil) is the coarse
+// Rademacher noise of sample (g / m) | 2^23 masked to the sites of that
+// colour and (dil > 1) that dof of the site
+__global__ void k_coarse_noise_probe(double2 *xi, unsigned long long seed, int g0, long ncoarse, int nrhs, int ncd,
+                                     CoarseProbe cp) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= ncoarse * nrhs) return;
+    const int r = (int)(i / ncoarse);
+    const long idx = i % ncoarse;
+    const int g = g0 + r, sample = g / cp.m, j = g % cp.m;
+    const int comp = cp.dil > 1 ? j % cp.dil : -1, colour = j / cp.dil;
+    const int X = (int)(idx / ncd), k = (int)(idx % ncd);
+    int x = X % cp.cd[0], q = X / cp.cd[0];
+    const int y = q % cp.cd[1];
+    q /= cp.cd[1];
+    const int z = q % cp.cd[2], t = q / cp.cd[2];
+    const long cval = (long)cp.sigma[0] * x + (long)cp.sigma[1] * y + (long)cp.sigma[2] * z + (long)cp.sigma[3] * t;
+    double v = 0.0;
+    if ((int)(cval % cp.nc) == colour && (comp < 0 || comp == k)) {
+        const unsigned long long h = mix64(seed ^ ((((unsigned long long)sample) | (1ULL << 23)) << 40) ^
+                                           (unsigned long long)idx);
+        v = (h >> 63) ? -1.0 : 1.0;
+    }
+    xi[i] = make_double2(v, 0.0);
+}
+
 // d = z - w on FP64 eo fields (both parities stored separately); elementwise
 __global__ void k_sub(double *z, const double *w, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] -= w[i];
@@ -94,16 +121,21 @@ __global__ void k_contract_fields(Geom g, const double *ae, const double *ao, co
     }
 }
 
-// X[sample0 + r][t] += sum_k part[r][t][k]
-__global__ void k_accumulate_fields(int T, const double *part, int bps, double *X, int sample0, int nrhs) {
+// X[sample][t] += sum over the batch's RHS g = g0 + r of that sample (g / m
+// == sample, m vectors per sample) of sum_k part[r][t][k]; fixed order
+__global__ void k_accumulate_fields(int T, const double *part, int bps, double *X, int g0, int nrhs, int m) {
+    const int s_first = g0 / m, nsamp = (g0 + nrhs - 1) / m - s_first + 1;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nrhs * T) return;
-    const int r = idx / T, t = idx % T;
-    const double *q = part + ((size_t)r * T + t) * bps * 2;
+    if (idx >= nsamp * T) return;
+    const int si = s_first + idx / T, t = idx % T;
+    const int a = max(g0, si * m), b = min(g0 + nrhs, (si + 1) * m);
     double re = 0, im = 0;
-    for (int k = 0; k < bps; ++k) { re += q[2 * k]; im += q[2 * k + 1]; }
-    X[((size_t)(sample0 + r) * T + t) * 2] += re;
-    X[((size_t)(sample0 + r) * T + t) * 2 + 1] += im;
+    for (int gi = a; gi < b; ++gi) {
+        const double *q = part + ((size_t)(gi - g0) * T + t) * bps * 2;
+        for (int k = 0; k < bps; ++k) { re += q[2 * k]; im += q[2 * k + 1]; }
+    }
+    X[((size_t)si * T + t) * 2] += re;
+    X[((size_t)si * T + t) * 2 + 1] += im;
 }
 
 // estimate = mean_1 + mean_2, variance = var_1 / N1 + var_2 / N2
@@ -117,14 +149,14 @@ __global__ void k_mlmc_combine(const double *m1, const double *v1, const double 
 }
 
 static int contract_fields(wd_ctx *c, const double *ae, const double *ao, const double *be, const double *bo,
-                           int gamma5, int nrhs, double *X, int sample0) {
+                           int gamma5, int nrhs, double *X, int g0, int m = 1) {
     const Geom &g = c->g;
     int bps = (2 * (g.Vh / g.T) + 1023) / 1024;
     if (bps < 1) bps = 1;
     double *part;
     WD_TRY(ws_get(c, "mlmc.part", sizeof(double) * 2 * (size_t)nrhs * g.T * bps, (void **)&part));
     k_contract_fields<<<dim3(bps, nrhs, g.T), 256, 0, c->st>>>(g, ae, ao, be, bo, gamma5, part, bps);
-    k_accumulate_fields<<<(nrhs * g.T + 127) / 128, 128, 0, c->st>>>(g.T, part, bps, X, sample0, nrhs);
+    k_accumulate_fields<<<(nrhs * g.T + 127) / 128, 128, 0, c->st>>>(g.T, part, bps, X, g0, nrhs, m);
     c->launches += 2;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
@@ -136,7 +168,8 @@ static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double 
 // of the plain Rademacher level 1 (WD_MLMC2_PROBE passes the probing one)
 int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int prec, int batch, double tol,
                    double *estimate, double *sample_var, int64_t *nsolves, double *samples_out,
-                   int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *), void *level1_user) {
+                   int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *), void *level1_user,
+                   const CoarseProbe *cp) {
     if (!c->mg) { set_error("trace_estimate: MLMC2 needs wd_mg_setup"); return WD_EINVAL; }
     const Geom &g = c->g;
     const int T = g.T;
@@ -176,9 +209,15 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         WD_TRY(contract_noise_eo(c, seed, s0, nb, gamma5, ze, zo, X1));
         ns += 2 * nb;
     }
-    // ---- level 2: (P xi)^dag B (P D_c^{-1} xi)
-    for (int s0 = 0; s0 < N2; s0 += B) {
-        const int nb = N2 - s0 < B ? N2 - s0 : B;
+    // ---- level 2: (P xi)^dag B (P D_c^{-1} xi), xi plain coarse noise or
+    // (cp) the coarse probing vectors of each sample
+    const int mc = cp ? cp->m : 1;          // coarse vectors per level-2 sample
+    const long total2 = (long)N2 * mc;
+    const int B2 = batch > 0 ? (int)(batch < total2 ? batch : total2)
+                             : auto_batch(c, (int)(total2 < (1L << 30) ? total2 : (1L << 30)));
+    for (long s0l = 0; s0l < total2; s0l += B2) {
+        const int s0 = (int)s0l;
+        const int nb = (int)(total2 - s0l < B2 ? total2 - s0l : B2);
         const size_t f = field_bytes(g, P64, nb);
         double *xi, *yc, *ae, *ao, *be, *bo;
         WD_TRY(ws_get(c, "mlmc.bc", sizeof(double2) * ncoarse * nb, (void **)&xi));
@@ -188,14 +227,18 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         WD_TRY(ws_get(c, "mlmc.ze", f, (void **)&be));
         WD_TRY(ws_get(c, "mlmc.zo", f, (void **)&bo));
         const long n = ncoarse * nb;
-        k_coarse_noise<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, s0, ncoarse, nb);
+        if (cp)
+            k_coarse_noise_probe<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, s0, ncoarse,
+                                                                                 nb, c->mg->ncd, *cp);
+        else
+            k_coarse_noise<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, s0, ncoarse, nb);
         c->launches++;
         WD_CUDA(cudaGetLastError());
         int s = coarse_solve(c, xi, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
         WD_TRY(mg_prolong_eo(c, xi, ae, ao, nb));
         WD_TRY(mg_prolong_eo(c, yc, be, bo, nb));
-        WD_TRY(contract_fields(c, ae, ao, be, bo, gamma5, nb, X2, s0));
+        WD_TRY(contract_fields(c, ae, ao, be, bo, gamma5, nb, X2, s0, mc));
         ns += nb;
     }
     double *m1, *v1, *m2, *v2, *mean, *var;

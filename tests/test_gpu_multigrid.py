@@ -132,6 +132,43 @@ def test_mlmc2_probe_per_sample(gamma5, dil, time_dil, d):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,agg,nv,d2,cfull", [((4, 4, 4, 4), (2, 2, 2, 2), 6, 1, True),
+                                                 ((4, 4, 4, 4), (2, 2, 2, 2), 6, 0, False),
+                                                 ((4, 2, 6, 4), (2, 2, 3, 2), 6, 2, True)])
+def test_mlmc_probe_both_levels_per_sample(dims, agg, nv, d2, cfull):
+    """Probing on both levels: level 1 with the fine probing vectors, level 2
+    with the colouring of the coarse torus x coarse-dof dilution; per-sample
+    values of both levels against the oracle."""
+    from paper_2607_05157_b300 import trace_estimate_mlmc_probe
+    from oracle import coloring
+    ctx, U, D, P = _setup(dims, agg, nv, kappa=0.12, seed=1001)
+    nc, sigma = coloring.search(dims, 1)
+    col = coloring.colors(dims, sigma, nc)
+    cd = multigrid.coarse_dims(dims, agg)
+    if d2 > 0:
+        nc2, sig2 = coloring.search(cd, d2)
+        ccol = coloring.colors(cd, sig2, nc2)
+    else:
+        nc2, ccol = 1, np.zeros(int(np.prod(cd)), np.int64)
+    cdil = 2 * nv if cfull else 1
+    N1, N2 = 2, 3
+    r = trace_estimate_mlmc_probe(ctx.h, 12, 1, N1, cdil, d2, N2, dims[3], seed=2016, op=1, prec=1, tol=1e-12,
+                                  batch=29)
+    Dinv = solver.dense_inverse(D)
+    Dcinv = solver.dense_inverse(multigrid.coarse_operator(D, P))
+    R1, R2 = estimators.mlmc2_probe(lambda v: Dinv @ v, lambda v: Dcinv @ v, P, dims, 2016, N1, N2, True, col, nc,
+                                    12, coarse_col=ccol, coarse_nc=nc2, coarse_dil=cdil)
+    for got, ref in ((r['samples1'], R1), (r['samples2'], R2)):
+        scale = max(np.abs(ref).max(), np.abs(ref).sum(1).mean())
+        assert np.abs(got - ref).max() <= 1e-8 * scale
+    m1, v1, mt1, vt1 = estimators.mean_and_variance(R1)
+    m2, v2, mt2, vt2 = estimators.mean_and_variance(R2)
+    assert abs(r['total'] - (mt1 + mt2)) <= 1e-8 * (np.abs(R1).sum(1).mean() + np.abs(R2).sum(1).mean())
+    assert abs(r['var_total'] - (vt1 / N1 + vt2 / N2)) <= 1e-6 * (vt1 / N1 + vt2 / N2)
+    assert r['n_solves'] == 2 * N1 * nc * 12 + N2 * nc2 * cdil
+    ctx.close()
+
+
 def test_gpu_test_vectors_give_orthonormal_prolongator():
     """Test vectors from inverse iterations on the GPU (no host input):
     P^dag P = I holds, seen as restrict(prolong(y)) = y."""
