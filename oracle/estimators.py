@@ -21,6 +21,10 @@ the dofs of timeslice t:  X(t) = sum_{j in t} conj(v_j) (B D^{-1} v)_j.
                the level-1 term tr(B M_1) of Eq. 12 estimated with the probing
                x dilution vectors of Eqs. 13-14 (optionally one timeslice per
                vector) instead of plain Rademacher vectors; level 2 as mlmc2.
+  mlmc3        the three-level estimator (Eqs. 9-12 with L = 3):
+               X_1 = eta^dag B (D^{-1} - P_1 D_2^{-1} P_1^dag) eta          fine noise,
+               X_2 = (P_1 xi)^dag B P_1 (D_2^{-1} - P_2 D_3^{-1} P_2^dag) xi  level-2 noise,
+               X_3 = (P_1 P_2 zeta)^dag B (P_1 P_2 D_3^{-1} zeta)           level-3 noise.
   mlmc_allocation  Eq. 6: the number of samples per level that minimises the
                total cost sum_l N_l C_l for a target variance eps^2.
 
@@ -145,6 +149,32 @@ def mlmc2_probe(solve, solve_coarse, P, dims, seed, N1, N2, gamma5, col, nc, dil
                 v = np.where(msk, xi, 0).astype(np.complex128)
                 X2[i] += contract(P @ v, P @ solve_coarse(v), dims, gamma5)
     return X1, X2
+
+
+LEVEL3_STREAM = 1 << 24
+
+
+def mlmc3(solve, solve2, solve3, P1, P2, dims, seed, N1, N2, N3, gamma5):
+    """Per-sample level values (X1 (N1, T), X2 (N2, T), X3 (N3, T)) of the
+    three-level estimator (Eq. 12 with L = 3).  Level-2 noise: coarse noise
+    samples i | COARSE_STREAM; level-3 noise: samples i | LEVEL3_STREAM."""
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    n2, n3 = P1.shape[1], P2.shape[1]
+    X1 = np.zeros((N1, T), np.complex128)
+    for i in range(N1):
+        eta = rademacher(seed, i, n).astype(np.complex128)
+        X1[i] = contract(eta, solve(eta) - P1 @ solve2(P1.conj().T @ eta), dims, gamma5)
+    X2 = np.zeros((N2, T), np.complex128)
+    for i in range(N2):
+        xi = rademacher(seed, i | COARSE_STREAM, n2).astype(np.complex128)
+        a = solve2(xi) - P2 @ solve3(P2.conj().T @ xi)
+        X2[i] = contract(P1 @ xi, P1 @ a, dims, gamma5)
+    X3 = np.zeros((N3, T), np.complex128)
+    for i in range(N3):
+        zeta = rademacher(seed, i | LEVEL3_STREAM, n3).astype(np.complex128)
+        X3[i] = contract(P1 @ (P2 @ zeta), P1 @ (P2 @ solve3(zeta)), dims, gamma5)
+    return X1, X2, X3
 
 
 def mlmc_allocation(V, C, eps):

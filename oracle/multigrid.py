@@ -80,3 +80,44 @@ def coarse_operator(Dmat, P):
 def gamma5_coarse(nv, Vc):
     """gamma5 on the coarse space: +1 on half 0, -1 on half 1 of every coarse site."""
     return np.tile(np.concatenate([np.ones(nv), -np.ones(nv)]), Vc)
+
+
+# ---- a third level (Sec. 2 with L = 3; the hierarchy of the paper's Table 2) --
+# The coarse space is aggregated again: coarse sites (coarse extents cd, coarse
+# dof index 2 nv X + nv h + k) are grouped into aggregates of agg2 coarse sites
+# per direction, every level-2 test vector is restricted to each aggregate and
+# chirality half h (the coarse dofs of half h keep the chirality of the fine
+# spins they came from), and the pieces of one (aggregate, half) are
+# orthonormalised by modified Gram-Schmidt in test-vector order.  Level-3 dof
+# index = 2 nv2 Xcc + nv2 h + k.  D_3 = P_2^dag D_c P_2 (Eq. 7 with l = 2).
+
+def aggregate_rows_coarse(cd, agg2, nv):
+    """For each (level-3 site, half): the sorted level-2 dof indices it owns.
+    Returns an int array (Vcc, 2, m) with m = nv * prod(agg2)."""
+    ccd = coarse_dims(cd, agg2)
+    Vcc = int(np.prod(ccd))
+    t, z, y, x = np.meshgrid(*[np.arange(L) for L in cd[::-1]], indexing='ij')
+    site = (x + cd[0] * (y + cd[1] * (z + cd[2] * t))).reshape(-1)
+    csite = ((x // agg2[0]) + ccd[0] * ((y // agg2[1]) + ccd[1] * ((z // agg2[2]) + ccd[2] * (t // agg2[3])))).reshape(-1)
+    rows = []
+    for c in range(Vcc):
+        sites = np.sort(site[csite == c])
+        rows.append([np.sort((2 * nv * sites[:, None] + nv * h + np.arange(nv)[None, :]).reshape(-1)) for h in range(2)])
+    return np.array(rows)
+
+
+def prolongator_coarse(tv2, cd, agg2, nv):
+    """P_2 as scipy CSR (2 nv Vc x 2 nv2 Vcc) from level-2 test vectors
+    tv2 (nv2, 2 nv Vc) (coarse dof order)."""
+    nv2 = tv2.shape[0]
+    rows = aggregate_rows_coarse(cd, agg2, nv)
+    Vcc = rows.shape[0]
+    n = tv2.shape[1]
+    R, C, Vals = [], [], []
+    for c in range(Vcc):
+        for h in range(2):
+            r = rows[c, h]
+            Q = mgs(tv2[:, r].T)
+            for k in range(nv2):
+                R.append(r); C.append(np.full(r.shape, 2 * nv2 * c + nv2 * h + k)); Vals.append(Q[:, k])
+    return sp.csr_matrix((np.concatenate(Vals), (np.concatenate(R), np.concatenate(C))), shape=(n, 2 * nv2 * Vcc))

@@ -231,3 +231,73 @@ def test_mlmc2_probe_coarse_level_reduces_to_plain_and_exact_limit(mg_probe):
     exact = np.array([d[ts == t].sum() for t in range(dims[3])])
     for i in range(2):
         assert np.abs(X2[i] - exact).max() < 1e-12 * np.abs(exact).max()
+
+
+# ---- three levels ----------------------------------------------------------
+
+@pytest.fixture(scope='module')
+def mg3():
+    dims, agg, nv = (4, 4, 4, 4), (2, 2, 2, 2), 6
+    U = synth.gauge_field(dims, 0.3, 1030)
+    D = wilson.sparse_matrix(U, 0.12, BC_AP)
+    P1 = multigrid.prolongator(synth.test_vectors(dims, nv, 31), dims, agg)
+    D2 = multigrid.coarse_operator(D, P1)
+    cd = multigrid.coarse_dims(dims, agg)
+    rng = np.random.default_rng(32)
+    nv2 = 6
+    tv2 = rng.standard_normal((nv2, D2.shape[0])) + 1j * rng.standard_normal((nv2, D2.shape[0]))
+    P2 = multigrid.prolongator_coarse(tv2, cd, (2, 2, 2, 2), nv)
+    D3 = multigrid.coarse_operator(D2, P2)
+    return dims, D, P1, D2, P2, D3
+
+
+def test_three_level_transfer_and_telescoping(mg3):
+    """P_2^dag P_2 = I; P_2 keeps the chirality halves (gamma5 of level 2
+    maps to gamma5 of level 3); the level split telescopes:
+    tr(M_1) + tr(P_1 M_2 P_1^dag) + tr(P_1 P_2 D_3^{-1} P_2^dag P_1^dag) = tr(D^{-1})
+    (Eqs. 10-11 with L = 3); the second oblique projector is idempotent."""
+    dims, D, P1, D2, P2, D3 = mg3
+    PP = (P2.conj().T @ P2).toarray()
+    assert np.abs(PP - np.eye(PP.shape[0])).max() < 1e-13
+    g2 = multigrid.gamma5_coarse(6, P1.shape[1] // 12)
+    g3 = multigrid.gamma5_coarse(6, P2.shape[1] // 12)
+    assert np.abs(g2[:, None] * P2.toarray() - P2.toarray() * g3[None, :]).max() < 1e-14
+    Dinv = solver.dense_inverse(D)
+    D2inv = solver.dense_inverse(D2)
+    D3inv = solver.dense_inverse(D3)
+    A1, A2 = P1.toarray(), P2.toarray()
+    M1 = Dinv - A1 @ D2inv @ A1.conj().T
+    M2 = D2inv - A2 @ D3inv @ A2.conj().T
+    total = np.trace(M1) + np.trace(A1 @ M2 @ A1.conj().T) + np.trace(A1 @ A2 @ D3inv @ A2.conj().T @ A1.conj().T)
+    assert abs(total - np.trace(Dinv)) < 1e-12 * abs(np.trace(Dinv))
+    Pi = A2 @ D3inv @ (A2.conj().T @ D2.toarray())
+    assert np.abs(Pi @ Pi - Pi).max() < 1e-10 * np.abs(Pi).max()
+
+
+def test_three_level_nine_point_sparsity(mg3):
+    """D_3 couples each level-3 site only to itself and its nearest
+    neighbours (a 9-point block stencil like D_2)."""
+    dims, D, P1, D2, P2, D3 = mg3
+    cd3 = multigrid.coarse_dims(multigrid.coarse_dims(dims, (2, 2, 2, 2)), (2, 2, 2, 2))
+    assert cd3 == (1, 1, 1, 1) and D3.shape == (12, 12)
+
+
+def test_mlmc3_unbiased_and_levels(mg3):
+    """Each level's sample mean is within 5 sigma of its exact trace, and the
+    three exact level traces sum to tr(D^{-1}) (B = 1)."""
+    dims, D, P1, D2, P2, D3 = mg3
+    Dinv = solver.dense_inverse(D)
+    D2inv = solver.dense_inverse(D2)
+    D3inv = solver.dense_inverse(D3)
+    X1, X2, X3 = estimators.mlmc3(lambda v: Dinv @ v, lambda v: D2inv @ v, lambda v: D3inv @ v, P1, P2, dims, 5,
+                                  48, 96, 256, False)
+    A1, A2 = P1.toarray(), P2.toarray()
+    exact = [np.trace(Dinv - A1 @ D2inv @ A1.conj().T),
+             np.trace(D2inv - A2 @ D3inv @ A2.conj().T),     # = tr(P_1 M_2 P_1^dag) since P_1^dag P_1 = I
+             np.trace(D3inv)]
+    for Xl, ex, M in ((X1, exact[0], Dinv - A1 @ D2inv @ A1.conj().T),
+                      (X2, exact[1], D2inv - A2 @ D3inv @ A2.conj().T), (X3, exact[2], D3inv)):
+        _, _, m, v = estimators.mean_and_variance(Xl)
+        V = estimators.hutchinson_variance(M)
+        assert abs(m - ex) < 5 * np.sqrt(V / Xl.shape[0]) + 1e-12
+    assert abs(sum(exact) - np.trace(Dinv)) < 1e-12 * abs(np.trace(Dinv))
