@@ -185,6 +185,35 @@ int wd_mlmc_level2_samples(wd_ctx *ctx, double *samples_out, int n2);
 int wd_connected_mlmc(wd_ctx *ctx, int N1, int N2, uint64_t seed, int prec, double tol, int batch, double *G,
                       double *var, double *samples1, double *samples2, int64_t *n_solves_out);
 
+/* ---- third multigrid level (Sec. 2 with L = 3) ----------------------- */
+
+/* Aggregates the coarse lattice of wd_mg_setup again (agg2[4] coarse sites per
+ * direction, dividing the coarse extents) and builds P_2 (level-2 test vectors
+ * restricted to each level-3 aggregate and chirality half, orthonormalised by
+ * modified Gram-Schmidt in test-vector order) and D_3 = P_2^dag D_c P_2 (Eq. 7
+ * with l = 2), a 9-point block stencil with 2 nv2 dofs per level-3 site.
+ * tv2 (host, nullable): [nv2][Vc][2 nv] complex level-2 test vectors; NULL
+ * builds them by tv_iters inverse iterations with the coarse solver from
+ * random coarse vectors (seed).  nv2: positive multiple of 6.  wd_mg_setup
+ * discards the third level. */
+int wd_mg3_setup(wd_ctx *ctx, const double *tv2, int nv2, const int agg2[4], int tv_iters, uint64_t seed);
+/* y = D_3 x on level-3 vectors [nrhs][Vcc][2 nv2] (device complex128, FP64). */
+int wd_coarse3_apply(wd_ctx *ctx, const double *in, double *out, int nrhs);
+/* y3 = P_2^dag y2 and y2 = P_2 y3 (device complex128; level-2 vectors
+ * [nrhs][Vc][2 nv], level-3 vectors [nrhs][Vcc][2 nv2]). */
+int wd_restrict2(wd_ctx *ctx, const double *y2, double *y3, int nrhs);
+int wd_prolong2(wd_ctx *ctx, const double *y3, double *y2, int nrhs);
+/* Three-level MLMC estimate of tr[B D^{-1}(t,t)] (Eq. 12 with L = 3):
+ *   X_1 = eta^dag B (D^{-1} - P_1 D_2^{-1} P_1^dag) eta              (N1 fine noise samples),
+ *   X_2 = (P_1 xi)^dag B P_1 (D_2^{-1} - P_2 D_3^{-1} P_2^dag) xi     (N2 coarse samples | 2^23),
+ *   X_3 = (P_1 P_2 zeta)^dag B P_1 P_2 D_3^{-1} zeta                 (N3 level-3 samples | 2^24).
+ * Level-3 solves run in FP64 to min(tol, 1e-12).  Outputs as trace_estimate
+ * for WD_MLMC2 (variance: sum_l s_l^2 / N_l); samples1..3 (host, nullable)
+ * [N_l][T][2].  N1, N2, N3 >= 2. */
+int trace_estimate_mlmc3(wd_ctx *ctx, int N1, int N2, int N3, uint64_t seed, int op, int prec, int batch,
+                         double tol, double *estimate, double *sample_var, int64_t *n_solves_out,
+                         double *samples1, double *samples2, double *samples3);
+
 /* Samples per level of a multilevel estimator (Sec. 2, Eq. 6): the N_l that
  * minimise the total cost sum_l N_l C_l for a target variance eps^2 of the
  * estimate, N_l = eps^-2 sqrt(V_l / C_l) sum_i sqrt(V_i C_i), rounded up (at

@@ -45,6 +45,12 @@ _SIGS = {
                                c_double, c_void_p, c_void_p, P(c_int64), c_void_p]),
     'wd_mlmc_level2_samples': (c_int, [c_void_p, c_void_p, c_int]),
     'mlmc_allocate': (c_int, [c_int, c_void_p, c_void_p, c_double, c_void_p]),
+    'wd_mg3_setup': (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_uint64]),
+    'wd_coarse3_apply': (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    'wd_restrict2': (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    'wd_prolong2': (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    'trace_estimate_mlmc3': (c_int, [c_void_p, c_int, c_int, c_int, c_uint64, c_int, c_int, c_int, c_double, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     'trace_estimate_mlmc_probe': (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_uint64, c_int, c_int,
                                           c_int, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     'wd_connected_mlmc': (c_int, [c_void_p, c_int, c_int, c_uint64, c_int, c_double, c_int, c_void_p, c_void_p,

@@ -152,6 +152,52 @@ def trace_estimate_mlmc_probe(h, dilution, d, N1, coarse_dil, d2, N2, T, seed=0,
                 samples1=s1[..., 0] + 1j * s1[..., 1], samples2=s2[..., 0] + 1j * s2[..., 1])
 
 
+def wd_mg3_setup(h, tv2, nv2, agg2, tv_iters=3, seed=0):
+    ptr = None
+    if tv2 is not None:
+        tv2 = np.ascontiguousarray(tv2, dtype=np.complex128)
+        ptr = _host_ptr(tv2)
+    check(lib.wd_mg3_setup(h, ptr, int(nv2), _iarr(agg2), int(tv_iters), ctypes.c_uint64(seed)), 'wd_mg3_setup')
+
+
+def wd_coarse3_apply(h, x, out):
+    import torch
+    check(lib.wd_coarse3_apply(h, _dev_ptr(x, torch.complex128, 'in'), _dev_ptr(out, torch.complex128, 'out'),
+                               x.shape[0]), 'wd_coarse3_apply')
+    return out
+
+
+def wd_restrict2(h, y2, y3):
+    import torch
+    check(lib.wd_restrict2(h, _dev_ptr(y2, torch.complex128), _dev_ptr(y3, torch.complex128), y2.shape[0]),
+          'wd_restrict2')
+    return y3
+
+
+def wd_prolong2(h, y3, y2):
+    import torch
+    check(lib.wd_prolong2(h, _dev_ptr(y3, torch.complex128), _dev_ptr(y2, torch.complex128), y3.shape[0]),
+          'wd_prolong2')
+    return y2
+
+
+def trace_estimate_mlmc3(h, N1, N2, N3, T, seed=0, op=1, prec=WD_MIXED_FP32, batch=0, tol=1e-10):
+    """Three-level MLMC.  Returns dict(estimate (T,), total, var (T,), var_total,
+    n_solves, samples1 (N1, T), samples2 (N2, T), samples3 (N3, T))."""
+    est = np.zeros(2 * (T + 1), np.float64)
+    var = np.zeros(T + 1, np.float64)
+    ns = ctypes.c_int64()
+    S = [np.zeros((N, T, 2), np.float64) for N in (N1, N2, N3)]
+    check(lib.trace_estimate_mlmc3(h, int(N1), int(N2), int(N3), ctypes.c_uint64(seed), int(op), int(prec),
+                                   int(batch), float(tol), _host_ptr(est), _host_ptr(var), ctypes.byref(ns),
+                                   _host_ptr(S[0]), _host_ptr(S[1]), _host_ptr(S[2])), 'trace_estimate_mlmc3')
+    e = est[0::2] + 1j * est[1::2]
+    out = dict(estimate=e[:T], total=e[T], var=var[:T], var_total=var[T], n_solves=ns.value)
+    for l in range(3):
+        out['samples%d' % (l + 1)] = S[l][..., 0] + 1j * S[l][..., 1]
+    return out
+
+
 def mlmc_allocate(V, C, eps):
     """Samples per level (int64 array) for variances V, costs C and a target
     standard error eps (host computation in libwd)."""

@@ -345,6 +345,7 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->launches = 0;
     c->prof = false;
     c->mg = nullptr;
+    c->mg3 = nullptr;
     c->last_n2 = 0;
     for (int p = 0; p < 5; ++p) { c->hop_R[p] = p == P64 || is_dd(p) ? 1 : 2; c->hop_threads[p] = 128; }
     for (int p = 0; p < 3; ++p) c->gauge[p] = nullptr;

@@ -122,6 +122,16 @@ struct wd_loop_graph {
     int kernels;                    // kernel launches per body (two iterations + condition)
 };
 
+// third multigrid level (wd_mg3.cu): level-2 sites aggregated by agg2
+struct wd_mg3 {
+    int nv2, ncd2;
+    int agg2[4], cd3[4];
+    int Vcc;
+    double2 *P2;       // [Vc][ncd][nv2]: column k of the half of coarse dof i
+    double2 *D3;       // [Vcc][9][ncd2][ncd2]
+    int *nbr3;         // [Vcc][9]
+};
+
 // Probing on the coarse level (wd_mlmc.cu): colour (sigma . X) mod nc of the
 // coarse site X (coarse extents cd), times dilution over the dil coarse dofs
 // of a site (dil = 1: none); m = nc * dil vectors per noise sample
@@ -169,6 +179,7 @@ struct wd_ctx {
     bool graph_off;                 // a graph call failed: plain loops from then on
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
     wd_mg *mg;
+    wd_mg3 *mg3;                    // third level (built on mg), nullable
     std::vector<double> last_level2;    // [n2][T][2]
     int last_n2;
 };

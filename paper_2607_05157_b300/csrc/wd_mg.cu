@@ -377,6 +377,18 @@ int coarse_apply64(wd_ctx *c, const double *x, double *y, const double *w, doubl
     return WD_OK;
 }
 
+// any 9-point block stencil (blocks [V][9][n][n], neighbour table [V][9]):
+// y = a*w + beta * A x, FP64 (the third level uses it)
+int block_stencil_apply64(wd_ctx *c, const double2 *A, const int *nbr, int n, int V, const double *x, double *y,
+                          const double *w, double a, double beta, int nrhs) {
+    dim3 grid(V, (nrhs + 7) / 8);
+    k_coarse_apply<double2, double><<<grid, n * 8, 0, c->st>>>(A, nbr, (const double2 *)x, (double2 *)y,
+                                                              (const double2 *)w, a, beta, n, V, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 int coarse_apply32(wd_ctx *c, const float *x, float *y, int nrhs) {
     wd_mg *g = c->mg;
     dim3 grid(g->Vc, (nrhs + 7) / 8);
@@ -470,7 +482,10 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
 
 using namespace wd;
 
+void wd_mg3_free(wd_ctx *c);   // wd_mg3.cu
+
 void wd_mg_free(wd_ctx *c) {
+    wd_mg3_free(c);               // the third level is built on this one
     if (!c || !c->mg) return;
     wd_mg *g = c->mg;
     cudaFree(g->P);

@@ -138,6 +138,17 @@ __global__ void k_accumulate_fields(int T, const double *part, int bps, double *
     X[((size_t)si * T + t) * 2 + 1] += im;
 }
 
+// three levels: estimate = sum of the means, variance = sum var_l / N_l
+__global__ void k_mlmc_combine3(const double *m1, const double *v1, const double *m2, const double *v2,
+                                const double *m3, const double *v3, int N1, int N2, int N3, int n, double *mean,
+                                double *var) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        mean[2 * t] = m1[2 * t] + m2[2 * t] + m3[2 * t];
+        mean[2 * t + 1] = m1[2 * t + 1] + m2[2 * t + 1] + m3[2 * t + 1];
+        var[t] = v1[t] / N1 + v2[t] / N2 + v3[t] / N3;
+    }
+}
+
 // estimate = mean_1 + mean_2, variance = var_1 / N1 + var_2 / N2
 __global__ void k_mlmc_combine(const double *m1, const double *v1, const double *m2, const double *v2, int N1, int N2,
                                int n, double *mean, double *var) {
@@ -163,6 +174,24 @@ static int contract_fields(wd_ctx *c, const double *ae, const double *ao, const 
 }
 
 static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double *var);
+
+// entry points of this file's kernels for the three-level estimator (wd_mg3.cu)
+int mlmc_contract_fields(wd_ctx *c, const double *ae, const double *ao, const double *be, const double *bo,
+                         int gamma5, int nrhs, double *X, int sample0) {
+    return contract_fields(c, ae, ao, be, bo, gamma5, nrhs, X, sample0, 1);
+}
+int mlmc_mean_var(wd_ctx *c, const double *X, int N, double *mean, double *var) {
+    return mean_var_dev(c, X, N, mean, var);
+}
+int coarse_noise_dev(wd_ctx *c, double *xi, uint64_t seed, int sample0, long ncoarse, int nrhs) {
+    const long n = ncoarse * nrhs;
+    k_coarse_noise<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, sample0, ncoarse, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+int mlmc_combine3(wd_ctx *c, const double *m1, const double *v1, const double *m2, const double *v2,
+                  const double *m3, const double *v3, int N1, int N2, int N3, double *mean, double *var);
 
 // level1 (nullable): fills X1 [N1][T][2] and adds its solves to *ns in place
 // of the plain Rademacher level 1 (WD_MLMC2_PROBE passes the probing one)
@@ -340,3 +369,13 @@ extern "C" int wd_mlmc_level2_samples(wd_ctx *c, double *samples_out, int n2) {
     memcpy(samples_out, c->last_level2.data(), sizeof(double) * c->last_level2.size());
     return WD_OK;
 }
+
+namespace wd {
+int mlmc_combine3(wd_ctx *c, const double *m1, const double *v1, const double *m2, const double *v2,
+                  const double *m3, const double *v3, int N1, int N2, int N3, double *mean, double *var) {
+    k_mlmc_combine3<<<1, 128, 0, c->st>>>(m1, v1, m2, v2, m3, v3, N1, N2, N3, c->g.T + 1, mean, var);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+}  // namespace wd
