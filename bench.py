@@ -267,6 +267,41 @@ def mlmc_probe_measure(wd, api, torch, synth):
             "probe_var_per_sample": svar(p["samples"])}
 
 
+def mlmc3_measure(wd, api, torch, synth):
+    """Row f3: three-level MLMC on 16^3x32 (kappa 0.13; aggregates 4^4 then
+    2^4, i.e. 4^3x8 and 2^3x4, 24 test vectors per level built on the GPU):
+    wall time, solves and per-sample variances of each level's total, beside
+    the two-level estimator on the same fine noise."""
+    import numpy as np
+    dims = (16, 16, 16, 32)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1008), 0.13, BC)
+    t0 = time.perf_counter()
+    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=5)
+    api.wd_mg3_setup(ctx.h, None, 24, (2, 2, 2, 2), tv_iters=3, seed=6)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+
+    def svar(S):
+        tot = S.sum(1)
+        return float(np.sum(np.abs(tot - tot.mean()) ** 2) / (len(tot) - 1))
+    api.trace_estimate_mlmc3(ctx.h, 2, 2, 2, 32, seed=1, op=1, tol=TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = api.trace_estimate_mlmc3(ctx.h, 4, 16, 64, 32, seed=2, op=1, tol=TOL)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    r2 = api.trace_estimate(ctx.h, wd.WD_MLMC2, 1, 4, 32, n2=16, seed=2, op=1, tol=TOL, with_samples=True)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx.close()
+    return {"workload": "16^3x32 kappa 0.13, tr[g5 D^-1(t,t)]; 3 levels: 4 fine + 16 level-2 + 64 level-3 samples; "
+                        "2 levels: 4 fine + 16 coarse samples (same fine noise)",
+            "setup_s": t_setup, "mlmc3_ms": 1e3 * (t1 - t0), "mlmc3_solves": r["n_solves"],
+            "mlmc3_var_per_sample": [svar(r["samples1"]), svar(r["samples2"]), svar(r["samples3"])],
+            "mlmc2_ms": 1e3 * (t2 - t1), "mlmc2_solves": r2["n_solves"],
+            "mlmc2_level1_var_per_sample": svar(r2["samples"])}
+
+
 def connected_measure(wd, api, torch, synth):
     """Row f4: connected pseudoscalar G(t) with the two-level decomposition on
     8^3x16 (N1 = 4 level-1 samples, N2 = 32 coarse samples): wall time, solves,
@@ -492,7 +527,8 @@ def main():
                              "gradient": gradient_measure(wd, api, torch, synth),
                              "batched": batched_measure(wd, torch, synth),
                              "mlmc_probe": mlmc_probe_measure(wd, api, torch, synth),
-                             "connected": connected_measure(wd, api, torch, synth)}
+                             "connected": connected_measure(wd, api, torch, synth),
+                             "mlmc3": mlmc3_measure(wd, api, torch, synth)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, dt, n = oracle_baseline(3)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
