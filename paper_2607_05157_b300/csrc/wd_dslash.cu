@@ -386,8 +386,9 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
 
 template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE, int PF = 0>
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
-    const int rb = blockIdx.x % A.nrb;
-    const int s = (blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
+    const int nsb = gridDim.x / A.nrb;
+    const int rb = A.rhs_major ? blockIdx.x / nsb : blockIdx.x % A.nrb;
+    const int s = (A.rhs_major ? blockIdx.x % nsb : blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
     if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE, PF>(A, rb, s);
 }
 
@@ -672,9 +673,15 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     if (A.nrhs <= 0) return cudaSuccess;
     // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined; R = 21, 22, 24:
     // timeslices staged through shared memory (FP32 arithmetic only); R = 31,
-    // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2
+    // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2; R = 51, 52,
+    // 54: plain with the site tile fastest in the block order
     constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
     if (R > 20 && R < 30) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
+    if (R > 50) {   // R = 51, 52, 54: plain, site tile fastest
+        if (!PACKED) return cudaErrorNotSupported;
+        A.rhs_major = 1;
+        R -= 50;
+    }
     int pf = 0;
     if (R > 30) {
         if (!PACKED) return cudaErrorNotSupported;

@@ -47,6 +47,10 @@ struct HopArgs {
     // anywhere): output sites more than one timeslice away get no hop term
     // (double-float stencil only; time-diluted and point sources)
     const int *tsup = nullptr;
+    // block order of the FP32/BF16 stencil: 0 = RHS tile fastest (the site
+    // tiles of all RHS run together), 1 = site tile fastest (the resident
+    // blocks sweep a few whole RHS fields at a time)
+    int rhs_major = 0;
 };
 
 // true if the hop can reach output timeslice t from RHS rhs's input support

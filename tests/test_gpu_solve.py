@@ -124,8 +124,11 @@ def test_graph_loop_matches_plain_loop(monkeypatch, prec):
     """The BiCGStab loop run as a captured CUDA graph with a device-side while
     node gives bit-identical solutions and iteration counts to the plain
     host-driven loop (the same kernels in the same order), on two solves in a
-    row (the second replays the cached graph), and meets the tolerance."""
+    row (the second replays the cached graph), and meets the tolerance.  The
+    autotuner is off: it picks launch variants by timing, and variants that
+    round differently would make the two contexts differ for that reason."""
     from paper_2607_05157_b300 import Context
+    monkeypatch.setenv('WD_NO_AUTOTUNE', '1')
     dims = (4, 4, 6, 8)
     U = synth.gauge_field(dims, 0.5, 1007)
     b = synth.spinors(dims, 5, 44)
