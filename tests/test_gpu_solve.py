@@ -146,3 +146,33 @@ def test_graph_loop_matches_plain_loop(monkeypatch, prec):
     x = out['graph'][1][0]
     for r in range(5):
         assert np.linalg.norm(b[r] - wilson.apply(U, x[r], 0.125, BC)) <= 1e-10 * np.linalg.norm(b[r]) * 1.01
+
+
+@pytest.mark.parametrize("shift", [200, -200])
+def test_fp64_norms_scale_invariant(shift):
+    """The FP64 norms (squares summed on the FP32 pipes from an exact integer
+    split of each double, with a running power-of-two exponent) keep the FP64
+    solve invariant under scaling the source by 2^shift far outside the FP32
+    range: the same iterations, the solution scaled bit for bit, the same
+    reported residual.  The reported residual of a solve stopped early (so
+    that the residual vector itself carries no cancellation) matches the
+    oracle's FP64 residual of the returned solution to 1e-12 relative."""
+    from paper_2607_05157_b300 import Context
+    dims = (4, 4, 4, 8)
+    U = synth.gauge_field(dims, 0.5, 1011)
+    b = synth.spinors(dims, 3, 71)
+    ctx = Context(dims, U, 0.125, BC)
+    x1, it1, res1 = ctx.solve(to_dev(b), tol=1e-11, prec=0)
+    x2, it2, res2 = ctx.solve(to_dev(b * 2.0 ** shift), tol=1e-11, prec=0)
+    x3, _, res3 = ctx.solve(to_dev(b * 2.0 ** shift), tol=1e-11, prec=0, max_iter=3, allow_noconv=True)
+    ctx.close()
+    x1, x2, x3 = x1.cpu().numpy(), x2.cpu().numpy(), x3.cpu().numpy() / 2.0 ** shift
+    assert np.array_equal(it1, it2)
+    assert np.array_equal(x1 * 2.0 ** shift, x2)
+    assert np.array_equal(res1, res2)
+    assert np.all(res1 <= 1e-11)
+    D = wilson.sparse_matrix(U, 0.125, BC)
+    for r in range(3):
+        tr = np.linalg.norm(b[r].reshape(-1) - D @ x3[r].reshape(-1)) / np.linalg.norm(b[r])
+        assert tr > 1e-5
+        assert abs(res3[r] - tr) <= 1e-12 * tr
