@@ -7,6 +7,8 @@
 // complex components of a site of each operand through the layout-aware
 // loaders (the chunk packing differs per precision), so operands of
 // different precisions can be mixed in one kernel.
+#include <algorithm>
+
 #include "wd_internal.h"
 
 namespace wd {
@@ -400,6 +402,122 @@ __global__ void __launch_bounds__(256) k_norm2_f64(const void *a, double *part, 
     block_partials<1>(d, part, nrhs, bpr);
 }
 
+// |a|^2 of double-float fields (each complex a float4 (re.h, im.h, re.l,
+// im.l), value h + l) with the same running-exponent float-pair sum as
+// k_norm2_f64.  The pair is first renormalised by TwoSum (a stencil output
+// need not be: after cancellation h can be 0 with l not), then v = (mh + ml)
+// 2^e with e the exponent of h, mh its significand and ml = l 2^-e carried
+// with the sign of l relative to h.
+__device__ __forceinline__ Split64 split_ddl(float h0, float l0, bool &nf) {
+    const float h = __fadd_rn(h0, l0), bb = __fsub_rn(h, h0);
+    const float l = __fadd_rn(__fsub_rn(h0, __fsub_rn(h, bb)), __fsub_rn(l0, bb));
+    Split64 r;
+    const unsigned hb = __float_as_uint(h);
+    const int ef = (int)((hb >> 23) & 0xFFu);
+    if (ef == 0 || ef == 0xFF) {
+        nf |= ef == 0xFF;
+        r.mh = r.ml = 0.f;
+        r.e = -4096;
+        return r;
+    }
+    r.e = ef - 127;
+    r.mh = __int_as_float(0x3F800000 | (int)(hb & 0x7FFFFFu));
+    r.ml = ldexpf((hb >> 31) ? -l : l, -r.e);
+    return r;
+}
+
+template <int UNR>
+__global__ void __launch_bounds__(256) k_norm2_ddl(const void *a, double *part, long nq, int nrhs, int bpr) {
+    const float4 *A = (const float4 *)a + (size_t)blockIdx.y * nq;
+    const FlatRange F = flat_range(nq);
+    float S = 0.f, C = 0.f;
+    int E = -4096;
+    bool nf = false;
+    for (long q = F.q0 + threadIdx.x; q < F.q1; q += UNR * blockDim.x) {
+        float4 ua[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const long qq = q + k * (long)blockDim.x;
+            ua[k] = qq < F.q1 ? __ldg(A + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        Split64 v[2 * UNR];
+        int Eg = -4096;
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            v[2 * k] = split_ddl(ua[k].x, ua[k].z, nf);
+            v[2 * k + 1] = split_ddl(ua[k].y, ua[k].w, nf);
+            Eg = max(Eg, max(v[2 * k].e, v[2 * k + 1].e));
+        }
+        if (Eg > E) {
+            const float sc = E == -4096 ? 0.f : pow2f_le0(2 * (E - Eg));
+            S = __fmul_rn(S, sc);
+            C = __fmul_rn(C, sc);
+            E = Eg;
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * UNR; ++j) {
+            const float sc = v[j].e == -4096 ? 0.f : pow2f_le0(v[j].e - E);
+            const float h = __fmul_rn(v[j].mh, sc), l = __fmul_rn(v[j].ml, sc);
+            const float p = __fmul_rn(h, h);
+            const float err = __fadd_rn(__fmaf_rn(h, h, -p), __fmul_rn(__fmul_rn(2.f, h), l));
+            const float s1 = __fadd_rn(S, p), bb = __fsub_rn(s1, S);
+            const float e1 = __fadd_rn(__fsub_rn(S, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+            S = s1;
+            C = __fadd_rn(C, __fadd_rn(e1, err));
+        }
+    }
+    double acc = 0.0;
+    if (E != -4096) {
+        const double t = __hiloint2double((E + 1023) << 20, 0);     // 2^E
+        acc = (((double)S + (double)C) * t) * t;
+    }
+    if (nf) acc = __longlong_as_double(0x7FF8000000000000LL);
+    double d[1] = {acc};
+    block_partials<1>(d, part, nrhs, bpr);
+}
+
+// FP32 copy of a double-float field times a per-RHS FP64 scale, on the FP32
+// pipes: out = RN(h + l) ms 2^es with scale = ms 2^es (ms rounded to FP32),
+// the power of two applied by ldexpf, so the scale may lie outside the FP32
+// range as long as the product does not.  Item i of a RHS is (site s, FP32
+// chunk j): the double-float chunks 2j, 2j+1 of s in, FP32 chunk j out.
+template <bool FL>
+__global__ void __launch_bounds__(256) k_ddl_to_f32(const void *a, void *b, const double *scale, long units) {
+    const long per = 6 * units;
+    const float4 *A = (const float4 *)a + (size_t)blockIdx.y * 12 * units;
+    float4 *B = (float4 *)b + (size_t)blockIdx.y * per;
+    float ms = 1.f;
+    int es = 0;
+    if (scale) {
+        const double sd = scale[blockIdx.y];
+        bool nf = false;
+        const Split64 sp = split64(__double2loint(sd), __double2hiint(sd), nf);
+        if (sp.e == -4096) { ms = nf ? __int_as_float(0x7FC00000) : 0.f; }
+        else {
+            ms = __fadd_rn(sp.mh, sp.ml);
+            es = sp.e;
+            if (sd < 0) ms = -ms;
+        }
+    }
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < per; i += (long)gridDim.x * blockDim.x) {
+        long i0, i1, o;
+        if (FL) {
+            const long u = i / 6, j = i - 6 * u;
+            i0 = 12 * u + 2 * j; i1 = i0 + 1; o = i;
+        } else {
+            const long j = i / units, s = i - j * units;
+            i0 = 2 * j * units + s; i1 = i0 + units; o = i;
+        }
+        const float4 v0 = __ldg(A + i0), v1 = __ldg(A + i1);
+        float4 r;
+        r.x = ldexpf(__fmul_rn(__fadd_rn(v0.x, v0.z), ms), es);
+        r.y = ldexpf(__fmul_rn(__fadd_rn(v0.y, v0.w), ms), es);
+        r.z = ldexpf(__fmul_rn(__fadd_rn(v1.x, v1.z), ms), es);
+        r.w = ldexpf(__fmul_rn(__fadd_rn(v1.y, v1.w), ms), es);
+        B[o] = r;
+    }
+}
+
 // ---- conversions and mixed axpy ---------------------------------------------
 template <typename SA, typename SB, bool FL>
 __global__ void k_convert(const void *a, void *b, const double *scale, long Vh, long n) {
@@ -445,6 +563,15 @@ int blas_copy_convert(wd_ctx *c, const Space &sp, int ps, const void *src, int p
                       const double *scale) {
     const long Vh = sp.units, n = Vh * nrhs;
     if (n == 0) return WD_OK;
+    if (ps == PDDL) {
+        if (pd != P32) { set_error("copy: double-float source needs an FP32 destination"); return WD_EINVAL; }
+        const unsigned bx = (unsigned)std::max(1, std::min(64, reduction_bpr(Vh, nrhs)));
+        if (sp.flat) k_ddl_to_f32<true><<<dim3(bx, nrhs), 256, 0, c->st>>>(src, dst, scale, Vh);
+        else k_ddl_to_f32<false><<<dim3(bx, nrhs), 256, 0, c->st>>>(src, dst, scale, Vh);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
+        return WD_OK;
+    }
     WD_DISPATCH_FLAT(sp.flat, FL, WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB,
         k_convert<SA, SB, FL><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, Vh, n))));
     c->launches++;
@@ -481,6 +608,8 @@ int blas_norm2(wd_ctx *c, const Space &sp, int prec, const void *a, int nrhs, do
     dim3 grid(bpr, nrhs);
     if (prec == P64)
         k_norm2_f64<4><<<grid, 256, 0, c->st>>>(a, part, 12L * sp.units, nrhs, bpr);
+    else if (prec == PDDL)
+        k_norm2_ddl<4><<<grid, 256, 0, c->st>>>(a, part, 12L * sp.units, nrhs, bpr);
     else if (prec == P32)
         k_norm2_flat<float, 4><<<grid, 256, 0, c->st>>>(a, part, 6L * sp.units, nrhs, bpr);
     else

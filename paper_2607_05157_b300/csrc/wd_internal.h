@@ -272,6 +272,9 @@ struct Problem {
     OpFn op64;  void *u64;      // FP64 operator (FP64 mode)
     OpFn oplo;  void *ulo;      // inner operator, inputs in pp, outputs in pw
     ResFn res64; void *ures;    // FP64 residual
+    // res64 writes the residual in the double-float layout (PDDL) instead of
+    // FP64: its norm and its FP32 copy then run on the FP32 pipes
+    bool res_ddl = false;
     const char *tag;            // workspace name prefix
     bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
     uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};

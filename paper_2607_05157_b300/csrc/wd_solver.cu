@@ -269,11 +269,19 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
     WD_TRY(ws_get(c, (tag + ".rn2").c_str(), sizeof(double) * nrhs, (void **)&rn2_d));
     WD_TRY(hws_get(c, (tag + ".hscale").c_str(), sizeof(double) * 2 * nrhs, (void **)&hsc));
     WD_TRY(blas_zero(c, x, f64));
-    WD_CUDA(cudaMemcpyAsync(r64, b, f64, cudaMemcpyDeviceToDevice, c->st));
+    // residual r64: FP64, or the double-float layout (same size) when the
+    // problem's residual writes it
+    const int rp = P.res_ddl ? PDDL : P64;
+    if (P.res_ddl) {
+        WD_CUDA(launch_to_ddl(b, r64, 12L * P.sp.units * nrhs, c->st));
+        c->launches++;
+    } else {
+        WD_CUDA(cudaMemcpyAsync(r64, b, f64, cudaMemcpyDeviceToDevice, c->st));
+    }
     std::vector<double> rn2(nrhs);
     int used = 0;
     for (int outer = 0; outer < 64; ++outer) {
-        WD_TRY(blas_norm2(c, P.sp, P64, r64, nrhs, rn2_d));
+        WD_TRY(blas_norm2(c, P.sp, rp, r64, nrhs, rn2_d));
         WD_CUDA(cudaMemcpyAsync(rn2.data(), rn2_d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
         WD_CUDA(cudaStreamSynchronize(c->st));
         int open = 0;
@@ -295,7 +303,7 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
         if (open == 0 || used >= max_iter) break;
         WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
         // b_lo = r / |r|   (zero for converged RHS, which then stay inactive)
-        WD_TRY(blas_copy_convert(c, P.sp, P64, r64, pw, blo, nrhs, scale_d));
+        WD_TRY(blas_copy_convert(c, P.sp, rp, r64, pw, blo, nrhs, scale_d));
         WD_TRY(bicg_init(c, pw, pp, V, blo, nrhs, inner_tol, nullptr));
         int ran = 0;
         WD_TRY(bicg_run(c, pw, pp, V, nrhs, max_iter - used, &ran));
@@ -332,12 +340,12 @@ static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
 
 // r = b - D_hat x = b - x + k^2 H_eo H_oe x on FP64 fields, with the stencil
 // S->pin (P64, or PDD: double-float arithmetic, the odd intermediate kept in
-// the double-float layout)
+// the double-float layout); r in S->pout (P64, PDD = FP64, or PDDL)
 static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
     SchurArgs *S = (SchurArgs *)u;
     const int pt = S->pin == PDD ? PDDL : S->pin;
     WD_TRY(hop(c, S->pin, pt, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
-    return hop(c, pt, S->pin, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
+    return hop(c, pt, S->pout, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
 }
 
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
@@ -373,12 +381,13 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     const int pp = prec == P16 ? P16 : (prec == P32 ? P32 : P64);
     void *tmplo = nullptr;
     if (prec != P64) WD_TRY(ws_get(c, "sol.tmplo", field_bytes(c->g, pp, nrhs), &tmplo));
-    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo}, sres = {pd, pd, tmp64};
+    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo}, sres = {pd, pd == PDD ? PDDL : pd, tmp64};
     Problem P;
     P.sp = sp;
     P.op64 = schur_op; P.u64 = &s64;
     P.oplo = schur_op; P.ulo = &slo;
     P.res64 = schur_res64; P.ures = &sres;
+    P.res_ddl = sres.pout == PDDL;
     P.tag = "fine";
     // the Schur operator's launches see the precisions and the odd workspace
     P.graph_ok = true;
