@@ -51,9 +51,10 @@ size_t field_bytes(const Geom &g, int prec, int nrhs) {
 }
 
 int reduction_bpr(long units, int nrhs) {
-    // aim for ~8 CTAs of 256 threads per SM over all RHS (one wave of
-    // resident CTAs of the light kernels), >= 1 unit per thread
-    int want = (8 * 148 + nrhs - 1) / (nrhs > 0 ? nrhs : 1);
+    // at most one wave of the light reduction kernels (7 resident CTAs of 256
+    // threads per SM): a second, partial wave costs more than fewer, longer
+    // CTAs; >= 1 unit per thread
+    int want = (7 * 148) / (nrhs > 0 ? nrhs : 1);
     int maxb = (int)((units + 255) / 256);
     if (want > maxb) want = maxb;
     if (want < 1) want = 1;
