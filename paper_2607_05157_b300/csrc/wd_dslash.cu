@@ -392,6 +392,18 @@ __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
     if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, PIPE, PF>(A, rb, s);
 }
 
+// Register-capped variant: the same site body with __launch_bounds__(128,
+// MINB), so that MINB CTAs of 128 threads fit per SM (more resident warps to
+// hide the neighbour-load latency, at the price of spills if the cap is
+// below what the body needs); site tile fastest in the block order
+template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, int MINB>
+__global__ void __launch_bounds__(128, MINB) hop_kernel_f2_cap(HopArgs A) {
+    const int nsb = gridDim.x / A.nrb;
+    const int rb = blockIdx.x / nsb;
+    const int s = (blockIdx.x % nsb) * blockDim.x + threadIdx.x;
+    if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, false, 0>(A, rb, s);
+}
+
 // Persistent batched stencil over several lattices (row a11): one launch walks
 // a static work list of (lattice, site tile, RHS tile) items -- the items of
 // lattice j are the blocks [base_j, base_j + blocks_j) -- with a grid sized to
@@ -674,9 +686,20 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     // R = 1, 2, 4: plain; R = 11, 12, 14: software-pipelined; R = 21, 22, 24:
     // timeslices staged through shared memory (FP32 arithmetic only); R = 31,
     // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2; R = 51, 52,
-    // 54: plain with the site tile fastest in the block order
+    // 54: plain with the site tile fastest in the block order; R = 62: two RHS,
+    // registers capped for 20 resident warps per SM
     constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
     if (R > 20 && R < 30) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
+    if (R == 62) {   // two RHS, register cap for 5 CTAs of 128 threads per SM, site tile fastest
+        if (!PACKED || threads > 128) return cudaErrorNotSupported;
+        A.nrb = (A.nrhs + 1) / 2;
+        const dim3 grid((unsigned)(((A.g.Vh + threads - 1) / threads) * A.nrb));
+        if constexpr (PACKED) {
+            if (dag) hop_kernel_f2_cap<SIn, SOut, SW, G, 2, true, 5><<<grid, threads, 0, st>>>(A);
+            else hop_kernel_f2_cap<SIn, SOut, SW, G, 2, false, 5><<<grid, threads, 0, st>>>(A);
+        }
+        return cudaGetLastError();
+    }
     if (R > 50) {   // R = 51, 52, 54: plain, site tile fastest
         if (!PACKED) return cudaErrorNotSupported;
         A.rhs_major = 1;

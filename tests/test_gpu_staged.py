@@ -23,7 +23,7 @@ def override():
     os.environ.pop('WD_HOP_R', None)
 
 
-@pytest.mark.parametrize("code", [1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 54])
+@pytest.mark.parametrize("code", [1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 54, 62])
 @pytest.mark.parametrize("prec,tol", [(1, 3e-6), (2, 2e-2)])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_variant_parity(override, code, prec, tol, dagger):
