@@ -55,6 +55,26 @@ def env_rank():
     return int(os.environ.get('RANK', 0)), int(os.environ.get('WORLD_SIZE', 1)), int(os.environ.get('LOCAL_RANK', 0))
 
 
+def rank_seed(rank):
+    """Noise seed of one replica: every rank draws its own samples."""
+    return NOISE_SEED + 7919 * rank
+
+
+def combine_ranks(dist, ms, nbytes, device):
+    """Whole-job numbers over replicas: the slowest rank's time (max) and the
+    algorithmic bytes of all ranks (sum), so value = all ranks' bytes / the
+    job's time.  dist None: one process."""
+    if dist is None:
+        return ms, nbytes
+    import torch
+    t = torch.tensor([ms, nbytes], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json')))
@@ -398,7 +418,7 @@ def main():
     T = DIMS[3]
     gauge = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
     ctx = wd.Context(DIMS, gauge, KAPPA, BC)
-    seed0 = NOISE_SEED + 7919 * rank
+    seed0 = rank_seed(rank)
 
     def trace_only(i, p=prec, batch=SAMPLES * T):
         return api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, SAMPLES, T, seed=seed0 + i, op=1,
@@ -446,12 +466,7 @@ def main():
     n_hop, ms_hop, by_hop = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
     n_h64, ms_h64, by_h64 = api.wd_profile_get(ctx.h, wd.WD_K_HOP64)
     api.wd_profile(ctx.h, False)
-    step_bytes = by_hop + by_h64
-    if dist:
-        t = torch.tensor([ms, step_bytes], dtype=torch.float64, device='cuda')
-        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, step_bytes = float(mx[0]), float(sm[1])
+    ms, step_bytes = combine_ranks(dist, ms, by_hop + by_h64, 'cuda')
     value = step_bytes / (ms * 1e-3) / 1e9
 
     # end to end through the public API: host (pinned) links uploaded and
@@ -468,12 +483,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
-    e_bytes = by_hop + by_h64
-    if dist:
-        t = torch.tensor([e_ms, e_bytes], dtype=torch.float64, device='cuda')
-        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        e_ms, e_bytes = float(mx[0]), float(sm[1])
+    e_ms, e_bytes = combine_ranks(dist, e_ms, by_hop + by_h64, 'cuda')
     h2d = gauge.nbytes
     d2h = 8 * (2 * (T + 1) + (T + 1))
 
