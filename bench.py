@@ -11,7 +11,9 @@ C(t) = sum_x |D^{-1}(x,t;0,0)|^2 from 12 point sources, each solve to a true
 FP64 relative residual of 1e-10 by FP32 (or BF16) BiCGStab inside FP64 defect
 correction.
 
-A step = one trace_estimate call plus one wd_point_correlator call: RHS generation on the device, even-odd
+A step = one trace_estimate call plus one wd_point_correlator call, issued from two host threads on two
+contexts with their own CUDA streams so that the two independent solves overlap on the GPU (--serial: one
+after the other on one context): RHS generation on the device, even-odd
 source, 256-RHS batched mixed-precision solve (stencil, BLAS-1, FP64 residual),
 odd-site reconstruction, FP64 per-timeslice contraction, mean and sample
 variance.  `value` = algorithmic stencil bytes moved by all stencil launches
@@ -386,6 +388,8 @@ def main():
     ap.add_argument('--prec', choices=['fp32', 'bf16'], default='fp32')
     ap.add_argument('--impl', choices=['wd', 'reference'], default='wd')
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--serial', action='store_true',
+                    help='run the correlator after the trace solve on one context (no second stream)')
     ap.add_argument('--no-fp64-compare', action='store_true')
     ap.add_argument('--no-secondary', action='store_true', help='skip the coarse / gradient / batched measurements')
     ap.add_argument('--coarse-only', action='store_true', help='only the tensor-core coarse stencil measurement')
@@ -417,17 +421,38 @@ def main():
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
     T = DIMS[3]
     gauge = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
-    ctx = wd.Context(DIMS, gauge, KAPPA, BC)
+    # The two independent parts of a step run on two contexts with their own
+    # streams, from two host threads, so that the 12-RHS correlator solve (small,
+    # latency-bound launches) fills the gaps of the 256-RHS trace solve; with
+    # --serial both run one after the other on one context.
+    if args.serial:
+        ctx = ctx_c = wd.Context(DIMS, gauge, KAPPA, BC)
+        pool = None
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        s_tr, s_c = torch.cuda.Stream(), torch.cuda.Stream()
+        ctx = wd.Context(DIMS, gauge, KAPPA, BC, stream=s_tr)
+        ctx_c = wd.Context(DIMS, gauge, KAPPA, BC, stream=s_c)
+        pool = ThreadPoolExecutor(1)
+    ctxs = [ctx] if ctx_c is ctx else [ctx, ctx_c]
     seed0 = rank_seed(rank)
 
     def trace_only(i, p=prec, batch=SAMPLES * T):
         return api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, SAMPLES, T, seed=seed0 + i, op=1,
                                   prec=p, batch=batch, tol=TOL)
 
-    def step(i, p=prec, batch=SAMPLES * T):
+    def correlator(p=prec):
+        return api.wd_point_correlator(ctx_c.h, (0, 0, 0, 0), T, prec=p, tol=TOL)
+
+    def step(i, p=prec, batch=SAMPLES * T, concurrent=True):
         # the whole workload: 256 time-diluted RHS for O(t) and 12 point sources for C(t)
-        r = trace_only(i, p, batch)
-        r['C'] = api.wd_point_correlator(ctx.h, (0, 0, 0, 0), T, prec=p, tol=TOL)
+        if pool is not None and concurrent:
+            fc = pool.submit(correlator, p)
+            r = trace_only(i, p, batch)
+            r['C'] = fc.result()
+        else:
+            r = trace_only(i, p, batch)
+            r['C'] = correlator(p)
         return r
 
     for i in range(args.warmup):
@@ -438,7 +463,7 @@ def main():
     torch.cuda.synchronize()
     # timed region: the steps as a user runs them (no per-launch events, so the
     # BiCGStab loops run as captured graphs)
-    l0 = api.wd_launch_count(ctx.h)
+    l0 = sum(api.wd_launch_count(c.h) for c in ctxs)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record()
@@ -449,23 +474,30 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    launches = api.wd_launch_count(ctx.h) - l0
+    launches = sum(api.wd_launch_count(c.h) for c in ctxs) - l0
 
     # profiled repetition of the same steps (same seeds, so the same work):
     # CUDA events around every stencil launch on the library's stream give the
     # per-kernel durations and algorithmic bytes of the roofline.  Events
     # cannot sit inside a captured graph, so these steps run plain launches.
-    api.wd_profile(ctx.h, True)
+    # The two parts run one after the other here, so that no kernel's
+    # duration includes another stream's work.
+    for c in ctxs:
+        api.wd_profile(c.h, True)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     for i in range(args.steps):
-        step(1000 + i)
+        step(1000 + i, concurrent=False)
     p1.record()
     torch.cuda.synchronize()
     ms_prof = p0.elapsed_time(p1)
-    n_hop, ms_hop, by_hop = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
-    n_h64, ms_h64, by_h64 = api.wd_profile_get(ctx.h, wd.WD_K_HOP64)
-    api.wd_profile(ctx.h, False)
+    n_hop = ms_hop = by_hop = n_h64 = ms_h64 = by_h64 = 0
+    for c in ctxs:
+        n, t, b = api.wd_profile_get(c.h, wd.WD_K_HOP)
+        n_hop, ms_hop, by_hop = n_hop + n, ms_hop + t, by_hop + b
+        n, t, b = api.wd_profile_get(c.h, wd.WD_K_HOP64)
+        n_h64, ms_h64, by_h64 = n_h64 + n, ms_h64 + t, by_h64 + b
+        api.wd_profile(c.h, False)
     ms, step_bytes = combine_ranks(dist, ms, by_hop + by_h64, 'cuda')
     value = step_bytes / (ms * 1e-3) / 1e9
 
@@ -478,13 +510,14 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(args.steps):
-        wd.lib.wd_update_gauge(ctx.h, ctypes.c_void_p(gptr), ctypes.c_double(KAPPA))
+        for c in ctxs:
+            wd.lib.wd_update_gauge(c.h, ctypes.c_void_p(gptr), ctypes.c_double(KAPPA))
         step(1000 + i)
     e1.record()
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
     e_ms, e_bytes = combine_ranks(dist, e_ms, by_hop + by_h64, 'cuda')
-    h2d = gauge.nbytes
+    h2d = gauge.nbytes * len(ctxs)
     d2h = 8 * (2 * (T + 1) + (T + 1))
 
     peaks = measured_peaks()
@@ -545,7 +578,10 @@ def main():
                                 "sample": f"3 of the 256 time-diluted solves of one step ({dt:.1f} s, {n} applies of D)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs:
+        c.close()
+    if pool is not None:
+        pool.shutdown()
     if dist:
         dist.destroy_process_group()
 
