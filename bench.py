@@ -455,8 +455,11 @@ def main():
             r['C'] = correlator(p)
         return r
 
+    # warm-up one part after the other: the autotuner times its launch-shape
+    # candidates on the first call of each shape, and the other stream's work
+    # would distort those timings
     for i in range(args.warmup):
-        step(i)
+        step(i, concurrent=False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

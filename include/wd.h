@@ -32,7 +32,17 @@
  *   that return host results synchronise that stream before returning.
  *   Every entry point returns a wd_status; on failure wd_last_error() gives
  *   a message (thread-local, valid until the next call on that thread).
- *   No entry point is safe to call concurrently on the same context.
+ *   No entry point is safe to call concurrently on the same context;
+ *   different contexts (each with its own stream) may be driven from
+ *   different host threads at once.
+ *   Launch shapes: the first stencil launch of each (input precision, output
+ *   precision, RHS-count bucket) on a context times the kernel's launch-shape
+ *   candidates on that context's stream and keeps the fastest.  Work of other
+ *   streams running meanwhile distorts that choice, so make the first call of
+ *   each shape on an otherwise idle GPU.  WD_NO_AUTOTUNE=1 (read at
+ *   wd_create) keeps the default shapes; WD_HOP_R / WD_DD_R pin one.  For a
+ *   fixed shape every result is bit-reproducible; shapes whose FP32 sums run
+ *   in another order can differ in the last bits.
  */
 #ifndef WD_H
 #define WD_H
