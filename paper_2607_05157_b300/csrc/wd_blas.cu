@@ -643,8 +643,43 @@ __global__ void k_bicg_init(const void *b, void *x, void *r, void *rh, void *p, 
     block_partials<1>(d, part, nrhs, bpr);
 }
 
+// The iteration kernels below skip every RHS whose state is inactive
+// (converged or broken down): its x and r keep their final values, and the
+// other fields of that RHS are neither read nor written again in this run.
+// Stencil launches inside the run walk the list of the active RHS that
+// k_scal_init / k_scal_beta build after every update of the states
+// (HopArgs::alist).
+
+// list[0 .. count) = the active RHS in ascending order (count: the number
+// k_scal_init / k_scal_beta store); run by the whole single block of those
+// kernels after their state updates, fixed order
+__device__ void build_active_list(const BiState *st, int nrhs, int *list) {
+    __shared__ int wc[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nrhs; c0 += blockDim.x) {
+        const int r = c0 + threadIdx.x;
+        const bool a = r < nrhs && st[r].active;
+        const unsigned m = __ballot_sync(0xffffffffu, a);
+        if (lane == 0) wc[wid] = __popc(m);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < wid; ++w) off += wc[w];
+        if (a) list[off + __popc(m & ((1u << lane) - 1u))] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < nw; ++w) tot += wc[w];
+            base += tot;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm2, double tol2, int nrhs, int bpr,
-                            int *count) {
+                            int *count, int *list) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -668,6 +703,7 @@ __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm
     }
     __syncthreads();
     if (threadIdx.x == 0) *count = cnt;
+    build_active_list(st, nrhs, list);
 }
 
 // partial sums of conj(a).b (slots 0, 1) and optionally |a|^2 (slot 2)
@@ -707,18 +743,30 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
+// alpha = rho / (r_hat, v) of one active RHS; breakdown masks the RHS
+__device__ void scal_alpha(BiState &s, double2 d) {
+    const double2 al = zdiv(s.rho, d);
+    if ((d.x == 0.0 && d.y == 0.0) || !zfinite(al)) {
+        s.active = 0; s.flag = 1;
+        s.alpha = make_double2(0, 0); s.omega = make_double2(0, 0); s.beta = make_double2(0, 0);
+        return;
+    }
+    s.alpha = al;
+}
+
+// omega = (t, s) / |t|^2 of one active RHS
+__device__ void scal_omega(BiState &s, double2 ts, double tt) {
+    if (tt == 0.0) { s.omega = make_double2(0, 0); return; }   // t = A s = 0 => s = 0
+    const double2 om = make_double2(ts.x / tt, ts.y / tt);
+    if (!zfinite(om)) { s.active = 0; s.flag = 1; s.omega = make_double2(0, 0); s.alpha = make_double2(0, 0); return; }
+    s.omega = om;
+}
+
 __global__ void k_scal_alpha(BiState *st, const double *part, int nrhs, int bpr) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
         BiState &s = st[r];
         if (!s.active) { s.alpha = make_double2(0, 0); continue; }
-        const double2 d = make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr));
-        double2 al = zdiv(s.rho, d);
-        if ((d.x == 0.0 && d.y == 0.0) || !zfinite(al)) {
-            s.active = 0; s.flag = 1;
-            s.alpha = make_double2(0, 0); s.omega = make_double2(0, 0); s.beta = make_double2(0, 0);
-            continue;
-        }
-        s.alpha = al;
+        scal_alpha(s, make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr)));
     }
 }
 
@@ -726,16 +774,12 @@ __global__ void k_scal_omega(BiState *st, const double *part, int nrhs, int bpr)
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
         BiState &s = st[r];
         if (!s.active) { s.omega = make_double2(0, 0); continue; }
-        const double2 ts = make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr));
-        const double tt = sum_part(part, 2, r, nrhs, bpr);
-        if (tt == 0.0) { s.omega = make_double2(0, 0); continue; }   // t = A s = 0 => s = 0
-        double2 om = make_double2(ts.x / tt, ts.y / tt);
-        if (!zfinite(om)) { s.active = 0; s.flag = 1; s.omega = make_double2(0, 0); s.alpha = make_double2(0, 0); continue; }
-        s.omega = om;
+        scal_omega(s, make_double2(sum_part(part, 0, r, nrhs, bpr), sum_part(part, 1, r, nrhs, bpr)),
+                   sum_part(part, 2, r, nrhs, bpr));
     }
 }
 
-__global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, int *count) {
+__global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, int *count, int *list) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -759,39 +803,7 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
     }
     __syncthreads();
     if (threadIdx.x == 0) *count = cnt;
-}
-
-// The iteration kernels below skip every RHS whose state is inactive
-// (converged or broken down): its x and r keep their final values, and the
-// other fields of that RHS are neither read nor written again in this run.
-// Stencil launches inside the run walk the list of the active RHS that
-// k_active_list builds after every update of the states (HopArgs::alist).
-
-// list[0 .. count) = the active RHS in ascending order (count: the number
-// k_scal_init / k_scal_beta stored); one block, fixed order
-__global__ void k_active_list(const BiState *st, int nrhs, int *list) {
-    __shared__ int wc[32];
-    __shared__ int base;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    for (int c0 = 0; c0 < nrhs; c0 += blockDim.x) {
-        const int r = c0 + threadIdx.x;
-        const bool a = r < nrhs && st[r].active;
-        const unsigned m = __ballot_sync(0xffffffffu, a);
-        if (lane == 0) wc[wid] = __popc(m);
-        __syncthreads();
-        int off = base;
-        for (int w = 0; w < wid; ++w) off += wc[w];
-        if (a) list[off + __popc(m & ((1u << lane) - 1u))] = r;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < nw; ++w) tot += wc[w];
-            base += tot;
-        }
-        __syncthreads();
-    }
+    build_active_list(st, nrhs, list);
 }
 
 // s = r - alpha v
@@ -880,9 +892,8 @@ int bicg_init(wd_ctx *c, int pw, int pp, BiVecs &V, const void *b, int nrhs, dou
     dim3 grid(V.bpr, nrhs);
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP,
         k_bicg_init<SW, SP, FL><<<grid, 256, 0, c->st>>>(b, V.x, V.r, V.rh, V.p, V.part, Vh, nrhs, V.bpr)));
-    k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count);
-    k_active_list<<<1, 256, 0, c->st>>>(V.st, nrhs, V.alist);
-    c->launches += 3;
+    k_scal_init<<<1, 256, 0, c->st>>>(V.st, V.part, bnorm2_dev, tol_rel * tol_rel, nrhs, V.bpr, V.count, V.alist);
+    c->launches += 2;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -892,10 +903,9 @@ int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
-    const int sb = (nrhs + 127) / 128;
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
         k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr, V.st);
-        k_scal_alpha<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
+        k_scal_alpha<<<(nrhs + 127) / 128, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
     }));
     c->launches += 3;
@@ -924,16 +934,14 @@ int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     const long Vh = V.sp.units, n = Vh * nrhs;
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
-    const int sb = (nrhs + 127) / 128;
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
         k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr, V.st);
-        k_scal_omega<<<sb, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
+        k_scal_omega<<<(nrhs + 127) / 128, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
         XrUpdate<SW, SP, FL>::run(c, V, nrhs);
-        k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count);
-        k_active_list<<<1, 256, 0, c->st>>>(V.st, nrhs, V.alist);
+        k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count, V.alist);
         k_bicg_p<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
     }));
-    c->launches += 6;
+    c->launches += 5;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
