@@ -259,26 +259,53 @@ __global__ void k_accumulate(EstParams P, int T, const double *part, int bps, do
 
 // mean and sample variance per timeslice and of the total over timeslices.
 // out_mean[2*(T+1)], out_var[T+1]
+// sum of v over the block (blockDim.x a power of two <= 256), fixed tree order;
+// every thread gets the result
+__device__ double block_sum_fixed(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// per-timeslice and total means and sample variances of X [N][T][2]: one
+// thread per timeslice column; the total (sum over t of each sample) with the
+// samples spread over the block and block sums in a fixed order
 __global__ void k_mean_var(const double *X, int N, int T, double *out_mean, double *out_var) {
-    for (int t = threadIdx.x; t <= T; t += blockDim.x) {
+    __shared__ double sh[256];
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
         double mr = 0, mi = 0;
-        for (int i = 0; i < N; ++i) {
-            double xr = 0, xi = 0;
-            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
-            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
-            mr += xr; mi += xi;
-        }
+        for (int i = 0; i < N; ++i) { mr += X[((size_t)i * T + t) * 2]; mi += X[((size_t)i * T + t) * 2 + 1]; }
         mr /= N; mi /= N;
         double v = 0;
         for (int i = 0; i < N; ++i) {
-            double xr = 0, xi = 0;
-            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
-            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
-            v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
+            const double xr = X[((size_t)i * T + t) * 2] - mr, xi = X[((size_t)i * T + t) * 2 + 1] - mi;
+            v += xr * xr + xi * xi;
         }
         out_mean[2 * t] = mr;
         out_mean[2 * t + 1] = mi;
         out_var[t] = N > 1 ? v / (N - 1) : NAN;
+    }
+    double sr = 0, si = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        for (int u = 0; u < T; ++u) { sr += X[((size_t)i * T + u) * 2]; si += X[((size_t)i * T + u) * 2 + 1]; }
+    const double mr = block_sum_fixed(sr, sh) / N, mi = block_sum_fixed(si, sh) / N;
+    double v = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double xr = 0, xi = 0;
+        for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+        v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
+    }
+    v = block_sum_fixed(v, sh);
+    if (threadIdx.x == 0) {
+        out_mean[2 * T] = mr;
+        out_mean[2 * T + 1] = mi;
+        out_var[T] = N > 1 ? v / (N - 1) : NAN;
     }
 }
 
@@ -351,7 +378,7 @@ int finish_estimate(wd_ctx *c, const double *X, int N, double *estimate, double 
     double *mean, *var;
     WD_TRY(ws_get(c, "est.mean", sizeof(double) * 2 * (T + 1), (void **)&mean));
     WD_TRY(ws_get(c, "est.var", sizeof(double) * (T + 1), (void **)&var));
-    k_mean_var<<<1, 128, 0, c->st>>>(X, N, T, mean, var);
+    k_mean_var<<<1, 256, 0, c->st>>>(X, N, T, mean, var);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     WD_CUDA(cudaMemcpyAsync(estimate, mean, sizeof(double) * 2 * (T + 1), cudaMemcpyDeviceToHost, c->st));
