@@ -23,7 +23,7 @@ class WDError(RuntimeError):
 
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f'libwd.so not built ({LIB_PATH}); run python -m paper_2607_05157_b300.build')
+    raise ImportError(f'libwd.so not built ({LIB_PATH}); run python paper_2607_05157_b300/build.py')
 
 lib = ctypes.CDLL(LIB_PATH)
 
