@@ -176,3 +176,30 @@ def test_fp64_norms_scale_invariant(shift):
         tr = np.linalg.norm(b[r].reshape(-1) - D @ x3[r].reshape(-1)) / np.linalg.norm(b[r])
         assert tr > 1e-5
         assert abs(res3[r] - tr) <= 1e-12 * tr
+
+
+@pytest.mark.parametrize("shift", [40, -40])
+def test_mixed_solve_scale_invariant(shift):
+    """The mixed-precision solve is invariant under scaling the source by
+    2^shift (inside the double-float range): the outer residual (double-float
+    layout), its norm (running power-of-two exponent) and its scaled FP32
+    copy (scale applied as a power of two and an FP32 significand) all
+    commute with the scaling, and the inner FP32 solves see the same
+    normalised residuals -- the same iterations, the solution scaled bit for
+    bit, the same reported residual."""
+    from paper_2607_05157_b300 import Context
+    dims = (4, 4, 4, 8)
+    U = synth.gauge_field(dims, 0.5, 1012)
+    b = synth.spinors(dims, 3, 72)
+    ctx = Context(dims, U, 0.125, BC)
+    x1, it1, res1 = ctx.solve(to_dev(b), tol=1e-10, prec=1)
+    x2, it2, res2 = ctx.solve(to_dev(b * 2.0 ** shift), tol=1e-10, prec=1)
+    ctx.close()
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    assert np.array_equal(it1, it2)
+    assert np.array_equal(x1 * 2.0 ** shift, x2)
+    assert np.array_equal(res1, res2)
+    D = wilson.sparse_matrix(U, 0.125, BC)
+    for r in range(3):
+        tr = np.linalg.norm(b[r].reshape(-1) - D @ x1[r].reshape(-1)) / np.linalg.norm(b[r])
+        assert tr <= 1e-10 * 1.01
