@@ -193,13 +193,19 @@ int hop_err_check(wd_ctx *c) {
 }
 
 int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const void *w, double a, double b,
-        int nrhs, bool dag, const void *w2, double cc, const int *tsup) {
+        int nrhs, bool dag, const void *w2, double cc, const int *tsup, bool w2_ddl) {
     if (nrhs <= 0) return WD_OK;
     HopArgs A;
     A.out = out; A.in = in; A.w = w; A.w2 = w2; A.a = a; A.b = b; A.c = cc;
     A.err = c->hop_err;
     A.alist = c->alist; A.acount = c->acount;
-    if (is_dd(pin)) A.tsup = tsup;
+    if (is_dd(pin)) {
+        A.tsup = tsup;
+        A.w2_ddl = w2_ddl ? 1 : 0;
+    } else if (w2_ddl) {
+        set_error("hop: a double-float addend needs the double-float stencil");
+        return WD_EINVAL;
+    }
     A.p = p; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
     // links in the precision of the input field; double-float: FP32 copy + remainder
     if (is_dd(pin)) {

@@ -519,6 +519,85 @@ __global__ void __launch_bounds__(256) k_ddl_to_f32(const void *a, void *b, cons
     }
 }
 
+// x (double-float layout) += scale * e (FP32 field) in double-float
+// arithmetic, item (site, FP32 chunk j) as in k_ddl_to_f32.  The scale
+// (FP64, per RHS) is split into sh + sl (sh: its leading 24 bits, sl the
+// next 24, each as a float scaled by ldexpf); the product (sh + sl) e keeps
+// the exact FMA error of sh e; the sum with x uses TwoSum twice and ends
+// renormalised (|l| <= ulp(h) / 2).
+__device__ __forceinline__ void dd_axpy_one(float &xh, float &xl, float sh, float sl, float e) {
+    const float p = __fmul_rn(sh, e);
+    const float q = __fmaf_rn(sl, e, __fmaf_rn(sh, e, -p));         // error of p plus sl e
+    const float s = __fadd_rn(xh, p), bb = __fsub_rn(s, xh);
+    const float err = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float t = __fadd_rn(xl, __fadd_rn(q, err));
+    xh = __fadd_rn(s, t);                                            // TwoSum: xl the exact error of xh
+    const float b2 = __fsub_rn(xh, s);
+    xl = __fadd_rn(__fsub_rn(s, __fsub_rn(xh, b2)), __fsub_rn(t, b2));
+}
+
+template <bool FL>
+__global__ void __launch_bounds__(256) k_axpy_ddl(void *x, const void *e, const double *scale, long units) {
+    const long per = 6 * units;
+    float4 *X = (float4 *)x + (size_t)blockIdx.y * 12 * units;
+    const float4 *Ev = (const float4 *)e + (size_t)blockIdx.y * per;
+    const double sd = scale[blockIdx.y];
+    bool nf = false;
+    const Split64 sp = split64(__double2loint(sd), __double2hiint(sd), nf);
+    if (sp.e == -4096) return;                  // zero scale: a converged RHS, x unchanged
+    const float sg = sd < 0 ? -1.f : 1.f;
+    const float sh = ldexpf(sg * sp.mh, sp.e), sl = ldexpf(sg * sp.ml, sp.e);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < per; i += (long)gridDim.x * blockDim.x) {
+        long i0, i1;
+        if (FL) {
+            const long u = i / 6, j = i - 6 * u;
+            i0 = 12 * u + 2 * j; i1 = i0 + 1;
+        } else {
+            const long j = i / units, st = i - j * units;
+            i0 = 2 * j * units + st; i1 = i0 + units;
+        }
+        const float4 ev = __ldg(Ev + i);
+        float4 a = X[i0], b = X[i1];
+        dd_axpy_one(a.x, a.z, sh, sl, ev.x);
+        dd_axpy_one(a.y, a.w, sh, sl, ev.y);
+        dd_axpy_one(b.x, b.z, sh, sl, ev.z);
+        dd_axpy_one(b.y, b.w, sh, sl, ev.w);
+        X[i0] = a;
+        X[i1] = b;
+    }
+}
+
+// h + l (a renormalised double-float pair) as a double, assembled with
+// integer operations: h's significand widened to 53 bits, l added in units
+// of its last bit (truncating what falls below), one renormalising shift.
+// Within one FP64 ulp of h + l.  h zero, subnormal or not finite: FP64 adds.
+__device__ __forceinline__ double ddpair_to_double(float h, float l) {
+    const unsigned hb = __float_as_uint(h), lb = __float_as_uint(l);
+    const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
+    if (eh == 0 || eh == 0xFF) return __dadd_rn((double)h, (double)l);
+    unsigned long long M = (1ull << 52) | ((unsigned long long)(hb & 0x7FFFFFu) << 29);
+    int E = eh - 127;                                            // h + l = M 2^(E - 52)
+    if (el != 0) {
+        const unsigned long long Ml = (1ull << 23) | (lb & 0x7FFFFFu);
+        const int sh = (el - 150) - (E - 52);                    // <= 5 for a renormalised pair
+        const unsigned long long add = sh >= 0 ? (sh <= 28 ? Ml << sh : 0ull) : (sh > -64 ? Ml >> -sh : 0ull);
+        if ((hb ^ lb) >> 31) M -= add;
+        else M += add;
+        if (M >> 53) { M >>= 1; E += 1; }
+        else if (!(M >> 52)) { M <<= 1; E -= 1; }
+    }
+    const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) |
+                                    ((unsigned long long)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
+__global__ void __launch_bounds__(256) k_ddl_to_f64(const float4 *a, double2 *b, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(a + i);
+        b[i] = make_double2(ddpair_to_double(v.x, v.z), ddpair_to_double(v.y, v.w));
+    }
+}
+
 // ---- conversions and mixed axpy ---------------------------------------------
 template <typename SA, typename SB, bool FL>
 __global__ void k_convert(const void *a, void *b, const double *scale, long Vh, long n) {
@@ -575,6 +654,25 @@ int blas_copy_convert(wd_ctx *c, const Space &sp, int ps, const void *src, int p
     }
     WD_DISPATCH_FLAT(sp.flat, FL, WD_DISPATCH_PREC(ps, SA, WD_DISPATCH_PREC(pd, SB,
         k_convert<SA, SB, FL><<<ew_blocks(n), 256, 0, c->st>>>(src, dst, scale, Vh, n))));
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int blas_axpy_ddl(wd_ctx *c, const Space &sp, void *x, const void *e, const double *scale, int nrhs) {
+    if (nrhs <= 0 || sp.units == 0) return WD_OK;
+    const unsigned bx = (unsigned)std::max(1, std::min(64, reduction_bpr(sp.units, nrhs)));
+    if (sp.flat) k_axpy_ddl<true><<<dim3(bx, nrhs), 256, 0, c->st>>>(x, e, scale, sp.units);
+    else k_axpy_ddl<false><<<dim3(bx, nrhs), 256, 0, c->st>>>(x, e, scale, sp.units);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int blas_ddl_to_f64(wd_ctx *c, const Space &sp, const void *x, double *x64, int nrhs) {
+    const long n = 12L * sp.units * nrhs;
+    if (n == 0) return WD_OK;
+    k_ddl_to_f64<<<ew_blocks(n / 12), 256, 0, c->st>>>((const float4 *)x, (double2 *)x64, n);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;

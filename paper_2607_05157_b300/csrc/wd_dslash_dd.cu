@@ -24,8 +24,8 @@
 // (re.h, im.h, re.l, im.l) -- same 16 bytes, same indexing.  An FP64 input is
 // split once by the memory-bound pass k_to_ddl instead of once per
 // neighbour read (8 times) inside the stencil; the intermediate field of the
-// two-hop Schur residual is written in ddl directly.  The addends w, w2 are
-// FP64; the output is FP64 (h + l, one FP64 add) or ddl.
+// two-hop Schur residual is written in ddl directly.  The addend w is FP64,
+// w2 FP64 or ddl (A.w2_ddl); the output is FP64 (h + l, one FP64 add) or ddl.
 //
 // Two arithmetic variants: scalar (R = 1, 2 RHS per thread) and packed
 // (R code 11, 12): (re, im) pairs through the f32x2 FMA/ADD instructions,
@@ -244,7 +244,15 @@ __global__ void __launch_bounds__(128) hop_kernel_dd(HopArgs A) {
                 o[k].im = o[k].im + dd_mul(a, d2dd(v.y));
             }
         }
-        if (A.w2) {
+        if (A.w2 && A.w2_ddl) {
+            const float4 *q = (const float4 *)A.w2 + (size_t)rhs * 12 * Vh + s;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float4 v = __ldg(q + k * Vh);
+                o[k].re = o[k].re + dd_mul(c, dd_make(v.x, v.z));
+                o[k].im = o[k].im + dd_mul(c, dd_make(v.y, v.w));
+            }
+        } else if (A.w2) {
             const double2 *q = (const double2 *)A.w2 + (size_t)rhs * 12 * Vh + s;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
@@ -489,7 +497,15 @@ __global__ void __launch_bounds__(128) hop_kernel_ddz(HopArgs A) {
                 zfma(o[k], ah, al, wh, neg2(wh), mk2(vr.l, vi.l));
             }
         }
-        if (A.w2) {
+        if (A.w2 && A.w2_ddl) {
+            const float4 *q = (const float4 *)A.w2 + (size_t)rhs * 12 * Vh + s;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float4 v = __ldg(q + k * Vh);
+                const float2 wh = mk2(v.x, v.y);
+                zfma(o[k], ch, cl, wh, neg2(wh), mk2(v.z, v.w));
+            }
+        } else if (A.w2) {
             const double2 *q = (const double2 *)A.w2 + (size_t)rhs * 12 * Vh + s;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {

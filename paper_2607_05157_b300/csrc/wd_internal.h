@@ -47,6 +47,9 @@ struct HopArgs {
     // anywhere): output sites more than one timeslice away get no hop term
     // (double-float stencil only; time-diluted and point sources)
     const int *tsup = nullptr;
+    // double-float stencil only: the second addend w2 is a double-float
+    // layout field (float4 (re.h, im.h, re.l, im.l) per complex) instead of FP64
+    int w2_ddl = 0;
     // block order of the FP32/BF16 stencil: 0 = RHS tile fastest (the site
     // tiles of all RHS run together), 1 = site tile fastest (the resident
     // blocks sweep a few whole RHS fields at a time)
@@ -200,7 +203,7 @@ void prof_end(wd_ctx *c, int slot);
 // for inner precision prec; SIn is the input storage, SOut the output storage.
 int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, const void *w,
         double a, double b, int nrhs, bool dag = false, const void *w2 = nullptr, double cc = 0.0,
-        const int *tsup = nullptr);
+        const int *tsup = nullptr, bool w2_ddl = false);
 
 int hop_err_check(wd_ctx *c);
 
@@ -230,6 +233,10 @@ inline size_t space_bytes(const Space &s, int prec, int nrhs) { return (size_t)n
 size_t field_bytes(const Geom &g, int prec, int nrhs);   // one parity of a fine field
 int blas_copy_convert(wd_ctx *c, const Space &sp, int prec_src, const void *src, int prec_dst, void *dst, int nrhs,
                       const double *scale_dev);
+// x (double-float layout) += scale[rhs] * e (FP32), in double-float arithmetic
+int blas_axpy_ddl(wd_ctx *c, const Space &sp, void *x_ddl, const void *e32, const double *scale_dev, int nrhs);
+// FP64 copy of a double-float layout field (integer assembly, within one FP64 ulp)
+int blas_ddl_to_f64(wd_ctx *c, const Space &sp, const void *x_ddl, double *x64, int nrhs);
 int blas_axpy_mixed(wd_ctx *c, const Space &sp, double *x64, int prec_e, const void *e, const double *scale_dev,
                     int nrhs);
 int blas_norm2(wd_ctx *c, const Space &sp, int prec, const void *a, int nrhs, double *out_dev);
@@ -275,6 +282,9 @@ struct Problem {
     // res64 writes the residual in the double-float layout (PDDL) instead of
     // FP64: its norm and its FP32 copy then run on the FP32 pipes
     bool res_ddl = false;
+    // the solution is kept in the double-float layout during the outer loop
+    // (res64 then reads x in that layout; FP64 x is written once at the end)
+    bool x_ddl = false;
     const char *tag;            // workspace name prefix
     bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
     uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};

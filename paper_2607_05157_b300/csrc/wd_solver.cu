@@ -268,7 +268,15 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
     WD_TRY(ws_get(c, (tag + ".scale").c_str(), sizeof(double) * 2 * nrhs, (void **)&scale_d));
     WD_TRY(ws_get(c, (tag + ".rn2").c_str(), sizeof(double) * nrhs, (void **)&rn2_d));
     WD_TRY(hws_get(c, (tag + ".hscale").c_str(), sizeof(double) * 2 * nrhs, (void **)&hsc));
-    WD_TRY(blas_zero(c, x, f64));
+    // the solution: FP64, or (x_ddl) a double-float layout copy updated in
+    // double-float arithmetic and assembled into FP64 once at the end
+    void *xd = nullptr;
+    if (P.x_ddl) {
+        WD_TRY(ws_get(c, (tag + ".xdd").c_str(), f64, &xd));
+        WD_CUDA(cudaMemsetAsync(xd, 0, f64, c->st));
+    } else {
+        WD_TRY(blas_zero(c, x, f64));
+    }
     // residual r64: FP64, or the double-float layout (same size) when the
     // problem's residual writes it
     const int rp = P.res_ddl ? PDDL : P64;
@@ -316,10 +324,16 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
             for (int r = 0; r < nrhs; ++r) { flags += hs[r].flag; mx = hs[r].iters > mx ? hs[r].iters : mx; }
             fprintf(stderr, "[wd]   inner: ran %d, max iters %d, breakdowns %d\n", ran, mx, flags);
         }
-        // x += |r| e  (FP64), then the FP64 residual r = b - A x
-        WD_TRY(blas_axpy_mixed(c, P.sp, x, pw, V.x, scale_d + nrhs, nrhs));
-        WD_TRY(P.res64(c, b, x, r64, nrhs, P.ures));
+        // x += |r| e  (FP64 or double-float), then the FP64 residual r = b - A x
+        if (P.x_ddl) {
+            WD_TRY(blas_axpy_ddl(c, P.sp, xd, V.x, scale_d + nrhs, nrhs));
+            WD_TRY(P.res64(c, b, (const double *)xd, r64, nrhs, P.ures));
+        } else {
+            WD_TRY(blas_axpy_mixed(c, P.sp, x, pw, V.x, scale_d + nrhs, nrhs));
+            WD_TRY(P.res64(c, b, x, r64, nrhs, P.ures));
+        }
     }
+    if (P.x_ddl) WD_TRY(blas_ddl_to_f64(c, P.sp, xd, x, nrhs));
     if (status == WD_OK)
         for (int r = 0; r < nrhs; ++r)
             if (bnorm2[r] > 0 && !(last_rn2[r] <= tol * tol * bnorm2[r])) status = WD_ENOCONV;
@@ -330,6 +344,7 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
 struct SchurArgs {
     int pin, pout;
     void *tmp;      // odd-parity field in precision pin
+    bool x_ddl;     // schur_res64: x in the double-float layout
 };
 
 static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
@@ -344,8 +359,8 @@ static int schur_op(wd_ctx *c, const void *in, void *out, int nrhs, void *u) {
 static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
     SchurArgs *S = (SchurArgs *)u;
     const int pt = S->pin == PDD ? PDDL : S->pin;
-    WD_TRY(hop(c, S->pin, pt, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
-    return hop(c, pt, S->pout, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0);
+    WD_TRY(hop(c, S->x_ddl ? PDDL : S->pin, pt, 1, S->tmp, x, nullptr, 0.0, 1.0, nrhs));
+    return hop(c, pt, S->pout, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0, nullptr, S->x_ddl);
 }
 
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
@@ -381,13 +396,15 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     const int pp = prec == P16 ? P16 : (prec == P32 ? P32 : P64);
     void *tmplo = nullptr;
     if (prec != P64) WD_TRY(ws_get(c, "sol.tmplo", field_bytes(c->g, pp, nrhs), &tmplo));
-    SchurArgs s64 = {P64, P64, tmp64}, slo = {pp, P32, tmplo}, sres = {pd, pd == PDD ? PDDL : pd, tmp64};
+    SchurArgs s64 = {P64, P64, tmp64, false}, slo = {pp, P32, tmplo, false},
+              sres = {pd, pd == PDD ? PDDL : pd, tmp64, pd == PDD};
     Problem P;
     P.sp = sp;
     P.op64 = schur_op; P.u64 = &s64;
     P.oplo = schur_op; P.ulo = &slo;
     P.res64 = schur_res64; P.ures = &sres;
     P.res_ddl = sres.pout == PDDL;
+    P.x_ddl = sres.x_ddl;
     P.tag = "fine";
     // the Schur operator's launches see the precisions and the odd workspace
     P.graph_ok = true;
