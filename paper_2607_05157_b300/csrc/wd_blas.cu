@@ -3,10 +3,13 @@
 // and deterministic two-stage reductions (per-block FP64 partials, then a
 // fixed-order sum), so that every Krylov scalar is an FP64 number.
 //
-// Elementwise kernels work per (RHS, site) unit: a thread loads the 12
-// complex components of a site of each operand through the layout-aware
-// loaders (the chunk packing differs per precision), so operands of
-// different precisions can be mixed in one kernel.
+// Elementwise kernels that mix precisions work per (RHS, site) unit: a
+// thread loads the 12 complex components of a site of each operand through
+// the layout-aware loaders (the chunk packing differs per precision).
+// Kernels whose operands share one precision stream each RHS as a flat run
+// of 16-byte chunks.  The FP64 steps of the defect correction (norms, the
+// residual's FP32 copy, the solution update) run on the FP32 pipes, on
+// integer splits of FP64 values or on double-float pairs.
 #include <algorithm>
 
 #include "wd_internal.h"
