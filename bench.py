@@ -256,6 +256,48 @@ def gradient_measure(wd, api, torch, synth):
             "ms": 1e3 * dt}
 
 
+def probing_measure(wd, api, torch, synth):
+    """The probing workload, 16^3x32 kappa 0.13: distance-2 (16 colours) and
+    distance-4 (64 colours) torus-colouring probing x 12 spin-colour
+    dilution for tr[g5 D^-1(t,t)] summed over t, against Hutchinson at equal
+    solve count (Eq. 14 vs Eq. 3): wall time, solves, and the variance of the
+    total of one estimate of that cost (the per-sample variance divided by
+    the samples one such estimate takes)."""
+    import numpy as np
+    dims = (16, 16, 16, 32)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1003), 0.13, BC)
+
+    def svar(S):
+        tot = S.sum(1)
+        return float(np.sum(np.abs(tot - tot.mean()) ** 2) / (len(tot) - 1))
+    out = {"workload": "16^3x32 kappa 0.13, tr[g5 D^-1(t,t)] summed over t; probing d = 2 (16 colours) and "
+                       "d = 4 (64 colours) x 12 dilution, 4 noise samples each; Hutchinson with 768 Rademacher "
+                       "vectors; solves to 1e-10, FP32 inner"}
+    api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 1, 32, d=2, seed=1, op=1, tol=TOL)    # tuning, workspaces
+    for d, N in ((2, 4), (4, 4)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = api.trace_estimate(ctx.h, wd.WD_PROBE, 12, N, 32, d=d, seed=2, op=1, tol=TOL, with_samples=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[f"probe_d{d}"] = {"ms": 1e3 * dt, "solves": r["n_solves"], "ms_per_solve": 1e3 * dt / r["n_solves"],
+                              "var_per_sample": svar(r["samples"]), "solves_per_sample": r["n_solves"] // N}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, 768, 32, seed=2, op=1, tol=TOL, with_samples=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    vh = svar(h["samples"])
+    out["hutchinson"] = {"ms": 1e3 * dt, "solves": h["n_solves"], "ms_per_solve": 1e3 * dt / h["n_solves"],
+                         "var_per_sample": vh}
+    for d in (2, 4):
+        q = out[f"probe_d{d}"]
+        # variance of one estimate costing q["solves_per_sample"] solves, both methods
+        q["var_hutchinson_over_probing_at_equal_solves"] = (vh / q["solves_per_sample"]) / q["var_per_sample"]
+    ctx.close()
+    return out
+
+
 def mlmc_probe_measure(wd, api, torch, synth):
     """Row f2: two-level MLMC with probing on both levels (level 1: probing
     d = 2 x 12 dilution; level 2: colouring of the coarse torus d = 1 x the 48
@@ -572,6 +614,7 @@ def main():
         line["secondary"] = {"coarse_tc": coarse_measure(wd, api, torch, synth),
                              "gradient": gradient_measure(wd, api, torch, synth),
                              "batched": batched_measure(wd, torch, synth),
+                             "probing": probing_measure(wd, api, torch, synth),
                              "mlmc_probe": mlmc_probe_measure(wd, api, torch, synth),
                              "connected": connected_measure(wd, api, torch, synth),
                              "mlmc3": mlmc3_measure(wd, api, torch, synth)}
