@@ -298,6 +298,39 @@ def probing_measure(wd, api, torch, synth):
     return out
 
 
+def mlmc2_large_measure(wd, api, torch, synth):
+    """The two-level workload, 24^3x48 kappa 0.13: GPU setup (24 test vectors
+    from 3 inverse iterations, 4^4 aggregates, Galerkin D_c), then the
+    two-level MLMC estimate of tr[g5 D^-1(t,t)] with 64 level-1 and 512 level-2
+    samples (Eq. 12, L = 2), against plain Hutchinson on the same 64 fine
+    noise samples: wall times, solves, per-sample variances of the total."""
+    import numpy as np
+    dims = (24, 24, 24, 48)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
+
+    def svar(S):
+        tot = S.sum(1)
+        return float(np.sum(np.abs(tot - tot.mean()) ** 2) / (len(tot) - 1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=4)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    m = api.trace_estimate(ctx.h, wd.WD_MLMC2, 1, 64, 48, n2=512, seed=2004, op=1, tol=TOL, with_samples=True)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    h = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, 64, 48, seed=2004, op=1, tol=TOL, with_samples=True)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    ctx.close()
+    return {"workload": "24^3x48 kappa 0.13, 4^4 aggregates, N_v = 24 (3 inverse iterations); tr[g5 D^-1(t,t)]; "
+                        "MLMC2 with 64 level-1 + 512 level-2 samples; Hutchinson with the same 64 fine samples",
+            "setup_s": t1 - t0, "mlmc2_s": t2 - t1, "mlmc2_solves": m["n_solves"],
+            "mlmc2_level1_var_per_sample": svar(m["samples"]), "mlmc2_var_total": m["var_total"],
+            "hutchinson_s": t3 - t2, "hutchinson_solves": h["n_solves"],
+            "hutchinson_var_per_sample": svar(h["samples"]), "hutchinson_var_total": h["var_total"]}
+
+
 def mlmc_probe_measure(wd, api, torch, synth):
     """Row f2: two-level MLMC with probing on both levels (level 1: probing
     d = 2 x 12 dilution; level 2: colouring of the coarse torus d = 1 x the 48
@@ -615,6 +648,7 @@ def main():
                              "gradient": gradient_measure(wd, api, torch, synth),
                              "batched": batched_measure(wd, torch, synth),
                              "probing": probing_measure(wd, api, torch, synth),
+                             "mlmc2_24": mlmc2_large_measure(wd, api, torch, synth),
                              "mlmc_probe": mlmc_probe_measure(wd, api, torch, synth),
                              "connected": connected_measure(wd, api, torch, synth),
                              "mlmc3": mlmc3_measure(wd, api, torch, synth)}
