@@ -156,6 +156,8 @@ struct wd_mg {
     int *nbr;          // [Vc][9]
     void *Wtc;         // tensor-core operand (bf16), built by wd_coarse_tc.cu
     float2 *Dc32;      // [Vc][9][ncd][ncd] complex64 copy for the FP32 CUDA-core path
+    float2 *Dclo;      // Dc - Dc32 as complex64: with Dc32 the double-float blocks of the FP64 residual
+    float2 *Phi, *Plo; // P as double-float pairs (FP32 copy and remainder), for the prolongation
 };
 
 struct wd_ctx {

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "wd_internal.h"
+#include "wd_dd.cuh"
 
 
 
@@ -267,9 +268,65 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
     for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) Dc[((size_t)X * 9 + b) * ncd * ncd + e] = A[e];
 }
 
-__global__ void k_dc_to32(const double2 *Dc, float2 *D32, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        D32[i] = make_float2((float)Dc[i].x, (float)Dc[i].y);
+__global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float hr = (float)Dc[i].x, hi = (float)Dc[i].y;
+        D32[i] = make_float2(hr, hi);
+        Dlo[i] = make_float2((float)(Dc[i].x - (double)hr), (float)(Dc[i].y - (double)hi));
+    }
+}
+
+// FP64 residual of the coarse solves in double-float arithmetic (the block
+// as Dc32 + Dclo, x split once into the double-float layout): y = a w + beta
+// A x with the block products and the sums over j and the 9 blocks kept as
+// float pairs (exact FMA errors, TwoSum), the final a w + beta acc in FP64.
+// One CTA per (X, 8-RHS tile), threads (i, r); each of the 9 blocks is
+// staged in shared memory by coalesced loads, transposed (column j
+// contiguous, so the threads of a warp read consecutive words), together
+// with the 8 RHS of its neighbour.
+__global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int *nbr, const float4 *x,
+                                  double2 *y, const double2 *w, double a, double beta, int ncd, int Vc, int nrhs) {
+    extern __shared__ float4 sm[];
+    const int ld = ncd + 1;                                     // padded column stride
+    float2 *Ah = (float2 *)sm, *Al = Ah + ncd * ld;
+    float4 *xs = (float4 *)(Al + ncd * ld + (ncd * ld) % 2);    // [8][ncd], 16-byte aligned
+    const int X = blockIdx.x, r0 = blockIdx.y * 8;
+    const int i = threadIdx.x % ncd, rr = threadIdx.x / ncd;
+    const int r = r0 + rr;
+    const int nn = ncd * ncd;
+    dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
+    for (int b = 0; b < 9; ++b) {
+        const int nb = nbr[X * 9 + b];
+        const size_t base = ((size_t)X * 9 + b) * nn;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int ei = e / ncd, ej = e - ei * ncd;          // row-major in global memory
+            Ah[ej * ld + ei] = __ldg(Dh + base + e);
+            Al[ej * ld + ei] = __ldg(Dl + base + e);
+        }
+        for (int e = threadIdx.x; e < 8 * ncd; e += blockDim.x) {
+            const int er = e / ncd, ej = e - er * ncd;
+            xs[e] = r0 + er < nrhs ? __ldg(x + ((size_t)(r0 + er) * Vc + nb) * ncd + ej) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (rr < 8) {
+            for (int j = 0; j < ncd; ++j) {
+                const float2 mh = Ah[j * ld + i], ml = Al[j * ld + i];
+                const float4 v = xs[rr * ncd + j];
+                const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+                const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+                dd_fma(are, mr, vr);
+                dd_fma(are, -mi, vi);
+                dd_fma(aim, mr, vi);
+                dd_fma(aim, mi, vr);
+            }
+        }
+    }
+    if (rr >= 8 || r >= nrhs) return;
+    const size_t o = ((size_t)r * Vc + X) * ncd + i;
+    double ore = beta * dd2d(are), oim = beta * dd2d(aim);
+    if (w) { ore += a * w[o].x; oim += a * w[o].y; }
+    y[o] = make_double2(ore, oim);
 }
 
 // ---- coarse stencil on CUDA cores (FP64 reference path and FP32) -----------
@@ -347,6 +404,40 @@ __global__ void k_prolong(const double2 *P, const double2 *yc, double *ve, doubl
     f[(size_t)comp * M.g.Vh + s] = acc;
 }
 
+// the same in double-float arithmetic: P as Phi + Plo, yc split once into the
+// double-float layout; within 2^-44 or so of the FP64 result, and not bound
+// by the GPU's FP64 rate
+__global__ void k_prolong_dd(const float2 *Ph, const float2 *Pl, const float4 *yc, double *ve, double *vo, MgGeom M,
+                             int nrhs) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)nrhs * M.g.V * 12) return;
+    const int comp = (int)(t % 12);
+    const long rest = t / 12;
+    const int site = (int)(rest % M.g.V), r = (int)(rest / M.g.V);
+    int c[4];
+    c[0] = site % M.g.X;
+    int q = site / M.g.X;
+    c[1] = q % M.g.Y; q /= M.g.Y;
+    c[2] = q % M.g.Z; c[3] = q / M.g.Z;
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
+    const int X = coarse_of(M, c), h = comp / 6;
+    const size_t pr = (((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv;
+    const float4 *yv = yc + ((size_t)r * M.Vc + X) * M.ncd + h * M.nv;
+    dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
+    for (int k = 0; k < M.nv; ++k) {
+        const float2 mh = __ldg(Ph + pr + k), ml = __ldg(Pl + pr + k);
+        const float4 v = __ldg(yv + k);
+        const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+        const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+        dd_fma(are, mr, vr);
+        dd_fma(are, -mi, vi);
+        dd_fma(aim, mr, vi);
+        dd_fma(aim, mi, vr);
+    }
+    double2 *f = (double2 *)(par ? vo : ve) + (size_t)r * 12 * M.g.Vh;
+    f[(size_t)comp * M.g.Vh + s] = make_double2(dd2d(are), dd2d(aim));
+}
+
 static MgGeom mg_geom(wd_ctx *c) {
     MgGeom M;
     M.g = c->g;
@@ -373,6 +464,24 @@ int coarse_apply64(wd_ctx *c, const double *x, double *y, const double *w, doubl
                                                                    (const double2 *)w, a, beta, g->ncd, g->Vc, nrhs);
     prof_end(c, slot);
     c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// y = a*w + beta * D_c x on FP64 vectors in double-float arithmetic
+int coarse_apply_dd(wd_ctx *c, const double *x, double *y, const double *w, double a, double beta, int nrhs) {
+    wd_mg *g = c->mg;
+    const long n = (long)g->Vc * g->ncd * nrhs;
+    void *xd;
+    WD_TRY(ws_get(c, "coarse.xdd", (size_t)n * sizeof(float4), &xd));
+    WD_CUDA(launch_to_ddl(x, xd, n, c->st));
+    dim3 grid(g->Vc, (nrhs + 7) / 8);
+    const size_t nld = (size_t)g->ncd * (g->ncd + 1);
+    const size_t smem = (2 * nld + nld % 2) * sizeof(float2) + (size_t)8 * g->ncd * sizeof(float4);
+    WD_CUDA(cudaFuncSetAttribute(k_coarse_apply_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_coarse_apply_dd<<<grid, g->ncd * 8, smem, c->st>>>(g->Dc32, g->Dclo, g->nbr, (const float4 *)xd, (double2 *)y,
+                                                         (const double2 *)w, a, beta, g->ncd, g->Vc, nrhs);
+    c->launches += 2;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -414,8 +523,19 @@ int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, in
 int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs) {
     MgGeom M = mg_geom(c);
     const long n = (long)nrhs * M.g.V * 12;
-    k_prolong<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(c->mg->P, (const double2 *)yc, ve, vo, M, nrhs);
-    c->launches++;
+    if (c->outer == PDD && c->mg->Phi) {
+        // double-float: the prolongated fields carry the FP64 values to ~2^-44
+        void *yd;
+        const long nc = (long)nrhs * M.Vc * M.ncd;
+        WD_TRY(ws_get(c, "mg.ydd", (size_t)nc * sizeof(float4), &yd));
+        WD_CUDA(launch_to_ddl(yc, yd, nc, c->st));
+        k_prolong_dd<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(c->mg->Phi, c->mg->Plo, (const float4 *)yd, ve,
+                                                                     vo, M, nrhs);
+        c->launches += 2;
+    } else {
+        k_prolong<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(c->mg->P, (const double2 *)yc, ve, vo, M, nrhs);
+        c->launches++;
+    }
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -435,7 +555,9 @@ static int cop32(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
 static int coptc(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
     return coarse_tc_apply(c, in, (float *)out, nrhs);
 }
-static int cres64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *) {
+// r = b - D_c x; u (nullable) points at a flag: nonzero = double-float arithmetic
+static int cres64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
+    if (u && *(const int *)u) return coarse_apply_dd(c, x, r, b, 1.0, -1.0, nrhs);
     return coarse_apply64(c, x, r, b, 1.0, -1.0, nrhs);
 }
 
@@ -457,7 +579,10 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
     // only when the tensor-core operand could not be built)
     const bool tc = prec != P64 && coarse_tc_ok(c);
     P.oplo = tc ? coptc : cop32; P.ulo = nullptr;
-    P.res64 = cres64; P.ures = nullptr;
+    // the FP64 residuals of the mixed solves in double-float arithmetic, as on
+    // the fine lattice (~2^-44 normwise), unless the tolerance asks for more
+    int use_dd = prec != P64 && tol >= 1e-12 && c->outer == PDD;
+    P.res64 = cres64; P.ures = &use_dd;
     P.tag = "coarse";
     const int inner = tc ? P16 : P32;
     std::vector<int> iters;
@@ -493,6 +618,9 @@ void wd_mg_free(wd_ctx *c) {
     cudaFree(g->nbr);
     if (g->Wtc) cudaFree(g->Wtc);
     if (g->Dc32) cudaFree(g->Dc32);
+    if (g->Dclo) cudaFree(g->Dclo);
+    if (g->Phi) cudaFree(g->Phi);
+    if (g->Plo) cudaFree(g->Plo);
     delete g;
     c->mg = nullptr;
 }
@@ -526,7 +654,9 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     const size_t nP = (size_t)c->g.V * 12 * nv;
     const size_t nD = (size_t)g->Vc * 9 * ncd * ncd;
     if (cudaMalloc(&g->P, nP * sizeof(double2)) != cudaSuccess || cudaMalloc(&g->Dc, nD * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&g->Dclo, nD * sizeof(float2)) != cudaSuccess || cudaMalloc(&g->Phi, nP * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&g->Plo, nP * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         wd_mg_free(c);
         set_error("wd_mg_setup: allocation failed");
@@ -556,8 +686,9 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int4 bc = make_int4(c->bc[0], c->bc[1], c->bc[2], c->bc[3]);
     k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
-    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, (long)nD);
-    c->launches += 5;
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
+    c->launches += 6;
     WD_CUDA(cudaGetLastError());
     WD_TRY(coarse_tc_build(c));
     WD_CUDA(cudaStreamSynchronize(c->st));
