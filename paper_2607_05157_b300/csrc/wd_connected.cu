@@ -25,8 +25,6 @@
 namespace wd {
 
 int gen_time_diluted_eo(wd_ctx *c, uint64_t seed, int stream, int g0, int nb, double *be, double *bo, int *tsup);
-int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
-int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
 int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
                  double *resid_out);
 int auto_batch(wd_ctx *c, int total);
@@ -211,10 +209,10 @@ extern "C" int wd_connected_mlmc(wd_ctx *c, int N1, int N2, uint64_t seed, int p
             WD_TRY(ws_get(c, "con.part", sizeof(double) * 4 * (size_t)nb * T * bps, (void **)&part));
             WD_TRY(gen_time_diluted_eo(c, seed, level == 1 ? 0 : LEVEL2_STREAM, (int)g0, nb, be, bo, tsup));
             // y_2 = P D_c^{-1} P^dag eta
-            WD_TRY(mg_restrict_eo(c, be, bo, bc, nb));
+            WD_TRY(mg_restrict_eo(c, be, bo, bc, nb, true));
             int s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
             if (s != WD_OK) return s;
-            WD_TRY(mg_prolong_eo(c, yc, we, wo, nb));
+            WD_TRY(mg_prolong_eo(c, yc, we, wo, nb, true));
             ns += nb;
             if (level == 1) {
                 // y_1 = D^{-1} eta - y_2

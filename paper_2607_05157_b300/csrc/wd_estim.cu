@@ -393,8 +393,6 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
                    double *estimate, double *sample_var, int64_t *nsolves, double *samples_out,
                    int (*level1)(wd_ctx *, void *, int, int, double, int, double *, int64_t *) = nullptr,
                    void *level1_user = nullptr, const CoarseProbe *cp = nullptr);
-int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
-int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
 int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
                  double *resid_out);
 
@@ -442,10 +440,10 @@ static int level1_probe(wd_ctx *c, void *u, int N1, int batch, double tol, int p
         }
         int s = solve_eo(c, be, bo, ze, zo, nb, tol, prec, 100000, nullptr, nullptr, tsup);
         if (s != WD_OK) return s;
-        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb));
+        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb, true));
         s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb));
+        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb, true));
         const long nf = (long)nb * 24 * g.Vh;
         k_sub_fields<<<1184, 256, 0, c->st>>>(ze, we, nf);
         k_sub_fields<<<1184, 256, 0, c->st>>>(zo, wo, nf);

@@ -291,6 +291,11 @@ struct Problem {
     bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
     uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};
 };
+// restriction P^dag v and prolongation P y between eo FP64 fine fields and
+// coarse FP64 vectors (wd_mg.cu); dd_ok: double-float arithmetic allowed
+// (~2^-44 relative, for the estimators), else FP64
+int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs, bool dd_ok = false);
+int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs, bool dd_ok = false);
 int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
              const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,
              std::vector<double> &last_rn2);

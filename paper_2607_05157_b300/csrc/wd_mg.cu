@@ -382,6 +382,39 @@ __global__ void k_restrict(const double2 *P, const double *ve, const double *vo,
     yc[t] = acc;
 }
 
+// the same in double-float arithmetic: P as Phi + Plo, the fine fields split
+// once into the double-float layout (ved, vod)
+__global__ void k_restrict_dd(const float2 *Ph, const float2 *Pl, const float4 *ved, const float4 *vod, double2 *yc,
+                              MgGeom M, int nrhs) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)nrhs * M.Vc * M.ncd) return;
+    const int i = (int)(t % M.ncd);
+    const long rest = t / M.ncd;
+    const int X = (int)(rest % M.Vc), r = (int)(rest / M.Vc);
+    const int h = i / M.nv, k = i % M.nv;
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
+    for (int j = 0; j < nsite; ++j) {
+        int c[4];
+        agg_site(M, X, j, c);
+        const int site = lex(M.g, c), par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
+        const float4 *f = (par ? vod : ved) + (size_t)r * 12 * M.g.Vh;
+        for (int q = 0; q < 6; ++q) {
+            const int comp = 6 * h + q;
+            const size_t pi = (((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv + k;
+            const float2 mh = __ldg(Ph + pi), ml = __ldg(Pl + pi);
+            const float4 v = __ldg(f + (size_t)comp * M.g.Vh + s);
+            const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+            const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+            dd_fma(are, mr, vr);                 // conj(P) v
+            dd_fma(are, mi, vi);
+            dd_fma(aim, mr, vi);
+            dd_fma(aim, -mi, vr);
+        }
+    }
+    yc[t] = make_double2(dd2d(are), dd2d(aim));
+}
+
 // v[x][comp] = sum_k P[x][comp][k] yc[X][nv*h(comp) + k]   (overwrites v)
 __global__ void k_prolong(const double2 *P, const double2 *yc, double *ve, double *vo, MgGeom M, int nrhs) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -511,19 +544,31 @@ int coarse_apply32(wd_ctx *c, const float *x, float *y, int nrhs) {
     return WD_OK;
 }
 
-int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs) {
+int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs, bool dd_ok) {
     MgGeom M = mg_geom(c);
     const long n = (long)nrhs * M.Vc * M.ncd;
-    k_restrict<<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->P, ve, vo, (double2 *)yc, M, nrhs);
-    c->launches++;
+    if (dd_ok && c->outer == PDD && c->mg->Phi) {
+        void *ved, *vod;
+        const long nf = 12L * M.g.Vh * nrhs;
+        WD_TRY(ws_get(c, "mg.vedd", (size_t)nf * sizeof(float4), &ved));
+        WD_TRY(ws_get(c, "mg.vodd", (size_t)nf * sizeof(float4), &vod));
+        WD_CUDA(launch_to_ddl(ve, ved, nf, c->st));
+        WD_CUDA(launch_to_ddl(vo, vod, nf, c->st));
+        k_restrict_dd<<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, (const float4 *)ved,
+                                                                      (const float4 *)vod, (double2 *)yc, M, nrhs);
+        c->launches += 3;
+    } else {
+        k_restrict<<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->P, ve, vo, (double2 *)yc, M, nrhs);
+        c->launches++;
+    }
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs) {
+int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs, bool dd_ok) {
     MgGeom M = mg_geom(c);
     const long n = (long)nrhs * M.g.V * 12;
-    if (c->outer == PDD && c->mg->Phi) {
+    if (dd_ok && c->outer == PDD && c->mg->Phi) {
         // double-float: the prolongated fields carry the FP64 values to ~2^-44
         void *yd;
         const long nc = (long)nrhs * M.Vc * M.ncd;

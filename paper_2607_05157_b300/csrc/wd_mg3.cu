@@ -268,8 +268,6 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
 int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, double *bo);
 int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma5, const double *ye,
                       const double *yo, double *X);
-int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
-int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
 int auto_batch(wd_ctx *c, int total);
 int mlmc_contract_fields(wd_ctx *c, const double *ae, const double *ao, const double *be, const double *bo,
                          int gamma5, int nrhs, double *X, int sample0);              // wd_mlmc.cu
@@ -491,13 +489,13 @@ extern "C" int trace_estimate_mlmc3(wd_ctx *c, int N1, int N2, int N3, uint64_t 
                 WD_TRY(gen_noise_eo(c, seed, s0, nb, ae, ao));
                 s = solve_eo(c, ae, ao, be, bo, nb, tol, prec, 100000, nullptr, nullptr);
                 if (s != WD_OK) return s;
-                WD_TRY(mg_restrict_eo(c, ae, ao, c2a, nb));
+                WD_TRY(mg_restrict_eo(c, ae, ao, c2a, nb, true));
                 s = coarse_solve(c, c2a, c2b, nb, tol, prec, 100000, nullptr);
                 if (s != WD_OK) return s;
                 double *we, *wo;
                 WD_TRY(ws_get(c, "ml3.we", f, (void **)&we));
                 WD_TRY(ws_get(c, "ml3.wo", f, (void **)&wo));
-                WD_TRY(mg_prolong_eo(c, c2b, we, wo, nb));
+                WD_TRY(mg_prolong_eo(c, c2b, we, wo, nb, true));
                 const long nf = (long)nb * 24 * g.Vh;
                 k_sub3<<<1184, 256, 0, c->st>>>((double2 *)be, (const double2 *)we, nf / 2);
                 k_sub3<<<1184, 256, 0, c->st>>>((double2 *)bo, (const double2 *)wo, nf / 2);
@@ -517,8 +515,8 @@ extern "C" int trace_estimate_mlmc3(wd_ctx *c, int N1, int N2, int N3, uint64_t 
                 WD_TRY(prolong2(c, c3b, c2w, nb));
                 k_sub3<<<1184, 256, 0, c->st>>>((double2 *)c2b, (const double2 *)c2w, n2 * nb);
                 c->launches++;
-                WD_TRY(mg_prolong_eo(c, c2a, ae, ao, nb));
-                WD_TRY(mg_prolong_eo(c, c2b, be, bo, nb));
+                WD_TRY(mg_prolong_eo(c, c2a, ae, ao, nb, true));
+                WD_TRY(mg_prolong_eo(c, c2b, be, bo, nb, true));
                 WD_TRY(mlmc_contract_fields(c, ae, ao, be, bo, op, nb, X[1], s0));
                 ns += 2 * nb;
             } else {
@@ -530,8 +528,8 @@ extern "C" int trace_estimate_mlmc3(wd_ctx *c, int N1, int N2, int N3, uint64_t 
                 if (s != WD_OK) return s;
                 WD_TRY(prolong2(c, c3a, c2a, nb));
                 WD_TRY(prolong2(c, c3b, c2b, nb));
-                WD_TRY(mg_prolong_eo(c, c2a, ae, ao, nb));
-                WD_TRY(mg_prolong_eo(c, c2b, be, bo, nb));
+                WD_TRY(mg_prolong_eo(c, c2a, ae, ao, nb, true));
+                WD_TRY(mg_prolong_eo(c, c2b, be, bo, nb, true));
                 WD_TRY(mlmc_contract_fields(c, ae, ao, be, bo, op, nb, X[2], s0));
                 ns += nb;
             }

@@ -21,8 +21,6 @@ namespace wd {
 int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, double *bo);
 int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma5, const double *ye,
                       const double *yo, double *X);
-int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs);
-int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs);
 int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, int prec, int max_iter,
                  double *resid_out);
 Space coarse_space(wd_ctx *c);
@@ -227,10 +225,10 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         WD_TRY(gen_noise_eo(c, seed, s0, nb, be, bo));
         int s = solve_eo(c, be, bo, ze, zo, nb, tol, prec, 100000, nullptr, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb));
+        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb, true));
         s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb));
+        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb, true));
         const long n = (long)nb * 24 * g.Vh;
         k_sub<<<1184, 256, 0, c->st>>>(ze, we, n);
         k_sub<<<1184, 256, 0, c->st>>>(zo, wo, n);
@@ -265,8 +263,8 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         WD_CUDA(cudaGetLastError());
         int s = coarse_solve(c, xi, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_prolong_eo(c, xi, ae, ao, nb));
-        WD_TRY(mg_prolong_eo(c, yc, be, bo, nb));
+        WD_TRY(mg_prolong_eo(c, xi, ae, ao, nb, true));
+        WD_TRY(mg_prolong_eo(c, yc, be, bo, nb, true));
         WD_TRY(contract_fields(c, ae, ao, be, bo, gamma5, nb, X2, s0, mc));
         ns += nb;
     }
