@@ -242,6 +242,7 @@ template <typename S, int UNR>
 __global__ void __launch_bounds__(256) k_xr_flat(void *x, void *r, const void *p, const void *s, const void *t,
                                                  const void *rh, const BiState *st, double *part, long nq,
                                                  int nrhs, int bpr) {
+    pdl_wait();
     typedef typename RT_of<S>::type RT;
     constexpr int NC = CIO<S>::NC;
     if (!st[blockIdx.y].active) return;          // converged RHS: x, r stay as they are
@@ -811,6 +812,7 @@ __global__ void k_scal_init(BiState *st, const double *part, const double *bnorm
 template <typename SA, typename SB, bool NORMA, bool FL>
 __global__ void k_dot_part(const void *a, const void *b, double *part, long Vh, int nrhs, int bpr,
                            const BiState *st) {
+    pdl_wait();
     typedef typename RT_of<SA>::type RT;
     if (st && !st[blockIdx.y].active) return;    // converged RHS: partials unused
     Range R = my_range(Vh);
@@ -864,6 +866,7 @@ __device__ void scal_omega(BiState &s, double2 ts, double tt) {
 }
 
 __global__ void k_scal_alpha(BiState *st, const double *part, int nrhs, int bpr) {
+    pdl_wait();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
         BiState &s = st[r];
         if (!s.active) { s.alpha = make_double2(0, 0); continue; }
@@ -872,6 +875,7 @@ __global__ void k_scal_alpha(BiState *st, const double *part, int nrhs, int bpr)
 }
 
 __global__ void k_scal_omega(BiState *st, const double *part, int nrhs, int bpr) {
+    pdl_wait();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
         BiState &s = st[r];
         if (!s.active) { s.omega = make_double2(0, 0); continue; }
@@ -881,6 +885,7 @@ __global__ void k_scal_omega(BiState *st, const double *part, int nrhs, int bpr)
 }
 
 __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, int *count, int *list) {
+    pdl_wait();
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -910,6 +915,7 @@ __global__ void k_scal_beta(BiState *st, const double *part, int nrhs, int bpr, 
 // s = r - alpha v
 template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *st, long Vh, long n) {
+    pdl_wait();
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         if (!st[u / Vh].active) continue;
@@ -928,6 +934,7 @@ __global__ void k_bicg_s(const void *r, const void *v, void *s, const BiState *s
 template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const void *t, const void *rh,
                           const BiState *st, double *part, long Vh, int nrhs, int bpr) {
+    pdl_wait();
     typedef typename RT_of<SW>::type RT;
     if (!st[blockIdx.y].active) return;          // converged RHS: x, r stay as they are
     Range R = my_range(Vh);
@@ -962,6 +969,7 @@ __global__ void k_bicg_xr(void *x, void *r, const void *p, const void *s, const 
 // p = r + beta (p - omega v)
 template <typename SW, typename SP, bool FL>
 __global__ void k_bicg_p(const void *r, void *p, const void *v, const BiState *st, long Vh, long n) {
+    pdl_wait();
     typedef typename RT_of<SW>::type RT;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const BiState &S = st[u / Vh];
@@ -1005,9 +1013,12 @@ int bicg_after_v(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SW, false, FL><<<grid, 256, 0, c->st>>>(V.rh, V.v, V.part, Vh, nrhs, V.bpr, V.st);
-        k_scal_alpha<<<(nrhs + 127) / 128, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
-        k_bicg_s<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.v, V.s, V.st, Vh, n);
+        launch_pdl(k_dot_part<SW, SW, false, FL>, grid, dim3(256), 0, c->st, (const void *)V.rh, (const void *)V.v,
+                   V.part, Vh, nrhs, V.bpr, (const BiState *)V.st);
+        launch_pdl(k_scal_alpha, dim3((nrhs + 127) / 128), dim3(128), 0, c->st, V.st, (const double *)V.part, nrhs,
+                   V.bpr);
+        launch_pdl(k_bicg_s<SW, SP, FL>, dim3(eb), dim3(256), 0, c->st, (const void *)V.r, (const void *)V.v, V.s,
+                   (const BiState *)V.st, Vh, n);
     }));
     c->launches += 3;
     WD_CUDA(cudaGetLastError());
@@ -1025,8 +1036,9 @@ template <typename SW, typename SP, bool FL> struct XrUpdate {
 };
 template <typename S, bool FL> struct XrUpdate<S, S, FL> {
     static void run(wd_ctx *c, BiVecs &V, int nrhs) {
-        k_xr_flat<S, 2><<<dim3(V.bpr, nrhs), 256, 0, c->st>>>(V.x, V.r, V.p, V.s, V.t, V.rh, V.st, V.part,
-                                                             (long)SIO<S>::NCH * V.sp.units, nrhs, V.bpr);
+        launch_pdl(k_xr_flat<S, 2>, dim3(V.bpr, nrhs), dim3(256), 0, c->st, V.x, V.r, (const void *)V.p,
+                   (const void *)V.s, (const void *)V.t, (const void *)V.rh, (const BiState *)V.st, V.part,
+                   (long)SIO<S>::NCH * V.sp.units, nrhs, V.bpr);
     }
 };
 
@@ -1036,11 +1048,15 @@ int bicg_after_t(wd_ctx *c, int pw, int pp, BiVecs &V, int nrhs) {
     dim3 grid(V.bpr, nrhs);
     const unsigned eb = ew_blocks(n);
     WD_DISPATCH_FLAT(V.sp.flat, FL, WD_DISPATCH_PAIR(pw, pp, SW, SP, {
-        k_dot_part<SW, SP, true, FL><<<grid, 256, 0, c->st>>>(V.t, V.s, V.part, Vh, nrhs, V.bpr, V.st);
-        k_scal_omega<<<(nrhs + 127) / 128, 128, 0, c->st>>>(V.st, V.part, nrhs, V.bpr);
+        launch_pdl(k_dot_part<SW, SP, true, FL>, grid, dim3(256), 0, c->st, (const void *)V.t, (const void *)V.s,
+                   V.part, Vh, nrhs, V.bpr, (const BiState *)V.st);
+        launch_pdl(k_scal_omega, dim3((nrhs + 127) / 128), dim3(128), 0, c->st, V.st, (const double *)V.part, nrhs,
+                   V.bpr);
         XrUpdate<SW, SP, FL>::run(c, V, nrhs);
-        k_scal_beta<<<1, 256, 0, c->st>>>(V.st, V.part, nrhs, V.bpr, V.count, V.alist);
-        k_bicg_p<SW, SP, FL><<<eb, 256, 0, c->st>>>(V.r, V.p, V.v, V.st, Vh, n);
+        launch_pdl(k_scal_beta, dim3(1), dim3(256), 0, c->st, V.st, (const double *)V.part, nrhs, V.bpr, V.count,
+                   V.alist);
+        launch_pdl(k_bicg_p<SW, SP, FL>, dim3(eb), dim3(256), 0, c->st, (const void *)V.r, V.p, (const void *)V.v,
+                   (const BiState *)V.st, Vh, n);
     }));
     c->launches += 5;
     WD_CUDA(cudaGetLastError());

@@ -386,6 +386,7 @@ __device__ __forceinline__ void hop_site_f2(const HopArgs &A, int rb, int s) {
 
 template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, bool PIPE, int PF = 0>
 __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
+    pdl_wait();
     const int nsb = gridDim.x / A.nrb;
     const int rb = A.rhs_major ? blockIdx.x / nsb : blockIdx.x % A.nrb;
     const int s = (A.rhs_major ? blockIdx.x % nsb : blockIdx.x / A.nrb) * blockDim.x + threadIdx.x;
@@ -730,8 +731,10 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
                 if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, true><<<grid, threads, 0, st>>>(A); \
                 else hop_kernel_f2<SIn, SOut, SW, G, RR, false, true><<<grid, threads, 0, st>>>(A);    \
             } else {                                                                                   \
-                if (dag) hop_kernel_f2<SIn, SOut, SW, G, RR, true, false><<<grid, threads, 0, st>>>(A); \
-                else hop_kernel_f2<SIn, SOut, SW, G, RR, false, false><<<grid, threads, 0, st>>>(A);   \
+                return dag ? launch_pdl(hop_kernel_f2<SIn, SOut, SW, G, RR, true, false>, grid, dim3(threads), \
+                                        0, st, A)                                                      \
+                           : launch_pdl(hop_kernel_f2<SIn, SOut, SW, G, RR, false, false>, grid,        \
+                                        dim3(threads), 0, st, A);                                      \
             }                                                                                          \
         } else {                                                                                       \
             if (dag) hop_kernel<SIn, SOut, SW, G, RR, true><<<grid, threads, 0, st>>>(A);              \

@@ -65,6 +65,28 @@ __device__ __forceinline__ bool hop_reaches(const HopArgs &A, int rhs, int t) {
     return dt <= 1 || dt == A.g.T - 1;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while its predecessor on the stream is still finishing; it must
+// call pdl_wait() before touching any memory, which returns once the
+// predecessor has completed and its writes are visible (a no-op for a normal
+// launch).  Hides the launch gap between the dependent kernels of a Krylov
+// iteration.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // RHS handled by slot r of RHS tile rb (R slots per tile), or -1 if none
 __device__ __forceinline__ int tile_rhs(const HopArgs &A, int rb, int r, int R) {
     const int k = rb * R + r;
