@@ -238,8 +238,7 @@ const char *wd_last_error(void);
 
 /* Build the aggregation prolongator P and D_c = P^dag D P (Eq. 7).
  * tv: host complex128 [nv][T][Z][Y][X][4][3] test vectors (nullable: then
- * nv vectors are generated on the GPU from Rademacher starts with
- * tv_iters inverse iterations v <- D^{-1} v / ||v|| at tolerance 1e-6).
+ * nv vectors are generated on the GPU as wd_mg_test_vectors does).
  * agg[4]: aggregate extents (must divide dims).  Each test vector is restricted
  * to each aggregate and chirality half (spins {0,1} / {2,3}) and
  * orthonormalised by modified Gram-Schmidt in test-vector order; coarse dof
@@ -247,6 +246,16 @@ const char *wd_last_error(void);
  * multiple of 8. */
 int wd_mg_setup(wd_ctx *ctx, const double *tv, int nv, const int agg[4], int tv_iters,
                 uint64_t seed);
+
+/* The test vectors wd_mg_setup(tv = NULL) builds (Sec. 2: the near-null space
+ * that P is built from; the paper takes the setup from DD-alpha-AMG): start k
+ * (k < nv) is the Rademacher vector of noise sample 2^22 + k of `seed` (the
+ * generator of trace_estimate), and each of `iters` inverse iterations
+ * replaces v by x / ||x|| with x = D^{-1} v from a mixed-precision solve to a
+ * relative residual of 1e-6 (norm over the whole lattice).  tv_out: device
+ * complex128 [nv][T][Z][Y][X][4][3], owned by the caller.  WD_EINVAL for
+ * nv < 1, iters < 0 or a null pointer. */
+int wd_mg_test_vectors(wd_ctx *ctx, int nv, int iters, uint64_t seed, double *tv_out);
 
 /* y_c = D_c x_c on the coarse lattice: device complex128 [nrhs][Vc][2nv].
  * prec WD_FP64 uses FP64 blocks; WD_MIXED_FP32 / WD_MIXED_BF16 run the
@@ -323,14 +332,15 @@ int wd_batch_solve(wd_batch *b, const double *const *rhs, double *const *x, cons
  * while running -- services that reserve their whole device-memory budget at
  * start-up, and frameworks whose caching allocator must own every byte of
  * device memory.  The even-odd staging fields live in one static device array
- * of 64 MiB that every GPU loading libwd holds until the process exits; a call
- * needing more staging (2 input + 2 output half-fields for nrhs fields; e.g.
- * FP64: 384 bytes per site and right-hand side) is rejected with WD_EINVAL.
- * The array's device address is looked up on the first call made with a given
- * device current, so make that first call before any latency-critical use.
- * All calls share the array and leave its contents behind: calls whose work
- * overlaps on the GPU (other streams, other host threads) race on it.  The
- * context itself must already exist (wd_create allocates). */
+ * of 64 MiB per GPU; a call needing more staging (2 input + 2 output
+ * half-fields for nrhs fields; e.g. FP64: 384 bytes per site and right-hand
+ * side) is rejected with WD_EINVAL.  The array comes into being on a GPU when
+ * the first context is created there: wd_create (which allocates anyway)
+ * loads the code that holds it and resolves its address, with the context's
+ * device current, and the array then stays until the process exits.  A call
+ * stages on its context's device whichever device is current.  All calls on
+ * one GPU share the array and leave its contents behind: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it. */
 int wd_apply_noalloc(wd_ctx *ctx, const void *in, void *out, int nrhs, int prec, int dagger);
 
 /* ---- instrumentation ------------------------------------------------- */

@@ -71,6 +71,34 @@ def prolongator(tv, dims, agg):
                          shape=(n, 2 * nv * Vc))
 
 
+# Test vectors (Sec. 2: the near-null space that P must capture; the paper takes
+# them from the DD-alpha-AMG setup).  Reading: N_v inverse iterations from
+# Rademacher starts -- start k is the noise vector of sample TV_STREAM + k
+# (Eq. 1's generator, a stream of its own), and each step replaces v by
+# D^{-1} v / ||D^{-1} v||, the 2-norm taken over the whole lattice.  The solve
+# is FP64 BiCGStab on the full operator.
+TV_STREAM = 1 << 22
+
+
+def test_vectors(apply_D, dims, nv, iters, seed, tol=1e-12):
+    """(nv, T, Z, Y, X, 4, 3) complex128: `iters` normalised inverse iterations
+    of the Rademacher starts of samples TV_STREAM + k, k < nv (iters = 0: the
+    starts themselves, unnormalised)."""
+    from .noise import rademacher
+    from .solver import bicgstab
+    X, Y, Z, T = dims
+    n = 12 * X * Y * Z * T
+    shape = (T, Z, Y, X, 4, 3)
+    out = np.empty((nv,) + shape, np.complex128)
+    for k in range(nv):
+        v = rademacher(seed, TV_STREAM + k, n).astype(np.complex128).reshape(shape)
+        for _ in range(iters):
+            x, _, _ = bicgstab(apply_D, v, tol=tol)
+            v = x / np.linalg.norm(x)
+        out[k] = v
+    return out
+
+
 def coarse_operator(Dmat, P):
     """Eq. 7: D_c = P^dagger D P (sparse)."""
     Ph = P.conj().T.tocsr()

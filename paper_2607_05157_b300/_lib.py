@@ -58,6 +58,7 @@ _SIGS = {
     'wd_point_correlator': (c_int, [c_void_p, P(c_int), c_int, c_double, c_void_p]),
     'wd_last_error': (ctypes.c_char_p, []),
     'wd_mg_setup': (c_int, [c_void_p, c_void_p, c_int, P(c_int), c_int, c_uint64]),
+    'wd_mg_test_vectors': (c_int, [c_void_p, c_int, c_int, c_uint64, c_void_p]),
     'wd_coarse_apply': (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),
     'wd_restrict': (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     'wd_prolong': (c_int, [c_void_p, c_void_p, c_void_p, c_int]),

@@ -224,6 +224,13 @@ def wd_mg_setup(h, tv, nv, agg, tv_iters=3, seed=0):
     check(lib.wd_mg_setup(h, ptr, int(nv), _iarr(agg), int(tv_iters), ctypes.c_uint64(seed)), 'wd_mg_setup')
 
 
+def wd_mg_test_vectors(h, nv, iters, seed, out):
+    import torch
+    check(lib.wd_mg_test_vectors(h, int(nv), int(iters), ctypes.c_uint64(seed), _dev_ptr(out, torch.complex128, 'out')),
+          'wd_mg_test_vectors')
+    return out
+
+
 def wd_coarse_apply(h, x, out, prec=WD_FP64):
     import torch
     check(lib.wd_coarse_apply(h, _dev_ptr(x, torch.complex128, 'in'), _dev_ptr(out, torch.complex128, 'out'),

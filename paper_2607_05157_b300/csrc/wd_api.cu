@@ -370,6 +370,7 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
     c->loop_dev = nullptr;
     c->graph_off = false;
     c->act_count = -1;
+    c->noalloc_scratch = nullptr;
     if (cudaMalloc(&c->hop_err, sizeof(int)) != cudaSuccess || cudaMemset(c->hop_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("wd_create: allocation failed");
@@ -393,6 +394,11 @@ extern "C" int wd_create(wd_ctx **out, const int dims[4], const double *gauge, d
         return WD_ENOMEM;
     }
     int s = ingest_gauge(c, gauge);
+    if (s != WD_OK) { wd_destroy(c); return s; }
+    // resolve the static array of wd_apply_noalloc here, with the context's
+    // device current: this loads its module (which holds the array) now, so
+    // that the allocation-free calls later find it in place
+    s = noalloc_scratch_ptr(&c->noalloc_scratch);
     if (s != WD_OK) { wd_destroy(c); return s; }
     *out = c;
     return WD_OK;

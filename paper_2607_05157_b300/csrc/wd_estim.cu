@@ -365,9 +365,10 @@ int estimate_rhs_range(wd_ctx *c, EstParams P, int total, int batch, double tol,
 
 int auto_batch(wd_ctx *c, int total) {
     // FP64 eo fields of the estimator and the solver (~14 half-fields) plus the
-    // FP32 Krylov vectors (8 half-fields) per RHS; keep the batch under ~48 GB
+    // FP32 Krylov vectors (8 half-fields) per RHS; keep the batch under ~96 GB
+    // (a third of the GPU's memory)
     const double per = (double)c->g.Vh * (14 * 192.0 + 8 * 96.0);
-    int b = (int)(48e9 / per);
+    int b = (int)(96e9 / per);
     if (b > 384) b = 384;
     if (b < 1) b = 1;
     return b < total ? b : total;

@@ -37,7 +37,7 @@ struct HopArgs {
     int p;                 // output parity
     int nrhs, nrb;
     Geom g;
-    int *err;              // error flag of the staged variant (bounded waits); set by hop()
+    int *err = nullptr;    // error flag of the staged variant (bounded waits); set by hop()
     // Inside a BiCGStab run: the RHS still working, ascending (alist[0 ..
     // *acount)); RHS tiles walk this list, so converged RHS cost nothing.
     // Null: all nrhs RHS.
@@ -180,6 +180,8 @@ struct wd_mg {
     float2 *Dc32;      // [Vc][9][ncd][ncd] complex64 copy for the FP32 CUDA-core path
     float2 *Dclo;      // Dc - Dc32 as complex64: with Dc32 the double-float blocks of the FP64 residual
     float2 *Phi, *Plo; // P as double-float pairs (FP32 copy and remainder), for the prolongation
+    double2 *Gt;       // [Vc][agg_t][2][nv][nv]: Gram matrices of P's columns restricted to one
+                       // timeslice of an aggregate and one chirality half (coarse contractions)
 };
 
 struct wd_ctx {
@@ -209,6 +211,8 @@ struct wd_ctx {
     int *loop_dev;                  // [iterations run, iteration limit] of a graph launch
     bool graph_off;                 // a graph call failed: plain loops from then on
     std::map<int, std::pair<int, int>> tuned;   // (pin, pout, RHS bucket) -> (R, threads)
+    void *noalloc_scratch;          // device address of the static array of wd_apply_noalloc on this
+                                    // context's device (resolved by wd_create)
     wd_mg *mg;
     wd_mg3 *mg3;                    // third level (built on mg), nullable
     std::vector<double> last_level2;    // [n2][T][2]
@@ -230,6 +234,11 @@ int hop(wd_ctx *c, int prec_in, int prec_out, int p, void *out, const void *in, 
         const int *tsup = nullptr, bool w2_ddl = false);
 
 int hop_err_check(wd_ctx *c);
+
+// Device address of the static staging array of wd_apply_noalloc on the
+// current device (wd_noalloc.cu); called by wd_create, which is where that
+// array's module is loaded and the array comes into being.
+int noalloc_scratch_ptr(void **out);
 
 // layout conversions between the user layout and the eo layout
 int user_to_eo(wd_ctx *c, const void *user, bool user_double, int prec, void *even, void *odd, int nrhs);
@@ -318,6 +327,10 @@ struct Problem {
 // (~2^-44 relative, for the estimators), else FP64
 int mg_restrict_eo(wd_ctx *c, const double *ve, const double *vo, double *yc, int nrhs, bool dd_ok = false);
 int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs, bool dd_ok = false);
+// per-timeslice contraction of coarse vectors: part[r][t] = sum_{x in t}
+// (P a_r)(x)^dag B (P b_r)(x), B = 1 or g5, evaluated on the coarse lattice
+// from the Gram matrices Gt (wd_mg.cu); part: device complex [nrhs][T]
+int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5, int nrhs, double *part);
 int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
              const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,
              std::vector<double> &last_rn2);

@@ -160,6 +160,65 @@ __global__ void k_block_mgs(double2 *P, MgGeom M) {
     }
 }
 
+// Gram matrices of P's columns restricted to one timeslice of an aggregate
+// and one chirality half: Gt[X][tau][h][k][l] = sum over the sites x of
+// aggregate X with t(x) = t0(X) + tau and the 6 components of half h of
+// conj(P_k(x)) P_l(x).  Since P is block diagonal over aggregates and halves,
+// sum_{x in t} (P a)(x)^dag B (P b)(x) = sum_{X, h} s_h a_{X,h}^dag Gt[X][t - t0(X)][h] b_{X,h}
+// (s_h = +1, or +1 / -1 on the halves for B = g5): the per-timeslice trace
+// contraction (Eq. 21) of two coarse vectors needs no fine fields.  One CTA
+// per (X, tau, h).
+__global__ void k_gram_t(const double2 *P, double2 *Gt, MgGeom M) {
+    const int at = M.agg[3], nv = M.nv;
+    const int b = blockIdx.x;                        // (X * at + tau) * 2 + h
+    const int h = b & 1, tau = (b >> 1) % at, X = (b >> 1) / at;
+    const int ns3 = M.agg[0] * M.agg[1] * M.agg[2];
+    for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) {
+        const int k = e / nv, l = e % nv;
+        double2 acc = make_double2(0, 0);
+        for (int j3 = 0; j3 < ns3; ++j3) {
+            int c[4];
+            agg_site(M, X, j3 + ns3 * tau, c);       // time offset tau inside the aggregate
+            const int site = lex(M.g, c);
+            for (int r = 0; r < 6; ++r) {
+                const int comp = 6 * h + r;
+                acc = zfma_conj(acc, P[pidx(M, site, comp, k)], P[pidx(M, site, comp, l)]);
+            }
+        }
+        Gt[(size_t)b * nv * nv + e] = acc;
+    }
+}
+
+// part[r][t] = sum_{X in timeslice t / agg_t} sum_h s_h a_{X,h}^dag Gt[X][t % agg_t][h] b_{X,h}
+// for coarse vectors a, b [nrhs][Vc][2 nv]; one CTA per (r, t), a fixed
+// assignment of (X, h, k) to threads and a fixed reduction order
+__global__ void __launch_bounds__(256) k_contract_coarse_t(const double2 *Gt, const double2 *a, const double2 *b,
+                                                           int gamma5, double *part, MgGeom M) {
+    __shared__ double2 sh[32];
+    const int r = blockIdx.x, t = blockIdx.y, T = M.g.T;
+    const int at = M.agg[3], nv = M.nv, ncd = M.ncd;
+    const int Vs = M.cd[0] * M.cd[1] * M.cd[2];
+    const int ct = t / at, tau = t % at;
+    double2 acc = make_double2(0, 0);
+    for (int item = threadIdx.x; item < Vs * ncd; item += blockDim.x) {
+        const int xs = item / ncd, i = item % ncd, h = i / nv, k = i % nv;
+        const int X = xs + Vs * ct;
+        const double2 *G = Gt + ((((size_t)X * at + tau) * 2 + h) * nv + k) * nv;
+        const double2 *bb = b + ((size_t)r * M.Vc + X) * ncd + nv * h;
+        double2 u = make_double2(0, 0);
+        for (int l = 0; l < nv; ++l) u = zfma(u, G[l], bb[l]);
+        const double2 av = a[((size_t)r * M.Vc + X) * ncd + i];
+        const double sg = (gamma5 && h == 1) ? -1.0 : 1.0;
+        acc.x += sg * (av.x * u.x + av.y * u.y);
+        acc.y += sg * (av.x * u.y - av.y * u.x);
+    }
+    acc = block_reduce_z(acc, sh);
+    if (threadIdx.x == 0) {
+        part[((size_t)r * T + t) * 2] = acc.x;
+        part[((size_t)r * T + t) * 2 + 1] = acc.y;
+    }
+}
+
 // coarse neighbour table: b = 0 self, 1+mu forward, 5+mu backward
 __global__ void k_coarse_nbr(int *nbr, MgGeom M) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
@@ -586,6 +645,17 @@ int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs,
 }
 
 // ---- coarse solves ------------------------------------------------------------
+int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5, int nrhs, double *part) {
+    wd_mg *g = c->mg;
+    if (!g || !g->Gt) { set_error("coarse contraction: no multigrid setup"); return WD_EINVAL; }
+    if (nrhs <= 0) return WD_OK;
+    k_contract_coarse_t<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Gt, (const double2 *)a, (const double2 *)b, gamma5,
+                                                              part, mg_geom(c));
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs);   // wd_coarse_tc.cu
 int coarse_tc_check(wd_ctx *c);
 int coarse_tc_build(wd_ctx *c);
@@ -666,6 +736,7 @@ void wd_mg_free(wd_ctx *c) {
     if (g->Dclo) cudaFree(g->Dclo);
     if (g->Phi) cudaFree(g->Phi);
     if (g->Plo) cudaFree(g->Plo);
+    if (g->Gt) cudaFree(g->Gt);
     delete g;
     c->mg = nullptr;
 }
@@ -701,7 +772,8 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     if (cudaMalloc(&g->P, nP * sizeof(double2)) != cudaSuccess || cudaMalloc(&g->Dc, nD * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Dclo, nD * sizeof(float2)) != cudaSuccess || cudaMalloc(&g->Phi, nP * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&g->Plo, nP * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&g->Plo, nP * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&g->Gt, sizeof(double2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess) {
         cudaGetLastError();
         wd_mg_free(c);
         set_error("wd_mg_setup: allocation failed");
@@ -718,6 +790,7 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     k_tv_to_P<<<(unsigned)((nP + 255) / 256), 256, 0, c->st>>>((const double2 *)tvd, g->P, M);
     k_block_mgs<<<2 * g->Vc, 256, 0, c->st>>>(g->P, M);
     k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
+    k_gram_t<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->P, g->Gt, M);
     double2 hg[4][4][4];
     host_gamma(hg);
     WD_CUDA(cudaMemcpyToSymbolAsync(c_gamma, hg, sizeof(hg), 0, cudaMemcpyHostToDevice, c->st));
@@ -733,7 +806,7 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
-    c->launches += 6;
+    c->launches += 7;
     WD_CUDA(cudaGetLastError());
     WD_TRY(coarse_tc_build(c));
     WD_CUDA(cudaStreamSynchronize(c->st));

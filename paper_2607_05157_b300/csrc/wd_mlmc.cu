@@ -240,19 +240,17 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
     // (cp) the coarse probing vectors of each sample
     const int mc = cp ? cp->m : 1;          // coarse vectors per level-2 sample
     const long total2 = (long)N2 * mc;
+    // level 2 holds coarse fields only (~24 per RHS in the coarse solve): up to ~32 GB of them per batch
+    long cb = (long)(32e9 / ((double)ncoarse * 16.0 * 24.0));
+    if (cb < 1) cb = 1;
     const int B2 = batch > 0 ? (int)(batch < total2 ? batch : total2)
-                             : auto_batch(c, (int)(total2 < (1L << 30) ? total2 : (1L << 30)));
+                             : (int)(total2 < cb ? total2 : (cb < (1L << 30) ? cb : (1L << 30)));
     for (long s0l = 0; s0l < total2; s0l += B2) {
         const int s0 = (int)s0l;
         const int nb = (int)(total2 - s0l < B2 ? total2 - s0l : B2);
-        const size_t f = field_bytes(g, P64, nb);
-        double *xi, *yc, *ae, *ao, *be, *bo;
+        double *xi, *yc;
         WD_TRY(ws_get(c, "mlmc.bc", sizeof(double2) * ncoarse * nb, (void **)&xi));
         WD_TRY(ws_get(c, "mlmc.yc", sizeof(double2) * ncoarse * nb, (void **)&yc));
-        WD_TRY(ws_get(c, "mlmc.be", f, (void **)&ae));
-        WD_TRY(ws_get(c, "mlmc.bo", f, (void **)&ao));
-        WD_TRY(ws_get(c, "mlmc.ze", f, (void **)&be));
-        WD_TRY(ws_get(c, "mlmc.zo", f, (void **)&bo));
         const long n = ncoarse * nb;
         if (cp)
             k_coarse_noise_probe<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>((double2 *)xi, seed, s0, ncoarse,
@@ -263,9 +261,14 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         WD_CUDA(cudaGetLastError());
         int s = coarse_solve(c, xi, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_prolong_eo(c, xi, ae, ao, nb, true));
-        WD_TRY(mg_prolong_eo(c, yc, be, bo, nb, true));
-        WD_TRY(contract_fields(c, ae, ao, be, bo, gamma5, nb, X2, s0, mc));
+        // X_2(t) = sum_{x in t} (P xi)^dag B (P y)(x), contracted on the coarse
+        // lattice with the per-timeslice Gram matrices of P (no fine fields)
+        double *part;
+        WD_TRY(ws_get(c, "mlmc.part", sizeof(double) * 2 * (size_t)nb * T, (void **)&part));
+        WD_TRY(mg_contract_coarse_t(c, xi, yc, gamma5, nb, part));
+        k_accumulate_fields<<<(nb * T + 127) / 128, 128, 0, c->st>>>(T, part, 1, X2, s0, nb, mc);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
         ns += nb;
     }
     double *m1, *v1, *m2, *v2, *mean, *var;
@@ -361,6 +364,16 @@ int mg_generate_tv(wd_ctx *c, int nv, int iters, uint64_t seed, double *tv_dev) 
 }  // namespace wd
 
 using namespace wd;
+
+extern "C" int wd_mg_test_vectors(wd_ctx *c, int nv, int iters, uint64_t seed, double *tv_out) {
+    if (!c || nv < 1 || iters < 0 || !tv_out) {
+        set_error("wd_mg_test_vectors: bad argument");
+        return WD_EINVAL;
+    }
+    WD_TRY(mg_generate_tv(c, nv, iters, seed, tv_out));
+    WD_CUDA(cudaStreamSynchronize(c->st));
+    return WD_OK;
+}
 
 extern "C" int wd_mlmc_level2_samples(wd_ctx *c, double *samples_out, int n2) {
     if (!c || !samples_out || n2 != c->last_n2) { set_error("wd_mlmc_level2_samples: no matching MLMC2 estimate"); return WD_EINVAL; }

@@ -9,9 +9,13 @@
 // this variant stages them in one file-scope device array instead, so a call
 // allocates nothing.
 //
-// The array holds WD_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU that loads
-// this library, until the process exits.  Its device address is looked up
-// once per device, on the first call made with that device current.  Every
+// The array holds WD_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU on which a
+// context is created, until the process exits.  With lazy module loading the
+// CUDA runtime creates a module's device arrays when the module is first
+// used, so wd_create resolves the array's device address (once per device,
+// with the context's device current) and keeps it in the context: the array
+// exists from wd_create on, and the entry point itself allocates nothing and
+// stages on the context's own device whichever device is current.  Every
 // call uses the same array and leaves its contents behind; the staging fields
 // are fully overwritten before they are read, so nothing needs clearing, but
 // two calls whose work overlaps on the GPU (different streams, or different
@@ -32,7 +36,8 @@ void *g_scratch[WD_NOALLOC_MAX_DEVICES];
 
 using namespace wd;
 
-static int noalloc_scratch_ptr(void **out) {
+namespace wd {
+int noalloc_scratch_ptr(void **out) {
     int dev = 0;
     WD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= WD_NOALLOC_MAX_DEVICES) {
@@ -52,6 +57,7 @@ static int noalloc_scratch_ptr(void **out) {
     *out = g_scratch[dev];
     return WD_OK;
 }
+}  // namespace wd
 
 extern "C" int wd_apply_noalloc(wd_ctx *c, const void *in, void *out, int nrhs, int prec, int dagger) {
     if (!c || nrhs < 0 || ((!in || !out) && nrhs > 0) || prec < 0 || prec > 2) {
@@ -70,14 +76,18 @@ extern "C" int wd_apply_noalloc(wd_ctx *c, const void *in, void *out, int nrhs, 
                   nrhs, need, WD_NOALLOC_SCRATCH_BYTES);
         return WD_EINVAL;
     }
-    unsigned char *base;
-    WD_TRY(noalloc_scratch_ptr((void **)&base));
+    unsigned char *base = (unsigned char *)c->noalloc_scratch;
+    if (!base) {
+        set_error("wd_apply_noalloc: the context has no static staging array");
+        return WD_ENOTSUP;
+    }
     void *ie = base, *io = base + a_in, *oe = base + 2 * a_in, *oo = base + 2 * a_in + a_out;
     const bool udbl = prec == P64;
     WD_TRY(user_to_eo(c, in, udbl, pf, ie, io, nrhs));
     const size_t per = (size_t)8 * 9 * c->g.Vh * (pf == P64 ? 16 : pf == P32 ? 8 : 4);
     HopArgs A;
     A.a = 1.0; A.b = -c->kappa; A.c = 0.0; A.w2 = nullptr; A.nrhs = nrhs; A.nrb = 1; A.g = c->g;
+    A.err = c->hop_err;
     const int R = c->hop_R[pf], th = c->hop_threads[pf];
     for (int p = 0; p < 2; ++p) {
         // (D x)_p = x_p - kappa H_{p,1-p} x_{1-p}

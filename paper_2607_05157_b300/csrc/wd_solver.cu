@@ -363,6 +363,21 @@ static int schur_res64(wd_ctx *c, const double *b, const double *x, double *r, i
     return hop(c, pt, S->pout, 0, r, S->tmp, b, 1.0, c->kappa * c->kappa, nrhs, false, x, -1.0, nullptr, S->x_ddl);
 }
 
+// dst[rhs][i] = fac[rhs] * src[rhs][i] for FP64 eo fields (per = doubles per
+// RHS of one parity); fac a power of two, so the product is exact
+__global__ void k_scale_rhs(double *dst, const double *src, const double *fac, long per, int nrhs) {
+    const long n = per * nrhs;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = fac[i / per] * src[i];
+}
+
+static int scale_rhs(wd_ctx *c, double *dst, const double *src, const double *fac, int nrhs) {
+    k_scale_rhs<<<1184, 256, 0, c->st>>>(dst, src, fac, 24L * c->g.Vh, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol,
              int prec, int max_iter, int *iters_out, double *resid_out, const int *src_tsup,
              const double **bhat_out) {
@@ -383,12 +398,44 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     WD_CUDA(cudaStreamSynchronize(c->st));
     for (int r = 0; r < nrhs; ++r) bnorm2[r] += bnorm2[nrhs + r];
     bnorm2.resize(nrhs);
-    WD_CUDA(cudaMemcpyAsync(bn2 + 2 * nrhs, bnorm2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
     // The FP64 steps (source, residuals, reconstruction) of a mixed solve run
     // the double-float stencil: FP64 fields, ~2^-44 normwise, well below the
     // tolerances the outer loop certifies (tol < 1e-12 and the FP64 mode keep
     // FP64 arithmetic).
     const int pd = prec == P64 || tol < 1e-12 ? P64 : c->outer;
+    // A double-float number holds magnitudes in [2^-103, 2^128): a source whose
+    // norm lies outside [2^-30, 2^30] is solved as 2^-e b (e its binary
+    // exponent, so the scaled norm lies in [1, 2)) and the solution scaled back
+    // by 2^e.  Powers of two commute with every rounding on the way, so the
+    // result is the unscaled solve's, scaled.
+    std::vector<double> fac(nrhs, 1.0);
+    bool rescale = false;
+    if (pd == PDD)
+        for (int r = 0; r < nrhs; ++r) {
+            const double nb = sqrt(bnorm2[r]);
+            if (nb > 0.0 && isfinite(nb) && (nb < 0x1p-30 || nb > 0x1p30)) {
+                int e;
+                frexp(nb, &e);
+                fac[r] = ldexp(1.0, 1 - e);
+                bnorm2[r] *= fac[r] * fac[r];
+                rescale = true;
+            }
+        }
+    double *fac_dev = nullptr;
+    std::vector<double> both;      // factors and their inverses (alive until the copy has run)
+    if (rescale) {
+        double *bs;
+        WD_TRY(ws_get(c, "sol.bscaled", 2 * f64, (void **)&bs));
+        WD_TRY(ws_get(c, "sol.fac", sizeof(double) * 2 * nrhs, (void **)&fac_dev));
+        both = fac;
+        for (int r = 0; r < nrhs; ++r) both.push_back(1.0 / fac[r]);
+        WD_CUDA(cudaMemcpyAsync(fac_dev, both.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
+        WD_TRY(scale_rhs(c, bs, b_e, fac_dev, nrhs));
+        WD_TRY(scale_rhs(c, bs + f64 / sizeof(double), b_o, fac_dev, nrhs));
+        b_e = bs;
+        b_o = bs + f64 / sizeof(double);
+    }
+    WD_CUDA(cudaMemcpyAsync(bn2 + 2 * nrhs, bnorm2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
     // b_hat = b_e + k H_eo b_o                                         (a3)
     WD_TRY(hop(c, pd, pd, 0, bhat, b_o, b_e, 1.0, k, nrhs, false, nullptr, 0.0, src_tsup));
     if (bhat_out) *bhat_out = bhat;
@@ -438,6 +485,12 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
             resid_out[r] = res;
             if (!(res <= tol * 1.0000001) && status == WD_OK) status = isfinite(res) ? WD_ENOCONV : WD_EBREAKDOWN;
         }
+    }
+    if (rescale) {
+        // back to the caller's scale (the relative residuals above are scale-free)
+        WD_TRY(scale_rhs(c, x_e, x_e, fac_dev + nrhs, nrhs));
+        if (x_o) WD_TRY(scale_rhs(c, x_o, x_o, fac_dev + nrhs, nrhs));
+        if (bhat_out) WD_TRY(scale_rhs(c, bhat, bhat, fac_dev + nrhs, nrhs));
     }
     WD_TRY(hop_err_check(c));
     if (iters_out)

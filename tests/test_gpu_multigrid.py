@@ -32,6 +32,70 @@ def _coarse_shape(dims, agg, nv, nrhs):
     return (nrhs, Vc, 2 * nv)
 
 
+# Element-wise bound factor of the tensor-core coarse stencil against the FP64
+# operator: BF16 operands (blocks and input rounded to nearest, 2^-9 each, so
+# 2^-8 per product), FP32 accumulation of at most 9 blocks x 2 x 96 real
+# products (gamma_n, n <= 1728, 2^-24 each), and a factor 2 for splitting each
+# complex product into its real terms: |y - ref| <= U_TC * sum_b |A_b| |x|.
+U_TC = 2 * (2.0 ** -8 + 1728 * 2.0 ** -24)
+
+
+def _coarse_nbr(cd):
+    """Neighbour table of the coarse torus, lexicographic (x fastest):
+    [Vc][9] with 0 the site, 1 + mu the forward and 5 + mu the backward one."""
+    Vc = int(np.prod(cd))
+    X = np.arange(Vc)
+    c = [X % cd[0], (X // cd[0]) % cd[1], (X // (cd[0] * cd[1])) % cd[2], X // (cd[0] * cd[1] * cd[2])]
+    def lexi(q):
+        return q[0] + cd[0] * (q[1] + cd[1] * (q[2] + cd[2] * q[3]))
+    nbr = np.empty((Vc, 9), np.int64)
+    nbr[:, 0] = X
+    for mu in range(4):
+        for k, step in ((1 + mu, 1), (5 + mu, -1)):
+            q = list(c)
+            q[mu] = (q[mu] + step) % cd[mu]
+            nbr[:, k] = lexi(q)
+    return nbr
+
+
+def _coarse_blocks(ctx, cd, ncd):
+    """The 9 blocks A_b(X) of D_c, read off the GPU's FP64 coarse operator
+    (held to the oracle's P^dag D P at 1e-12 by test_transfer_and_coarse_operator)
+    by probing: a distance-2 colouring of the coarse torus (every extent >= 3,
+    so that X and its 8 neighbours are 9 distinct sites with 9 distinct
+    colours) and, per colour and coarse dof k, one application to the vector
+    that is e_k on every site of that colour.  Returns (A [Vc][9][ncd][ncd], nbr)."""
+    import torch
+    from oracle import coloring
+    from paper_2607_05157_b300 import wd_coarse_apply
+    assert min(cd) >= 3
+    nbr = _coarse_nbr(cd)
+    Vc = nbr.shape[0]
+    nc, sigma = coloring.search(cd, 2)
+    col = coloring.colors(cd, sigma, nc)
+    which = np.full((Vc, nc), -1, np.int64)        # block b of site Y that sees colour c
+    for b in range(9):
+        which[np.arange(Vc), col[nbr[:, b]]] = b
+    assert (which >= 0).all()
+    A = np.zeros((Vc, 9, ncd, ncd), np.complex128)
+    probes = [(c, k) for c in range(nc) for k in range(ncd)]
+    for i0 in range(0, len(probes), 128):
+        chunk = probes[i0:i0 + 128]
+        x = np.zeros((len(chunk), Vc, ncd), np.complex128)
+        for r, (c, k) in enumerate(chunk):
+            x[r, col == c, k] = 1.0
+        y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(x.shape, dtype=torch.complex128, device='cuda'),
+                            0).cpu().numpy()
+        for r, (c, k) in enumerate(chunk):
+            A[np.arange(Vc), which[:, c], :, k] = y[r]
+    return A, nbr
+
+
+def _coarse_abs_bound(A, nbr, x):
+    """sum_b |A_b(X)| |x(nbr_b(X))| for one coarse vector x [Vc][ncd]."""
+    return sum(np.einsum('vij,vj->vi', np.abs(A[:, b]), np.abs(x[nbr[:, b]])) for b in range(9))
+
+
 @pytest.mark.parametrize("dims,agg,nv", CASES)
 def test_transfer_and_coarse_operator(dims, agg, nv):
     from paper_2607_05157_b300 import wd_restrict, wd_prolong, wd_coarse_apply
@@ -48,13 +112,18 @@ def test_transfer_and_coarse_operator(dims, agg, nv):
     for r in range(3):
         assert rel(rc[r].reshape(-1), P.conj().T @ v[r].reshape(-1)) < 1e-12
         assert rel(pf[r].reshape(-1), P @ yc[r].reshape(-1)) < 1e-12
-    # coarse operator, FP64 and mixed (BF16 tensor-core or FP32 operands)
+    # coarse operator, FP64 and mixed (BF16 tensor-core or FP32 operands), the
+    # mixed one element by element against U_TC |D_c| |x|
     y64 = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
     ylo = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    Dabs = Dc.copy()
+    Dabs.data = np.abs(Dabs.data)
     for r in range(3):
         ref = Dc @ yc[r].reshape(-1)
         assert rel(y64[r].reshape(-1), ref) < 1e-12
         assert rel(ylo[r].reshape(-1), ref) < 2e-2
+        bound = Dabs @ np.abs(yc[r].reshape(-1))
+        assert np.all(np.abs(ylo[r].reshape(-1) - ref) <= U_TC * bound)
     ctx.close()
 
 
@@ -203,13 +272,98 @@ def test_tensor_core_coarse_stencil_16x16x16x32():
     rng = np.random.default_rng(12)
     x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
     y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
     P = multigrid.prolongator(tv, dims, agg)
     shape = synth.spinors(dims, 1, 0).shape[1:]
+    A, nbr = _coarse_blocks(ctx, [L // a for L, a in zip(dims, agg)], 2 * nv)
     for r in (0, 127, 129):
         f = (P @ x[r].reshape(-1)).reshape(shape)
         ref = P.conj().T @ wilson.apply(U, f, 0.13, BC).reshape(-1)
+        assert rel(y64[r].reshape(-1), ref) < 1e-12
         err = rel(y[r].reshape(-1), ref)
         # BF16 operands leave a ~1e-3 error floor: proves the tensor-core path ran
         # (the FP32 CUDA-core fallback would sit near 1e-7)
         assert 1e-5 < err < 2e-2, err
+    # every element of every RHS against the probed blocks
+    for r in range(x.shape[0]):
+        bound = _coarse_abs_bound(A, nbr, x[r])
+        assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
+    ctx.close()
+
+
+def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
+    """The two-level workload's coarse lattice (24^3 x 48, 4^4 aggregates, 24
+    test vectors: 2592 coarse sites of 48 x 48 blocks), 200 RHS (a full and a
+    ragged 128-row tile): every element of sampled RHS against the FP64 coarse
+    operator within U_TC |A| |x|, the blocks probed from that operator."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply
+    dims, agg, nv = (24, 24, 24, 48), (4, 4, 4, 4), 24
+    ctx = Context(dims, synth.gauge_field(dims, 0.5, 1004), 0.13, BC)
+    wd_mg_setup(ctx.h, None, nv, agg, tv_iters=1, seed=5)
+    cs = _coarse_shape(dims, agg, nv, 200)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
+    A, nbr = _coarse_blocks(ctx, [L // a for L, a in zip(dims, agg)], 2 * nv)
+    for r in (0, 1, 64, 127, 128, 199):
+        bound = _coarse_abs_bound(A, nbr, x[r])
+        assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
+        assert 1e-5 < rel(y[r], y64[r]) < 2e-2
+    ctx.close()
+
+
+def test_gpu_test_vectors_match_oracle_inverse_iteration():
+    """wd_mg_test_vectors against the oracle's inverse iteration (Sec. 2's
+    setup) from the same Rademacher starts, after 1, 2 and 3 iterations.  Each
+    GPU solve stops at a relative residual eps = 1e-6 while the oracle solves to
+    1e-12, so the normalised map v -> D^{-1} v / |D^{-1} v| (Lipschitz constant
+    at most 2 cond(D)) bounds the error of iterate i by
+    e_i <= 2 cond(D) (e_{i-1} + eps), e_0 = 0; cond(D) from the dense SVD."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_test_vectors
+    dims, kappa, nv, seed, eps = (4, 4, 4, 4), 0.12, 12, 31, 1e-6
+    U = synth.gauge_field(dims, 0.5, 1004)
+    ctx = Context(dims, U, kappa, BC)
+    sv = np.linalg.svd(wilson.sparse_matrix(U, kappa, BC).toarray(), compute_uv=False)
+    cond = sv[0] / sv[-1]
+    e_prev = 0.0
+    for iters in (1, 2, 3):
+        out = torch.empty((nv,) + synth.spinors(dims, 1, 0).shape[1:], dtype=torch.complex128, device='cuda')
+        got = wd_mg_test_vectors(ctx.h, nv, iters, seed, out).cpu().numpy()
+        ref = multigrid.test_vectors(lambda v: wilson.apply(U, v, kappa, BC), dims, nv, iters, seed)
+        e = max(np.linalg.norm((got[k] - ref[k]).reshape(-1)) for k in range(nv))
+        bound = 2 * cond * (e_prev + eps)
+        assert e <= bound, (iters, e, bound)
+        assert all(abs(np.linalg.norm(got[k]) - 1.0) < 1e-12 for k in range(nv))
+        e_prev = e
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,agg,nv", [((4, 4, 4, 4), (2, 2, 2, 2), 12), ((8, 8, 8, 8), (4, 4, 4, 4), 24)])
+def test_gpu_built_prolongator_matches_oracle_mgs(dims, agg, nv):
+    """wd_mg_setup(tv = NULL) builds P from its own test vectors: P^dag v and
+    P y agree element by element with the oracle's prolongator (block MGS,
+    Sec. 2) of the same GPU test vectors (wd_mg_test_vectors, same seed)."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_setup, wd_mg_test_vectors, wd_restrict, wd_prolong
+    U = synth.gauge_field(dims, 0.5, 1005)
+    ctx = Context(dims, U, 0.13, BC)
+    shape = synth.spinors(dims, 1, 0).shape[1:]
+    tv = wd_mg_test_vectors(ctx.h, nv, 3, 9, torch.empty((nv,) + shape, dtype=torch.complex128,
+                                                          device='cuda')).cpu().numpy()
+    wd_mg_setup(ctx.h, None, nv, agg, tv_iters=3, seed=9)
+    P = multigrid.prolongator(tv, dims, agg)
+    v = synth.spinors(dims, 2, 21)
+    cs = _coarse_shape(dims, agg, nv, 2)
+    rng = np.random.default_rng(22)
+    y = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    rc = wd_restrict(ctx.h, to_dev(v), torch.empty(cs, dtype=torch.complex128, device='cuda')).cpu().numpy()
+    pf = wd_prolong(ctx.h, to_dev(y), torch.empty(v.shape, dtype=torch.complex128, device='cuda')).cpu().numpy()
+    for r in range(2):
+        ref_r = P.conj().T @ v[r].reshape(-1)
+        ref_p = P @ y[r].reshape(-1)
+        assert np.abs(rc[r].reshape(-1) - ref_r).max() <= 1e-12 * np.abs(ref_r).max()
+        assert np.abs(pf[r].reshape(-1) - ref_p).max() <= 1e-12 * np.abs(ref_p).max()
     ctx.close()

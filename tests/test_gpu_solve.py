@@ -178,15 +178,16 @@ def test_fp64_norms_scale_invariant(shift):
         assert abs(res3[r] - tr) <= 1e-12 * tr
 
 
-@pytest.mark.parametrize("shift", [40, -40])
+@pytest.mark.parametrize("shift", [40, -40, 200, -200, 133, -134])
 def test_mixed_solve_scale_invariant(shift):
     """The mixed-precision solve is invariant under scaling the source by
-    2^shift (inside the double-float range): the outer residual (double-float
-    layout), its norm (running power-of-two exponent) and its scaled FP32
-    copy (scale applied as a power of two and an FP32 significand) all
-    commute with the scaling, and the inner FP32 solves see the same
-    normalised residuals -- the same iterations, the solution scaled bit for
-    bit, the same reported residual."""
+    2^shift: the outer residual (double-float layout), its norm (running
+    power-of-two exponent) and its scaled FP32 copy (scale applied as a power
+    of two and an FP32 significand) all commute with the scaling, the inner
+    FP32 solves see the same normalised residuals, and a source whose norm
+    leaves [2^-30, 2^30] (2^+-200, 1e+-40: outside the double-float range) is
+    solved at a power-of-two scale of norm in [1, 2) -- the same iterations,
+    the solution scaled bit for bit, the same reported residual."""
     from paper_2607_05157_b300 import Context
     dims = (4, 4, 4, 8)
     U = synth.gauge_field(dims, 0.5, 1012)

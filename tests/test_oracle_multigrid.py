@@ -301,3 +301,86 @@ def test_mlmc3_unbiased_and_levels(mg3):
         V = estimators.hutchinson_variance(M)
         assert abs(m - ex) < 5 * np.sqrt(V / Xl.shape[0]) + 1e-12
     assert abs(sum(exact) - np.trace(Dinv)) < 1e-12 * abs(np.trace(Dinv))
+
+
+# ---- test vectors by inverse iteration (Sec. 2's setup) ---------------------
+
+def _free_dinv(v, dims, kappa, bc):
+    """D^{-1} v for U = 1 from the momentum-space closed form
+    D(p)^{-1} = (a - i gamma.b) / (a^2 + |b|^2) (independent of the stencil
+    and of the solver): twist the antiperiodic directions, FFT, multiply,
+    inverse FFT, untwist."""
+    from oracle.gamma import GAMMA, ID4
+    w = np.asarray(v, np.complex128)
+    twist = np.ones(w.shape[:4], np.complex128)
+    ps = []
+    for mu, L in enumerate(dims):
+        ax = 3 - mu                                  # axes (t, z, y, x)
+        k = np.arange(L)
+        ps.append((2 * np.pi * k + (np.pi if bc[mu] == -1 else 0.0)) / L)
+        if bc[mu] == -1:
+            shp = [1, 1, 1, 1]
+            shp[ax] = L
+            twist = twist * np.exp(1j * np.pi * k / L).reshape(shp)
+    wt = np.fft.fftn(w / twist[..., None, None], axes=(0, 1, 2, 3))
+    pt, pz, py, px = np.meshgrid(ps[3], ps[2], ps[1], ps[0], indexing='ij')
+    P = [px, py, pz, pt]
+    a = 1 - 2 * kappa * sum(np.cos(p) for p in P)
+    bs = [2 * kappa * np.sin(p) for p in P]
+    den = a * a + sum(b * b for b in bs)
+    M = np.einsum('...,st->...st', a / den, ID4)
+    for mu in range(4):
+        M = M - 1j * np.einsum('...,st->...st', bs[mu] / den, GAMMA[mu])
+    yt = np.einsum('tzyxsr,tzyxrc->tzyxsc', M, wt)
+    return np.fft.ifftn(yt, axes=(0, 1, 2, 3)) * twist[..., None, None]
+
+
+def test_free_dinv_helper_inverts_the_stencil():
+    dims, kappa, bc = (4, 4, 2, 6), 0.12, (1, 1, 1, -1)
+    U = synth.unit_gauge(dims)
+    v = synth.spinors(dims, 1, 3)[0]
+    y = _free_dinv(v, dims, kappa, bc)
+    assert np.abs(wilson.apply(U, y, kappa, bc) - v).max() < 1e-12 * np.abs(v).max()
+
+
+def test_test_vectors_free_field_closed_form():
+    """Two inverse iterations on U = 1 equal D^{-2} eta / ||D^{-2} eta|| with
+    D^{-1} from momentum space, for the Rademacher starts of samples 2^22 + k."""
+    from oracle import noise
+    dims, kappa, bc, seed = (4, 4, 4, 4), 0.12, (1, 1, 1, -1), 7
+    U = synth.unit_gauge(dims)
+    tv = multigrid.test_vectors(lambda v: wilson.apply(U, v, kappa, bc), dims, 2, 2, seed)
+    shape = (dims[3], dims[2], dims[1], dims[0], 4, 3)
+    for k in range(2):
+        v = noise.rademacher(seed, (1 << 22) + k, 12 * 256).reshape(shape)
+        for _ in range(2):
+            v = _free_dinv(v, dims, kappa, bc)
+            v = v / np.linalg.norm(v)
+        assert np.abs(tv[k] - v).max() < 1e-9
+    # no iterations: the starts themselves
+    tv0 = multigrid.test_vectors(lambda v: wilson.apply(U, v, kappa, bc), dims, 1, 0, seed)
+    assert np.array_equal(tv0[0].real.reshape(-1), noise.rademacher(seed, 1 << 22, 12 * 256))
+
+
+def test_test_vectors_converge_to_the_smallest_eigenspace():
+    """Inverse iteration converges to the invariant subspace of the eigenvalues
+    of D of smallest modulus (a complex-conjugate pair for this gamma5-hermitian
+    D); the eigen-decomposition is numpy's dense one."""
+    dims, kappa, bc = (2, 2, 2, 2), 0.16, (1, 1, 1, -1)
+    U = synth.gauge_field(dims, 0.5, 11)
+    Dm = wilson.sparse_matrix(U, kappa, bc).toarray()
+    lam, E = np.linalg.eig(Dm)
+    mod = np.abs(lam)
+    order = np.argsort(mod)
+    m0 = mod[order[0]]
+    low = order[mod[order] <= m0 * (1 + 1e-9)]
+    nxt = mod[order[len(low)]]
+    ratio = m0 / nxt
+    assert ratio < 0.95
+    iters = int(np.ceil(np.log(1e-11) / np.log(ratio)))
+    tv = multigrid.test_vectors(lambda v: wilson.apply(U, v, kappa, bc), dims, 1, iters, 5)
+    v = tv[0].reshape(-1)
+    B = E[:, low]
+    coef = np.linalg.lstsq(B, v, rcond=None)[0]
+    assert np.linalg.norm(v - B @ coef) < 1e-7
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-14

@@ -18,7 +18,7 @@ def _call(fn, ctx, x, out, prec, dagger):
     return fn(ctx.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.shape[0], prec, dagger)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-6), (2, 1e-2)])
 def test_noalloc_matches_apply_twice(prec, tol):
     import torch
     from paper_2607_05157_b300 import Context, lib, WD_OK
@@ -31,8 +31,15 @@ def test_noalloc_matches_apply_twice(prec, tol):
         ref = torch.empty_like(x)
         got = torch.full_like(x, float('nan'))
         assert _call(lib.wd_apply, ctx, x, ref, prec, dagger) == WD_OK
+        # a first call loads the kernels it uses (code, not data); the second one
+        # is checked to leave the device's free memory as it was: nothing allocated
+        assert _call(lib.wd_apply_noalloc, ctx, x, got, prec, dagger) == WD_OK
+        got.fill_(float('nan'))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert _call(lib.wd_apply_noalloc, ctx, x, got, prec, dagger) == WD_OK
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
         a, b = got.cpu().numpy(), ref.cpu().numpy()
         for r in range(nrhs):
             assert np.linalg.norm(a[r] - b[r]) <= tol * np.linalg.norm(b[r])
