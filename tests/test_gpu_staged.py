@@ -10,6 +10,7 @@ import pytest
 import synth
 from oracle import wilson
 from tests.gpu_util import rel, to_dev
+from tests.test_gpu_dslash import ELEM_U, abs_stencil_bound, assert_elementwise
 
 pytestmark = pytest.mark.gpu
 BC = (1, 1, 1, -1)
@@ -32,12 +33,14 @@ def test_variant_parity(override, code, prec, tol, dagger):
     override(code)
     dims = (8, 8, 8, 16)            # timeslice of 256 half-sites: the staged variant applies
     U = synth.gauge_field(dims, 0.5, 1002)
-    psi = synth.spinors(dims, 7, 33)
+    psi = synth.spinors(dims, 7, 33).astype(np.complex64).astype(np.complex128)
     ctx = Context(dims, U, 0.125, BC)
     y = ctx.apply(to_dev(psi, torch.complex64), prec=prec, dagger=dagger).cpu().numpy()
     f = wilson.apply_dagger if dagger else wilson.apply
     for r in (0, 3, 6):
-        assert rel(y[r], f(U, psi[r], 0.125, BC)) < tol
+        ref = f(U, psi[r], 0.125, BC)
+        assert rel(y[r], ref) < tol
+        assert_elementwise(y[r], ref, abs_stencil_bound(U, psi[r], 0.125), ELEM_U[prec], (code, r))
     ctx.close()
 
 
