@@ -19,7 +19,12 @@
 // into a TMEM accumulator and releases each stage with tcgen05.commit; the 4
 // warps then read their 32 TMEM lanes with tcgen05.ld and store FP32 rows.
 // Every mbarrier wait is bounded: on timeout the kernel raises an error flag,
-// skips the remaining work, frees its TMEM and returns.
+// skips the remaining work, lets the copies it issued land, frees its TMEM
+// and returns; a producer wait also gives up as soon as another role of the
+// CTA has failed.  The environment variable WD_TEST_TC_STALL=1 makes the MMA
+// issuer wait, with a short limit, on a barrier nothing arrives on (a test of
+// that failure path without any fault: the call returns WD_ETIMEOUT and the
+// context stays usable).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -31,6 +36,7 @@ static constexpr int TC_M = 128;      // RHS per tile
 static constexpr int TC_KC = 32;      // K elements (bf16) per chunk = one 64-byte swizzle row
 static constexpr int TC_STAGES = 4;
 static constexpr long TC_SPIN = 1L << 24;   // bounded waits
+static constexpr long TC_SPIN_TEST = 1L << 10;   // the short limit of the stall test
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -40,10 +46,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// bounded wait for phase `parity` to complete; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait for phase `parity` to complete; returns false after `limit`
+// polls, or early once *abort (another role's failure flag) is set
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long limit = TC_SPIN,
+                                          const volatile int *abort = nullptr) {
     const uint32_t a = smem_u32(bar);
-    for (long i = 0; i < TC_SPIN; ++i) {
+    for (long i = 0; i < limit; ++i) {
+        if (abort && (i & 255) == 255 && *abort) return false;
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -92,6 +101,7 @@ struct TcArgs {
     float *y;           // FP32 coarse field [nrhs][Vc][ncd] complex
     int *err;           // set to a nonzero code on a timed-out wait
     int Vc, ncd, nrhs;
+    int stall_test;     // 1: the MMA issuer waits (short limit) on a barrier nothing arrives on
 };
 
 template <int N>
@@ -138,7 +148,10 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
         // producer: TMA loads of chunk kc into stage kc % S
         for (int kc = 0; kc < NCHUNK && !s_fail; ++kc) {
             const int s = kc % TC_STAGES;
-            if (kc >= TC_STAGES && !mbar_wait(&empty[s], ((kc / TC_STAGES) - 1) & 1)) { s_fail = 1; break; }
+            if (kc >= TC_STAGES && !mbar_wait(&empty[s], ((kc / TC_STAGES) - 1) & 1, TC_SPIN, &s_fail)) {
+                if (!s_fail) s_fail = 1;
+                break;
+            }
             const int b = kc / KB, kk = (kc % KB) * TC_KC;
             const int nb = A.nbr[X * 9 + b];
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
@@ -151,7 +164,8 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
         constexpr uint32_t idesc = idesc_bf16_f32(TC_M, N);
         for (int kc = 0; kc < NCHUNK; ++kc) {
             const int s = kc % TC_STAGES;
-            if (!mbar_wait(&full[s], (kc / TC_STAGES) & 1)) { s_fail = 2; break; }
+            const bool got = A.stall_test ? mbar_wait(done, 0, TC_SPIN_TEST) : mbar_wait(&full[s], (kc / TC_STAGES) & 1);
+            if (!got) { s_fail = 2; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
@@ -173,7 +187,7 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
     }
     __syncwarp();
     // epilogue: all 4 warps wait for the accumulator, read their 32 lanes
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, A.stall_test ? TC_SPIN_TEST : TC_SPIN, &s_fail));
     if (!ok && lane == 0) s_fail = 3;
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncwarp();
@@ -291,6 +305,10 @@ int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs) {
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
     TcArgs A;
     A.nbr = g->nbr; A.y = y; A.err = err; A.Vc = g->Vc; A.ncd = g->ncd; A.nrhs = nrhs;
+    {
+        const char *e = getenv("WD_TEST_TC_STALL");
+        A.stall_test = e && atoi(e) == 1;
+    }
     const unsigned grid = (unsigned)g->Vc * ((nrhs + TC_M - 1) / TC_M);
     const size_t smem = tc_smem(N);
     int slot;
