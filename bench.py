@@ -1,27 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the trace-estimation hot path on B300.
 
-Workload (the 8^3 x 16 configuration): Wilson-Dirac operator on an 8^3 x 16
-lattice (antiperiodic in t), kappa = 0.125, synthetic SU(3) links
-(Gram-Schmidt projection of I + 0.5 G, seed 1002) standing in for the paper's
-RQCD ensemble; per step and per GPU 256 right-hand sides = 16 Rademacher
-samples x 16 timeslices (time dilution), estimating the disconnected loop
-O(t) = tr[g5 D^{-1}(t,t)] (Eq. 21), plus the pseudoscalar correlator
-C(t) = sum_x |D^{-1}(x,t;0,0)|^2 from 12 point sources, each solve to a true
-FP64 relative residual of 1e-10 by FP32 (or BF16) BiCGStab inside FP64 defect
-correction.
+Headline workload (the largest single-GPU configuration: the two-level
+multigrid MLMC one): Wilson-Dirac operator on a 24^3 x 48 lattice
+(antiperiodic in t), kappa = 0.13, synthetic SU(3) links (Gram-Schmidt
+projection of I + 0.5 G, seed 1004) standing in for the paper's RQCD ensemble;
+4^4 aggregates, N_v = 24 test vectors from 3 inverse iterations on Rademacher
+starts, coarse operator P^dag D P as a 9-point stencil of 48 x 48 blocks
+(2592 coarse sites) applied on the tensor cores (BF16 operands, FP32
+accumulate).  One step = one two-level MLMC estimate (Eq. 12, L = 2) of
+tr[g5 D^{-1}(t,t)] with 64 level-1 and 512 level-2 samples: RHS generation on
+the device, the 64-RHS fine solve and its coarse correction P D_c^{-1} P^dag,
+512 coarse solves, per-timeslice FP64 contractions, means and variances; all
+solves to a true relative residual of 1e-10 by FP32 (or BF16) inner BiCGStab
+inside FP64 defect correction.  The multigrid setup (test vectors, P, D_c) is
+a one-off per gauge field, outside the timed steps (reported as setup_s; the
+end-to-end steps include it).
 
-A step = one trace_estimate call plus one wd_point_correlator call, issued from two host threads on two
-contexts with their own CUDA streams so that the two independent solves overlap on the GPU (--serial: one
-after the other on one context): RHS generation on the device, even-odd
-source, 256-RHS batched mixed-precision solve (stencil, BLAS-1, FP64 residual),
-odd-site reconstruction, FP64 per-timeslice contraction, mean and sample
-variance.  `value` = algorithmic stencil bytes moved by all stencil launches
-of the step / step time (GB/s), so it is the whole job's rate in the metric's
-unit; `roofline` gives the dominant kernel (the FP32/BF16 stencil) against the
-measured HBM copy bandwidth.  `trace_time` compares, at the same noise and so
-the same statistical error, the mixed batched path with the plain FP64
-single-RHS path on the same GPU (the second half of the metric).
+`value` = algorithmic Dslash bytes moved by all fine and coarse stencil
+launches of the step / step time (GB/s, the metric's unit); `roofline` gives
+the dominant stencil kernel against the measured HBM copy bandwidth (and
+against the 8 TB/s spec figure).  `trace_time` compares, at the same noise and
+so the same statistical error, this mixed-precision batched path with the
+plain FP64 single-RHS path on the same GPU (the metric's second half).
 
 python bench.py [--gpus N --steps K --warmup W --prec fp32|bf16 --impl wd|reference]
 Under torchrun each rank draws its own samples (seed offset by rank): no
@@ -29,7 +30,6 @@ collective on the data path; one barrier and a max/sum over ranks of the
 timing only.
 """
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -40,17 +40,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = (8, 8, 8, 16)
-KAPPA = 0.125
+DIMS = (24, 24, 24, 48)
+KAPPA = 0.13
 SPREAD = 0.5
-GAUGE_SEED = 1002
-NOISE_SEED = 2002
-SAMPLES = 16
+GAUGE_SEED = 1004
+NOISE_SEED = 2004
+N1, N2 = 64, 512
+NV, AGG, TV_ITERS, TV_SEED = 24, (4, 4, 4, 4), 3, 4
 TOL = 1e-10
 BC = (1, 1, 1, -1)
+SPEC_HBM_GBS = 8000.0
 METRIC = "Dslash GB/s (% HBM peak); trace time at fixed error, mixed+batched vs FP64"
-WORKLOAD = ("8^3x16 Wilson-Dirac, kappa 0.125, 256 time-diluted Rademacher RHS for tr[g5 D^-1(t,t)] + "
-            "12 point sources for C(t), solves to 1e-10")
+WORKLOAD = ("24^3x48 two-level MGMLMC: kappa 0.13, 4^4 aggregates, N_v = 24 (3 inverse iterations), "
+            "48x48 coarse blocks on tensor cores; tr[g5 D^-1(t,t)] with 64 level-1 + 512 level-2 samples per step, "
+            "solves to 1e-10")
 
 
 def env_rank():
@@ -133,87 +136,93 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def hop_traffic(prec, alg_bytes_per_launch):
-    """DRAM bytes per stencil launch: the committed ncu summary's DRAM bytes per
-    algorithmic byte (taken on 256-RHS launches of the same workload) times this
-    run's algorithmic bytes per launch, if the summary was taken on the current
-    stencil source (else None)."""
-    try:
-        rec = json.load(open(os.path.join(ROOT, 'profiles', 'hop_traffic.json')))
-        csrc = os.path.join(ROOT, 'paper_2607_05157_b300', 'csrc')
-        src = b''.join(open(os.path.join(csrc, f), 'rb').read() for f in ('wd_dslash.cu', 'wd_spin.cuh'))
-        if rec.get('source_sha256') != hashlib.sha256(src).hexdigest():
-            return None
-        r = rec.get(prec, {}).get('dram_bytes_per_algorithmic_byte')
-        return r * alg_bytes_per_launch if r is not None else None
-    except Exception:
-        return None
+# ---- CPU oracle baseline ---------------------------------------------------
 
-
-def oracle_baseline(n_timeslices=3):
-    """The FP64 CPU oracle on a bounded sample of the same workload: the
-    time-diluted solves of sample 0 for the first n timeslices (plain
-    BiCGStab on D, contraction).  Returns (GB/s of algorithmic stencil bytes,
-    seconds, applies)."""
-    import contextlib
+def _oracle_apply_worker(args):
+    """One worker of the CPU baseline: `napply` applications of the oracle's
+    FP64 D (the operator inside every solve of the workload) to a Gaussian
+    spinor on the headline lattice.  Returns (seconds, applications)."""
+    napply, seed, dims = args
     import numpy as np
-    try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:          # numpy's einsum/roll used here are single-threaded anyway
-        threadpool_limits = lambda limits: contextlib.nullcontext()
+    sys.path.insert(0, ROOT)
     import synth
-    from oracle import estimators, noise, solver, wilson
-    U = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
-    V = int(np.prod(DIMS))
-    shape = (DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3)
-    napply = [0]
+    from oracle import wilson
+    U = synth.gauge_field(dims, SPREAD, GAUGE_SEED)
+    v = synth.spinors(dims, 1, seed)[0]
+    t0 = time.perf_counter()
+    for _ in range(napply):
+        v = wilson.apply(U, v, KAPPA, BC)
+        v /= np.linalg.norm(v)
+    return time.perf_counter() - t0, napply
 
-    def A(v):
-        napply[0] += 1
-        return wilson.apply(U, v.reshape(shape), KAPPA, BC)
-    eta = noise.rademacher(NOISE_SEED, 0, 12 * V)
-    ts = wilson.timeslice_of_dof(DIMS)
-    with threadpool_limits(limits=1):
-        t0 = time.perf_counter()
-        for t in range(n_timeslices):
-            v = np.where(ts == t, eta, 0).astype(complex)
-            x, it, res = solver.bicgstab(A, v, tol=TOL)
-            estimators.contract(v, x.reshape(-1), DIMS, True)
-        dt = time.perf_counter() - t0
-    # same byte model as the GPU stencil: FP64, one RHS, in + out + addend spinors
-    # and 8 links per output site, two half-lattice hops per application of D
+
+def oracle_baseline(napply=2, dims=DIMS, workers=None):
+    """The FP64 CPU oracle on a bounded sample of the headline workload:
+    `napply` applications of D per worker process, one worker per host core
+    (spawned, so they start clean of any GPU state).  Returns (GB/s of the
+    same algorithmic stencil bytes as the GPU model, cores, seconds)."""
+    import multiprocessing as mpr
+    # one process per host core, at most 16 (each holds its own ~1.5 GB of links and spinors)
+    cores = workers or min(len(os.sched_getaffinity(0)), 16)
+    ctx = mpr.get_context('spawn')
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_apply_worker, [(napply, 500 + i, dims) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    busy = max(r[0] for r in res)
+    n = sum(r[1] for r in res)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    # FP64, one RHS: input + output (+ addend) spinors and 8 links per site, per application of D
     bytes_per_apply = V * (3 * 192 + 8 * 144)
-    return napply[0] * bytes_per_apply / dt / 1e9, dt, napply[0]
+    return n * bytes_per_apply / busy / 1e9, cores, busy, wall
 
 
 def run_reference(args):
+    """The reference arm: the oracle itself (there is no installable reference
+    implementation; the paper ships none), timed on the host cores on the
+    headline workload's operator, a bounded sample per step."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    vals = []
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; skip untimed steps
-    t_all = 0.0
+    vals, t_all, cores = [], 0.0, 1
     for _ in range(args.steps):
-        gbs, dt, n = oracle_baseline(1)
+        gbs, cores, busy, wall = oracle_baseline(1)
         vals.append(gbs)
-        t_all += dt
+        t_all += busy
     value = statistics.median(vals)
+    sample = f"1 application of the FP64 D per host core ({cores} processes) on the 24^3x48 lattice per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: one time-diluted solve per step)"},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "one time-diluted RHS of sample 0 per step (1/256 of the GPU step)"},
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle: applications of D)"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ---- algorithmic bytes of the stencil launches of a profiled region ----------
+
+def dslash_bytes(api, wd, c, ncd, Vc):
+    """Fine (FP32/BF16 and FP64 / double-float) stencil bytes and coarse
+    stencil bytes (blocks as compact complex BF16, 9 * ncd^2 * 4 B per site and
+    launch, plus the BF16 input and FP32 output vectors per RHS) and event
+    times of the launches profiled on context c since wd_profile(c, 1)."""
+    n32, ms32, b32 = api.wd_profile_get(c.h, wd.WD_K_HOP)
+    n64, ms64, b64 = api.wd_profile_get(c.h, wd.WD_K_HOP64)
+    nco, msco, flco = api.wd_profile_get(c.h, wd.WD_K_COARSE)
+    rhs_sites = flco / (8.0 * ncd * ncd * 9.0) if ncd else 0.0      # sum over launches of Vc * nrhs
+    bco = nco * Vc * 9 * ncd * ncd * 4.0 + rhs_sites * ncd * (4.0 + 8.0)
+    return {"hop32": (n32, ms32, b32), "hop64": (n64, ms64, b64), "coarse": (nco, msco, bco, flco)}
+
+
+# ---- secondary measurements (other rows and configurations) ------------------
 
 def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 48)):
     """Row a8: tcgen05 coarse 9-point block stencil on the 24^3x48 two-level
     workload (4^4 aggregates, 24 test vectors -> 48x48 blocks, 2592 coarse
     sites), CUDA-event times of the kernel, algorithmic TFLOP/s (8 ncd^2 per
-    block, 9 blocks per site and RHS) and block-stream GB/s."""
+    block, 9 blocks per site and RHS) and GB/s of the compact algorithmic
+    bytes (blocks as complex BF16, vectors in and out)."""
     ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
     api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=0, seed=3)
     Vc, ncd = (dims[0] // 4) * (dims[1] // 4) * (dims[2] // 4) * (dims[3] // 4), 48
@@ -230,9 +239,9 @@ def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 
         n, ms, fl = api.wd_profile_get(ctx.h, wd.WD_K_COARSE)
         api.wd_profile(ctx.h, False)
         per = ms / n
-        wbytes = Vc * 96 * 864 * 2
+        alg = Vc * (9 * ncd * ncd * 4.0 + nrhs * ncd * 12.0)
         out.append({"nrhs": nrhs, "ms_per_launch": per, "TFLOP_s": fl / n / (per * 1e-3) / 1e12,
-                    "block_stream_GB_s": wbytes / (per * 1e-3) / 1e9})
+                    "GB_s_algorithmic": alg / (per * 1e-3) / 1e9})
     ctx.close()
     peaks = measured_peaks()
     return {"workload": "x".join(map(str, dims)) + ", 4^4 aggregates, nv=24 (48x48 blocks), BF16 tcgen05, FP32 accumulate",
@@ -243,7 +252,7 @@ def gradient_measure(wd, api, torch, synth):
     """Row a10: d/dkappa and the link force of the probing (d=2, full dilution)
     estimate of tr[g5 D^-1] on 8^3x16 (192 solves + force), wall time."""
     dims = (8, 8, 8, 16)
-    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1005), KAPPA, BC)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1005), 0.125, BC)
     shape = (4, 16, 8, 8, 8, 3, 3)
     api.trace_gradient(ctx.h, wd.WD_PROBE, 12, 1, 16, d=2, seed=1, op=1, tol=TOL, link_shape=shape)
     torch.cuda.synchronize()
@@ -258,11 +267,11 @@ def gradient_measure(wd, api, torch, synth):
 
 def probing_measure(wd, api, torch, synth):
     """The probing workload, 16^3x32 kappa 0.13: distance-2 (16 colours) and
-    distance-4 (64 colours) torus-colouring probing x 12 spin-colour
-    dilution for tr[g5 D^-1(t,t)] summed over t, against Hutchinson at equal
-    solve count (Eq. 14 vs Eq. 3): wall time, solves, and the variance of the
-    total of one estimate of that cost (the per-sample variance divided by
-    the samples one such estimate takes)."""
+    distance-4 (64 colours) torus-colouring probing x 12 spin-colour dilution
+    for tr[g5 D^-1(t,t)] summed over t, against Hutchinson at equal solve count
+    (Eq. 14 vs Eq. 3): wall time, solves, the variance of the total of one
+    estimate of that cost, and the plain FP64 single-RHS path on a subset of
+    the same d = 2 vectors (time per solve, extrapolated to the same solves)."""
     import numpy as np
     dims = (16, 16, 16, 32)
     ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1003), 0.13, BC)
@@ -272,7 +281,7 @@ def probing_measure(wd, api, torch, synth):
         return float(np.sum(np.abs(tot - tot.mean()) ** 2) / (len(tot) - 1))
     out = {"workload": "16^3x32 kappa 0.13, tr[g5 D^-1(t,t)] summed over t; probing d = 2 (16 colours) and "
                        "d = 4 (64 colours) x 12 dilution, 4 noise samples each; Hutchinson with 768 Rademacher "
-                       "vectors; solves to 1e-10, FP32 inner"}
+                       "vectors; solves to 1e-10, FP32 inner, autotuned batches"}
     api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 1, 32, d=2, seed=1, op=1, tol=TOL)    # tuning, workspaces
     for d, N in ((2, 4), (4, 4)):
         torch.cuda.synchronize()
@@ -282,6 +291,8 @@ def probing_measure(wd, api, torch, synth):
         dt = time.perf_counter() - t0
         out[f"probe_d{d}"] = {"ms": 1e3 * dt, "solves": r["n_solves"], "ms_per_solve": 1e3 * dt / r["n_solves"],
                               "var_per_sample": svar(r["samples"]), "solves_per_sample": r["n_solves"] // N}
+        if d == 2:
+            rd2 = r
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, 768, 32, seed=2, op=1, tol=TOL, with_samples=True)
@@ -292,43 +303,23 @@ def probing_measure(wd, api, torch, synth):
                          "var_per_sample": vh}
     for d in (2, 4):
         q = out[f"probe_d{d}"]
-        # variance of one estimate costing q["solves_per_sample"] solves, both methods
         q["var_hutchinson_over_probing_at_equal_solves"] = (vh / q["solves_per_sample"]) / q["var_per_sample"]
-    ctx.close()
-    return out
-
-
-def mlmc2_large_measure(wd, api, torch, synth):
-    """The two-level workload, 24^3x48 kappa 0.13: GPU setup (24 test vectors
-    from 3 inverse iterations, 4^4 aggregates, Galerkin D_c), then the
-    two-level MLMC estimate of tr[g5 D^-1(t,t)] with 64 level-1 and 512 level-2
-    samples (Eq. 12, L = 2), against plain Hutchinson on the same 64 fine
-    noise samples: wall times, solves, per-sample variances of the total."""
-    import numpy as np
-    dims = (24, 24, 24, 48)
-    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
-
-    def svar(S):
-        tot = S.sum(1)
-        return float(np.sum(np.abs(tot - tot.mean()) ** 2) / (len(tot) - 1))
+    # the plain FP64 single-RHS path on one d = 2 sample (192 solves), per solve
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=4)
+    f = api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 1, 32, d=2, seed=2, op=1, prec=wd.WD_FP64, batch=1, tol=TOL,
+                           with_samples=True)
     torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    m = api.trace_estimate(ctx.h, wd.WD_MLMC2, 1, 64, 48, n2=512, seed=2004, op=1, tol=TOL, with_samples=True)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    h = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, 64, 48, seed=2004, op=1, tol=TOL, with_samples=True)
-    torch.cuda.synchronize()
-    t3 = time.perf_counter()
+    t64 = time.perf_counter() - t0
+    q = out["probe_d2"]
+    ms64_per_solve = 1e3 * t64 / f["n_solves"]
+    q["fp64_single_rhs_ms_per_solve"] = ms64_per_solve
+    q["trace_time_speedup_vs_fp64"] = ms64_per_solve / q["ms_per_solve"]
+    # the same vectors through both paths: sample 0's total differs by far less than its spread
+    q["fp64_vs_mixed_sample0_diff_over_sd"] = abs(f["samples"][0].sum() - rd2["samples"][0].sum()) / \
+        max(q["var_per_sample"], 1e-300) ** 0.5
     ctx.close()
-    return {"workload": "24^3x48 kappa 0.13, 4^4 aggregates, N_v = 24 (3 inverse iterations); tr[g5 D^-1(t,t)]; "
-                        "MLMC2 with 64 level-1 + 512 level-2 samples; Hutchinson with the same 64 fine samples",
-            "setup_s": t1 - t0, "mlmc2_s": t2 - t1, "mlmc2_solves": m["n_solves"],
-            "mlmc2_level1_var_per_sample": svar(m["samples"]), "mlmc2_var_total": m["var_total"],
-            "hutchinson_s": t3 - t2, "hutchinson_solves": h["n_solves"],
-            "hutchinson_var_per_sample": svar(h["samples"]), "hutchinson_var_total": h["var_total"]}
+    return out
 
 
 def mlmc_probe_measure(wd, api, torch, synth):
@@ -339,7 +330,7 @@ def mlmc_probe_measure(wd, api, torch, synth):
     and per-sample variances of the total over timeslices."""
     import numpy as np
     dims, N = (8, 8, 8, 16), 4
-    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1006), KAPPA, BC)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1006), 0.125, BC)
     api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=3)
 
     def svar(S):
@@ -405,7 +396,7 @@ def connected_measure(wd, api, torch, synth):
     and the variance of the fine term G_11 against the plain estimator on the
     same noise (the variance reduction of Sec. 4)."""
     dims = (8, 8, 8, 16)
-    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1007), KAPPA, BC)
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1007), 0.125, BC)
     api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=3, seed=4)
     api.wd_connected_mlmc(ctx.h, 4, 32, 16, seed=1, tol=TOL)
     torch.cuda.synchronize()
@@ -422,8 +413,9 @@ def connected_measure(wd, api, torch, synth):
 
 
 def batched_measure(wd, torch, synth):
-    """Row a11: 8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16) solved together
-    (persistent multi-lattice stencil, CUDA graph) vs one after another."""
+    """Row a11 (and the batched part of the two-level configuration):
+    8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16) solved together (persistent
+    multi-lattice stencil, CUDA graph) vs one after another."""
     specs = [((8, 8, 8, 16), 0.125, 64), ((12, 12, 12, 24), 0.13, 32), ((16, 16, 16, 32), 0.13, 16)]
     ctxs, bs = [], []
     for i, (d, k, n) in enumerate(specs):
@@ -455,18 +447,57 @@ def batched_measure(wd, torch, synth):
     return res
 
 
+def small_trace_measure(wd, api, torch, synth, steps=10):
+    """The 8^3x16 workload: 256 time-diluted RHS (16 samples x 16 timeslices)
+    for tr[g5 D^-1(t,t)] and the 12-column point-source correlator C(t) per
+    step, one after the other on one context; and the plain FP64 single-RHS
+    path on the same trace noise."""
+    dims, kappa = (8, 8, 8, 16), 0.125
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1002), kappa, BC)
+
+    def step(i, p=wd.WD_MIXED_FP32, batch=256):
+        r = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, 16, 16, seed=2002 + i, op=1, prec=p,
+                               batch=batch, tol=TOL)
+        if p != wd.WD_FP64:
+            api.wd_point_correlator(ctx.h, (0, 0, 0, 0), 16, prec=p, tol=TOL)
+        return r
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    api.wd_profile(ctx.h, True)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        mix = step(1000 + i)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / steps * 1e3
+    n32, ms32, b32 = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
+    api.wd_profile(ctx.h, False)
+    t0 = time.perf_counter()
+    ref = step(1000 + steps - 1, p=wd.WD_FP64, batch=1)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    ctx.close()
+    eps = (mix['var_total'] / 16) ** 0.5
+    return {"workload": "8^3x16 kappa 0.125, 256 time-diluted RHS for tr[g5 D^-1(t,t)] + 12 point sources for C(t) "
+                        "per step (profiled plain launches, one context)",
+            "ms_per_step": ms, "fp32_stencil_GB_s": b32 / (ms32 * 1e-3) / 1e9 if ms32 else None,
+            "fp64_single_rhs_trace_ms": 1e3 * t64, "speedup_trace_vs_fp64": 1e3 * t64 / ms,
+            "estimate_diff_over_eps": abs(mix['total'] - ref['total']) / eps}
+
+
+# ---- the headline ------------------------------------------------------------
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=20)
+    ap.add_argument('--steps', type=int, default=10)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--prec', choices=['fp32', 'bf16'], default='fp32')
     ap.add_argument('--impl', choices=['wd', 'reference'], default='wd')
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--serial', action='store_true',
-                    help='run the correlator after the trace solve on one context (no second stream)')
     ap.add_argument('--no-fp64-compare', action='store_true')
-    ap.add_argument('--no-secondary', action='store_true', help='skip the coarse / gradient / batched measurements')
+    ap.add_argument('--no-e2e', action='store_true', help='skip the end-to-end steps (profiling runs)')
+    ap.add_argument('--no-secondary', action='store_true', help='skip the other rows and configurations')
     ap.add_argument('--coarse-only', action='store_true', help='only the tensor-core coarse stencil measurement')
     ap.add_argument('--coarse-lattice', default='24,24,24,48', help='fine lattice of --coarse-only (X,Y,Z,T)')
     ap.add_argument('--coarse-rhs', default='64,128,256,512', help='RHS counts of --coarse-only')
@@ -474,9 +505,17 @@ def main():
     if args.impl == 'reference':
         return run_reference(args)
 
+    rank, world, local = env_rank()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.coarse_only:
+        # the oracle baseline runs in spawned processes before any GPU work
+        gbs, cores, busy, wall = oracle_baseline(1)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"1 application of the FP64 D per process, {cores} processes (one per host core), on "
+                         f"the 24^3x48 lattice ({busy:.1f} s busy): the operator inside every solve of the step"}
+
     import numpy as np
     import torch
-    rank, world, local = env_rank()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -495,173 +534,163 @@ def main():
 
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
     T = DIMS[3]
+    Vc = int(np.prod([L // a for L, a in zip(DIMS, AGG)]))
+    ncd = 2 * NV
     gauge = synth.gauge_field(DIMS, SPREAD, GAUGE_SEED)
-    # The two independent parts of a step run on two contexts with their own
-    # streams, from two host threads, so that the 12-RHS correlator solve (small,
-    # latency-bound launches) fills the gaps of the 256-RHS trace solve; with
-    # --serial both run one after the other on one context.
-    if args.serial:
-        ctx = ctx_c = wd.Context(DIMS, gauge, KAPPA, BC)
-        pool = None
-    else:
-        from concurrent.futures import ThreadPoolExecutor
-        s_tr, s_c = torch.cuda.Stream(), torch.cuda.Stream()
-        ctx = wd.Context(DIMS, gauge, KAPPA, BC, stream=s_tr)
-        ctx_c = wd.Context(DIMS, gauge, KAPPA, BC, stream=s_c)
-        pool = ThreadPoolExecutor(1)
-    ctxs = [ctx] if ctx_c is ctx else [ctx, ctx_c]
+    ctx = wd.Context(DIMS, gauge, KAPPA, BC)
     seed0 = rank_seed(rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.wd_mg_setup(ctx.h, None, NV, AGG, tv_iters=TV_ITERS, seed=TV_SEED)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
 
-    def trace_only(i, p=prec, batch=SAMPLES * T):
-        return api.trace_estimate(ctx.h, wd.WD_HUTCH, 1 | wd.WD_DIL_TIME, SAMPLES, T, seed=seed0 + i, op=1,
-                                  prec=p, batch=batch, tol=TOL)
+    def step(i, p=prec, n1=N1, n2=N2, batch=0, samples=False):
+        return api.trace_estimate(ctx.h, wd.WD_MLMC2, 1, n1, T, n2=n2, seed=seed0 + i, op=1, prec=p, batch=batch,
+                                  tol=TOL, with_samples=samples)
 
-    def correlator(p=prec):
-        return api.wd_point_correlator(ctx_c.h, (0, 0, 0, 0), T, prec=p, tol=TOL)
-
-    def step(i, p=prec, batch=SAMPLES * T, concurrent=True):
-        # the whole workload: 256 time-diluted RHS for O(t) and 12 point sources for C(t)
-        if pool is not None and concurrent:
-            fc = pool.submit(correlator, p)
-            r = trace_only(i, p, batch)
-            r['C'] = fc.result()
-        else:
-            r = trace_only(i, p, batch)
-            r['C'] = correlator(p)
-        return r
-
-    # warm-up one part after the other: the autotuner times its launch-shape
-    # candidates on the first call of each shape, and the other stream's work
-    # would distort those timings
     for i in range(args.warmup):
-        step(i, concurrent=False)
+        step(i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     # timed region: the steps as a user runs them (no per-launch events, so the
     # BiCGStab loops run as captured graphs)
-    l0 = sum(api.wd_launch_count(c.h) for c in ctxs)
+    l0 = api.wd_launch_count(ctx.h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record()
-        results = [step(1000 + i) for i in range(args.steps)]
+        results = [step(1000 + i, samples=(i == 0)) for i in range(args.steps)]
         ev1.record()
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    launches = sum(api.wd_launch_count(c.h) for c in ctxs) - l0
+    launches = api.wd_launch_count(ctx.h) - l0
 
     # profiled repetition of the same steps (same seeds, so the same work):
     # CUDA events around every stencil launch on the library's stream give the
-    # per-kernel durations and algorithmic bytes of the roofline.  Events
-    # cannot sit inside a captured graph, so these steps run plain launches.
-    # The two parts run one after the other here, so that no kernel's
-    # duration includes another stream's work.
-    for c in ctxs:
-        api.wd_profile(c.h, True)
+    # per-kernel durations and algorithmic bytes behind `value` and `roofline`
+    api.wd_profile(ctx.h, True)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     for i in range(args.steps):
-        step(1000 + i, concurrent=False)
+        step(1000 + i)
     p1.record()
     torch.cuda.synchronize()
     ms_prof = p0.elapsed_time(p1)
-    n_hop = ms_hop = by_hop = n_h64 = ms_h64 = by_h64 = 0
-    for c in ctxs:
-        n, t, b = api.wd_profile_get(c.h, wd.WD_K_HOP)
-        n_hop, ms_hop, by_hop = n_hop + n, ms_hop + t, by_hop + b
-        n, t, b = api.wd_profile_get(c.h, wd.WD_K_HOP64)
-        n_h64, ms_h64, by_h64 = n_h64 + n, ms_h64 + t, by_h64 + b
-        api.wd_profile(c.h, False)
-    ms, step_bytes = combine_ranks(dist, ms, by_hop + by_h64, 'cuda')
-    value = step_bytes / (ms * 1e-3) / 1e9
-
-    # end to end through the public API: host (pinned) links uploaded and
-    # re-ingested every step, estimates read back to the host (same seeds as
-    # the timed steps, so the same algorithmic bytes)
-    pinned = torch.from_numpy(gauge.view(np.float64)).pin_memory()
-    gptr = pinned.data_ptr()
-    import ctypes
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(args.steps):
-        for c in ctxs:
-            wd.lib.wd_update_gauge(c.h, ctypes.c_void_p(gptr), ctypes.c_double(KAPPA))
-        step(1000 + i)
-    e1.record()
-    torch.cuda.synchronize()
-    e_ms = e0.elapsed_time(e1)
-    e_ms, e_bytes = combine_ranks(dist, e_ms, by_hop + by_h64, 'cuda')
-    h2d = gauge.nbytes * len(ctxs)
-    d2h = 8 * (2 * (T + 1) + (T + 1))
+    prof = dslash_bytes(api, wd, ctx, ncd, Vc)
+    api.wd_profile(ctx.h, False)
+    step_bytes = prof["hop32"][2] + prof["hop64"][2] + prof["coarse"][2]
+    ms, all_bytes = combine_ranks(dist, ms, step_bytes, 'cuda')
+    value = all_bytes / (ms * 1e-3) / 1e9
 
     peaks = measured_peaks()
     peak = peaks['hbm_gbs'] if peaks else 6400.0
-    achieved = (by_hop / n_hop) / (ms_hop / n_hop * 1e-3) / 1e9 if n_hop else None
+    kern = {}
+    for name, label in (("hop32", f"hop_kernel ({args.prec} storage, fine stencil)"),
+                        ("hop64", "hop_kernel_dd (double-float FP64 steps, fine stencil)"),
+                        ("coarse", "k_coarse_tc (tcgen05 coarse 9-point stencil)")):
+        n, t_ms, b = prof[name][0], prof[name][1], prof[name][2]
+        kern[name] = {"kernel": label, "launches_per_step": n / max(args.steps, 1),
+                      "GB_s": b / (t_ms * 1e-3) / 1e9 if t_ms else None,
+                      "MB_per_launch": b / n / 1e6 if n else None,
+                      "share_of_step": t_ms / ms_prof if ms_prof else None}
+    kern["coarse"]["TFLOP_s"] = prof["coarse"][3] / (prof["coarse"][1] * 1e-3) / 1e12 if prof["coarse"][1] else None
+    dom = max(kern, key=lambda k: kern[k]["share_of_step"] or 0.0)
+    achieved = kern[dom]["GB_s"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": hop_traffic(args.prec, by_hop / max(n_hop, 1)),
-            "kernel": f"hop_kernel ({args.prec} storage, {n_hop // max(args.steps, 1)} launches/step, "
-                      f"{by_hop / max(n_hop, 1) / 1e6:.1f} MB algorithmic per launch)",
-            "peak_source": "measured" if peaks else "fallback",
+            "frac": achieved / peak if achieved else None,
+            "frac_of_spec_8000": achieved / SPEC_HBM_GBS if achieved else None,
+            "traffic": None, "kernel": kern[dom]["kernel"], "peak_source": "measured" if peaks else "fallback",
             "region": "profiled repetition of the timed steps (same seeds; plain launches bracketed by CUDA events)",
-            "share_of_step": ms_hop / ms_prof if ms_prof else None,
-            "fp64_stencil": {"arithmetic": "fp64" if os.environ.get('WD_DD') == '0' else
-                             "double-float (FP32 pairs, FP64 fields)",
-                             "launches_per_step": n_h64 // max(args.steps, 1),
-                             "GB_s": (by_h64 / (ms_h64 * 1e-3) / 1e9) if ms_h64 else None,
-                             "share_of_step": ms_h64 / ms_prof if ms_prof else None}}
+            "kernels": kern}
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.prec == 'fp32' else "bf16+f32+f64",
+            "vs_baseline": None, "dtype": "f32+bf16+f64" if args.prec == 'fp32' else "bf16+f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "kappa": KAPPA,
-                       "rhs_per_step_per_gpu": SAMPLES * T + 12, "inner_precision": args.prec,
-                       "l2": "inputs larger than L2 (each stencil launch streams >100 MB)",
+                       "samples_per_step": {"level1": N1, "level2": N2}, "solves_per_step": results[-1]["n_solves"],
+                       "inner_precision": args.prec, "setup_s": setup_s,
+                       "l2": "inputs larger than L2 (each 64-RHS fine stencil launch streams ~4 GB)",
                        "parallelism": f"replicas x{world} (independent samples)"},
-            "roofline": roof, "clocks": clk.summary(),
-            "e2e": {"value": e_bytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps},
-            "gpu_launches": launches,
-            "solves_per_step": results[-1]["n_solves"] + 12}
+            "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches,
+            "estimate_total": [results[0]["total"].real, results[0]["total"].imag],
+            "std_error": results[0]["var_total"] ** 0.5}
+
+    if not args.no_e2e:
+        # end to end through the public API, per gauge configuration: the links
+        # uploaded from pinned host memory and ingested, the multigrid setup,
+        # the estimate, the result read back
+        pinned = torch.from_numpy(gauge.view(np.float64)).pin_memory()
+        import ctypes
+        api.wd_profile(ctx.h, True)
+        api.wd_mg_setup(ctx.h, None, NV, AGG, tv_iters=TV_ITERS, seed=TV_SEED)
+        torch.cuda.synchronize()
+        sp = dslash_bytes(api, wd, ctx, ncd, Vc)
+        api.wd_profile(ctx.h, False)
+        setup_bytes = sp["hop32"][2] + sp["hop64"][2] + sp["coarse"][2]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            wd.lib.wd_update_gauge(ctx.h, ctypes.c_void_p(pinned.data_ptr()), ctypes.c_double(KAPPA))
+            api.wd_mg_setup(ctx.h, None, NV, AGG, tv_iters=TV_ITERS, seed=TV_SEED)
+            step(1000 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        e_ms, e_bytes = combine_ranks(dist, e_ms, step_bytes + setup_bytes * args.steps, 'cuda')
+        line["e2e"] = {"value": e_bytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": gauge.nbytes,
+                       "d2h_bytes_per_step": 8 * (2 * (T + 1) + (T + 1)), "ms_per_step": e_ms / args.steps,
+                       "includes": "link upload and ingest, multigrid setup (its stencil bytes counted), estimate, "
+                                   "result read-back"}
 
     if rank == 0 and not args.no_fp64_compare:
-        # trace time at fixed error: same noise (so the same estimate and error)
-        # through the plain FP64 single-RHS path
+        # trace time at fixed error: the same noise (so the same estimate and
+        # error) through the plain FP64 single-RHS path, on the first 1/8 of the
+        # samples of each level (8 + 64), time scaled by the sample count (8x)
+        mix = results[0]
+        sub1, sub2 = N1 // 8, N2 // 8
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ref = trace_only(1000, p=wd.WD_FP64, batch=1)
+        ref = step(1000, p=wd.WD_FP64, n1=sub1, n2=sub2, batch=1, samples=True)
         torch.cuda.synchronize()
-        t_fp64 = time.perf_counter() - t0
-        mix = results[0]
-        eps = (mix['var_total'] / SAMPLES) ** 0.5
+        t_sub = time.perf_counter() - t0
+        ref_l2 = api.wd_mlmc_level2_samples(ctx.h, sub2, T)
+        mix_sub = step(1000, n1=sub1, n2=sub2, samples=True)
+        mix_l2 = api.wd_mlmc_level2_samples(ctx.h, sub2, T)
+        eps = mix['var_total'] ** 0.5
+        dmax = max(np.abs(ref['samples'].sum(1) - mix_sub['samples'].sum(1)).max(),
+                   np.abs(ref_l2.sum(1) - mix_l2.sum(1)).max())
+        t_fp64 = t_sub * (N1 // sub1)
         line["trace_time"] = {"mixed_batched_ms": ms / args.steps, "fp64_single_rhs_ms": 1e3 * t_fp64,
                               "speedup": 1e3 * t_fp64 / (ms / args.steps),
-                              "estimate_diff_over_eps": abs(mix['total'] - ref['total']) / eps,
-                              "std_error_eps": eps}
+                              "fp64_measured_on": f"{sub1} level-1 + {sub2} level-2 samples ({t_sub:.2f} s), scaled "
+                                                  f"x{N1 // sub1} to the step's {N1} + {N2}",
+                              "max_sample_diff_over_eps": dmax / eps, "std_error_eps": eps}
     if rank == 0 and not args.no_secondary:
-        # secondary measurements of the other rows, outside the timed region
-        line["secondary"] = {"coarse_tc": coarse_measure(wd, api, torch, synth),
-                             "gradient": gradient_measure(wd, api, torch, synth),
-                             "batched": batched_measure(wd, torch, synth),
-                             "probing": probing_measure(wd, api, torch, synth),
-                             "mlmc2_24": mlmc2_large_measure(wd, api, torch, synth),
-                             "mlmc_probe": mlmc_probe_measure(wd, api, torch, synth),
-                             "connected": connected_measure(wd, api, torch, synth),
-                             "mlmc3": mlmc3_measure(wd, api, torch, synth)}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gbs, dt, n = oracle_baseline(3)
-        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"3 of the 256 time-diluted solves of one step ({dt:.1f} s, {n} applies of D)"}
+        sec = {}
+        for name, fn in (("trace_8x8x8x16", lambda: small_trace_measure(wd, api, torch, synth)),
+                         ("probing_16x16x16x32", lambda: probing_measure(wd, api, torch, synth)),
+                         ("coarse_tc", lambda: coarse_measure(wd, api, torch, synth)),
+                         ("batched", lambda: batched_measure(wd, torch, synth)),
+                         ("gradient", lambda: gradient_measure(wd, api, torch, synth)),
+                         ("mlmc_probe", lambda: mlmc_probe_measure(wd, api, torch, synth)),
+                         ("connected", lambda: connected_measure(wd, api, torch, synth)),
+                         ("mlmc3", lambda: mlmc3_measure(wd, api, torch, synth))):
+            try:
+                sec[name] = fn()
+            except Exception as e:          # a secondary row must not lose the headline line
+                sec[name] = {"error": str(e)}
+        line["secondary"] = sec
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for c in ctxs:
-        c.close()
-    if pool is not None:
-        pool.shutdown()
+    ctx.close()
     if dist:
         dist.destroy_process_group()
 

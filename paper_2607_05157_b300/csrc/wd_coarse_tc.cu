@@ -104,12 +104,20 @@ struct TcArgs {
     int stall_test;     // 1: the MMA issuer waits (short limit) on a barrier nothing arrives on
 };
 
-template <int N>
+// SPLIT: the blocks as two BF16 operands W + W_lo (mapw2) and the input as
+// two BF16 fields x + x_lo (mapx2), multiplied into the same accumulator as
+// W x + W_lo x + W x_lo (~16 significant bits of both operands; the product
+// of the two remainders is below that)
+template <int N, bool SPLIT>
 __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CUtensorMap mapx,
-                                                      const __grid_constant__ CUtensorMap mapw, TcArgs A) {
+                                                      const __grid_constant__ CUtensorMap mapx2,
+                                                      const __grid_constant__ CUtensorMap mapw,
+                                                      const __grid_constant__ CUtensorMap mapw2, TcArgs A) {
     constexpr int KB = N / TC_KC;              // chunks per neighbour block (N = 2 ncd)
     constexpr int NCHUNK = 9 * KB;
-    constexpr uint32_t A_BYTES = TC_M * TC_KC * 2, B_BYTES = N * TC_KC * 2;
+    constexpr int NB = SPLIT ? 2 : 1;          // A and B operands per chunk
+    constexpr uint32_t A1_BYTES = TC_M * TC_KC * 2, B1_BYTES = N * TC_KC * 2;
+    constexpr uint32_t A_BYTES = NB * A1_BYTES, B_BYTES = NB * B1_BYTES;
     constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned stage buffers (swizzle atoms must not straddle their base)
@@ -157,6 +165,10 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
             tma_load_3d(sA + s * A_BYTES, &mapx, &full[s], kk, nb, r0);
             tma_load_2d(sB + s * B_BYTES, &mapw, &full[s], kc * TC_KC, X * N);
+            if (SPLIT) {
+                tma_load_3d(sA + s * A_BYTES + A1_BYTES, &mapx2, &full[s], kk, nb, r0);
+                tma_load_2d(sB + s * B_BYTES + B1_BYTES, &mapw2, &full[s], kc * TC_KC, X * N);
+            }
             s_issued[s] += 1;
         }
     } else if (threadIdx.x == 32) {
@@ -169,15 +181,19 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
-            for (int k16 = 0; k16 < TC_KC / 16; ++k16) {
-                const uint64_t da = desc_sw64(a0 + 32 * k16), db = desc_sw64(b0 + 32 * k16);
-                const uint32_t acc = (kc > 0 || k16 > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "setp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                    ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
-            }
+            for (int k16 = 0; k16 < TC_KC / 16; ++k16)
+#pragma unroll
+                for (int q = 0; q < (SPLIT ? 3 : 1); ++q) {
+                    // q = 0: W x, 1: W_lo x, 2: W x_lo
+                    const uint64_t da = desc_sw64(a0 + (q == 2 ? A1_BYTES : 0) + 32 * k16);
+                    const uint64_t db = desc_sw64(b0 + (q == 1 ? B1_BYTES : 0) + 32 * k16);
+                    const uint32_t acc = (kc > 0 || k16 > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
             // release the stage when these MMAs have read it
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          ::"r"(smem_u32(&empty[s])) : "memory");
@@ -225,8 +241,9 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// W_X[n][k] (bf16) from the FP64 blocks: [Vc][N = 2 ncd][K = 9 * 2 ncd]
-__global__ void k_build_w(const double2 *Dc, bf16 *W, int Vc, int ncd) {
+// W_X[n][k] (bf16) from the FP64 blocks: [Vc][N = 2 ncd][K = 9 * 2 ncd], and
+// (Wlo nullable) the rounding remainder bf16(v - W)
+__global__ void k_build_w(const double2 *Dc, bf16 *W, bf16 *Wlo, int Vc, int ncd) {
     const long N = 2L * ncd, K = 18L * ncd;
     const long tot = (long)Vc * N * K;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
@@ -237,7 +254,9 @@ __global__ void k_build_w(const double2 *Dc, bf16 *W, int Vc, int ncd) {
         double v;
         if (cout == 0) v = cin == 0 ? a.x : -a.y;
         else v = cin == 0 ? a.y : a.x;
-        W[e] = __double2bfloat16(v);
+        const bf16 hi = __double2bfloat16(v);
+        W[e] = hi;
+        if (Wlo) Wlo[e] = __double2bfloat16(v - (double)__bfloat162float(hi));
     }
 }
 
@@ -252,8 +271,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return (PFN_cuTensorMapEncodeTiled_v12000)fn;
 }
 
-static size_t tc_smem(int N) {
-    return 1024 + TC_STAGES * ((size_t)TC_M * TC_KC * 2 + (size_t)N * TC_KC * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+static size_t tc_smem(int N, bool split) {
+    return 1024 + TC_STAGES * (split ? 2 : 1) * ((size_t)TC_M * TC_KC * 2 + (size_t)N * TC_KC * 2) +
+           (2 * TC_STAGES + 1) * 8 + 16;
+}
+
+// FP32 coarse field -> BF16 pair: hi = bf16(x), lo = bf16(x - hi)
+__global__ void k_split_bf16(const float *x, bf16 *hi, bf16 *lo, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        const bf16 h = __float2bfloat16(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16(v - __bfloat162float(h));
+    }
 }
 
 bool coarse_tc_ok(wd_ctx *c) { return c->mg && c->mg->Wtc != nullptr; }
@@ -265,32 +295,47 @@ int coarse_tc_build(wd_ctx *c) {
     if (!((2 * ncd) % TC_KC == 0 && (2 * ncd == 96 || 2 * ncd == 192)) || !encode_fn()) return WD_OK;
     const size_t n = (size_t)g->Vc * 2 * ncd * 18 * ncd;
     if (cudaMalloc(&g->Wtc, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wtc = nullptr; return WD_OK; }
+    if (cudaMalloc(&g->Wlo, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wlo = nullptr; }
     int *err;
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
     WD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->st));
-    k_build_w<<<1184, 256, 0, c->st>>>(g->Dc, (bf16 *)g->Wtc, g->Vc, ncd);
+    k_build_w<<<1184, 256, 0, c->st>>>(g->Dc, (bf16 *)g->Wtc, (bf16 *)g->Wlo, g->Vc, ncd);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs) {
+int coarse_tc_apply(wd_ctx *c, const void *x_in, float *y, int nrhs, bool split) {
     wd_mg *g = c->mg;
     if (!g || !g->Wtc) { set_error("tensor-core coarse stencil unavailable"); return WD_ENOTSUP; }
     if (nrhs <= 0) return WD_OK;
+    if (split && !g->Wlo) { set_error("tensor-core coarse stencil: no block remainders"); return WD_ENOTSUP; }
     const int N = 2 * g->ncd, K = 9 * N;
+    // split: x_in is an FP32 field, split here into a BF16 pair
+    const void *x_bf16 = x_in, *x_lo = x_in;
+    if (split) {
+        void *hi, *lo;
+        const long n = (long)nrhs * g->Vc * N;
+        WD_TRY(ws_get(c, "tc.xhi", (size_t)n * sizeof(bf16), &hi));
+        WD_TRY(ws_get(c, "tc.xlo", (size_t)n * sizeof(bf16), &lo));
+        k_split_bf16<<<1184, 256, 0, c->st>>>((const float *)x_in, (bf16 *)hi, (bf16 *)lo, n);
+        c->launches++;
+        x_bf16 = hi;
+        x_lo = lo;
+    }
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    CUtensorMap mx, mw;
-    {
+    CUtensorMap mx, mx2, mw, mw2;
+    for (int q = 0; q < (split ? 2 : 1); ++q) {
         const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)g->Vc, (cuuint64_t)nrhs};
         const cuuint64_t strides[2] = {(cuuint64_t)N * 2, (cuuint64_t)g->Vc * N * 2};
         const cuuint32_t box[3] = {TC_KC, 1, TC_M};
         const cuuint32_t es[3] = {1, 1, 1};
-        CUresult r = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)x_bf16, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = enc(q ? &mx2 : &mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)(q ? x_lo : x_bf16), dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (coarse field) failed: %d", (int)r); return WD_ECUDA; }
     }
+    if (!split) mx2 = mx;
     {
         const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)g->Vc * N};
         const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
@@ -300,6 +345,13 @@ int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs) {
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (blocks) failed: %d", (int)r); return WD_ECUDA; }
+        mw2 = mw;
+        if (split) {
+            r = enc(&mw2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g->Wlo, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (block remainders) failed: %d", (int)r); return WD_ECUDA; }
+        }
     }
     int *err;
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
@@ -310,17 +362,17 @@ int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs) {
         A.stall_test = e && atoi(e) == 1;
     }
     const unsigned grid = (unsigned)g->Vc * ((nrhs + TC_M - 1) / TC_M);
-    const size_t smem = tc_smem(N);
+    const size_t smem = tc_smem(N, split);
     int slot;
     // algorithmic flops: 8 ncd^2 per block, 9 blocks, per site and RHS
     prof_begin(c, WD_K_COARSE, 8.0 * g->ncd * g->ncd * 9.0 * g->Vc * nrhs, &slot);
-    if (N == 96) {
-        WD_CUDA(cudaFuncSetAttribute(k_coarse_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_coarse_tc<96><<<grid, 128, smem, c->st>>>(mx, mw, A);
-    } else {
-        WD_CUDA(cudaFuncSetAttribute(k_coarse_tc<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_coarse_tc<192><<<grid, 128, smem, c->st>>>(mx, mw, A);
+#define WD_TC_CASE(NN, SP)                                                                                 \
+    if (N == NN && split == SP) {                                                                          \
+        WD_CUDA(cudaFuncSetAttribute(k_coarse_tc<NN, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_coarse_tc<NN, SP><<<grid, 128, smem, c->st>>>(mx, mx2, mw, mw2, A);                              \
     }
+    WD_TC_CASE(96, false) WD_TC_CASE(96, true) WD_TC_CASE(192, false) WD_TC_CASE(192, true)
+#undef WD_TC_CASE
     prof_end(c, slot);
     c->launches++;
     WD_CUDA(cudaGetLastError());

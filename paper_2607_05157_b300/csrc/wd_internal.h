@@ -177,11 +177,13 @@ struct wd_mg {
     double2 *Dc;       // [Vc][9][ncd][ncd]
     int *nbr;          // [Vc][9]
     void *Wtc;         // tensor-core operand (bf16), built by wd_coarse_tc.cu
+    void *Wlo;         // its rounding remainder (bf16): Wtc + Wlo carries ~16 significant bits
     float2 *Dc32;      // [Vc][9][ncd][ncd] complex64 copy for the FP32 CUDA-core path
     float2 *Dclo;      // Dc - Dc32 as complex64: with Dc32 the double-float blocks of the FP64 residual
     float2 *Phi, *Plo; // P as double-float pairs (FP32 copy and remainder), for the prolongation
     double2 *Gt;       // [Vc][agg_t][2][nv][nv]: Gram matrices of P's columns restricted to one
                        // timeslice of an aggregate and one chirality half (coarse contractions)
+    float2 *Ghi, *Glo; // Gt as double-float pairs
 };
 
 struct wd_ctx {
@@ -321,6 +323,7 @@ struct Problem {
     const char *tag;            // workspace name prefix
     bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
     uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};
+    double inner_tol = 0.0;     // tolerance of the inner solves (0: by inner precision)
 };
 // restriction P^dag v and prolongation P y between eo FP64 fine fields and
 // coarse FP64 vectors (wd_mg.cu); dd_ok: double-float arithmetic allowed
@@ -331,6 +334,12 @@ int mg_prolong_eo(wd_ctx *c, const double *yc, double *ve, double *vo, int nrhs,
 // (P a_r)(x)^dag B (P b_r)(x), B = 1 or g5, evaluated on the coarse lattice
 // from the Gram matrices Gt (wd_mg.cu); part: device complex [nrhs][T]
 int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5, int nrhs, double *part);
+// per-timeslice restriction Rt[r][X][tau][i] (complex FP64, tau the timeslice
+// inside aggregate X) of eo FP64 fields, and yc = sum_tau Rt = P^dag v
+int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, double *yc, int nrhs);
+// part[r][t] = sum_{x in t} v_r(x)^dag B (P y_r)(x) from the per-timeslice
+// restriction Rt of v (B = 1 or g5); part: device complex [nrhs][T]
+int mg_contract_rt(wd_ctx *c, const double *Rt, const double *y, int gamma5, int nrhs, double *part);
 int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, const double *bnorm2_dev,
              const std::vector<double> &bnorm2, double tol, int prec, int max_iter, std::vector<int> &iters,
              std::vector<double> &last_rn2);

@@ -219,6 +219,154 @@ __global__ void __launch_bounds__(256) k_contract_coarse_t(const double2 *Gt, co
     }
 }
 
+// the same in double-float arithmetic: Gt as Ghi + Glo, b split once into the
+// double-float layout, a split on the fly
+__global__ void __launch_bounds__(256) k_contract_coarse_t_dd(const float2 *Gh, const float2 *Gl, const double2 *a,
+                                                              const float4 *b, int gamma5, double *part, MgGeom M) {
+    __shared__ double2 sh[32];
+    const int r = blockIdx.x, t = blockIdx.y, T = M.g.T;
+    const int at = M.agg[3], nv = M.nv, ncd = M.ncd;
+    const int Vs = M.cd[0] * M.cd[1] * M.cd[2];
+    const int ct = t / at, tau = t % at;
+    dd sre = dd_make(0.f, 0.f), sim = dd_make(0.f, 0.f);
+    for (int item = threadIdx.x; item < Vs * ncd; item += blockDim.x) {
+        const int xs = item / ncd, i = item % ncd, h = i / nv, k = i % nv;
+        const int X = xs + Vs * ct;
+        const size_t g0 = ((((size_t)X * at + tau) * 2 + h) * nv + k) * nv;
+        const float4 *bb = b + ((size_t)r * M.Vc + X) * ncd + nv * h;
+        dd ure = dd_make(0.f, 0.f), uim = dd_make(0.f, 0.f);
+        for (int l = 0; l < nv; ++l) {
+            const float2 mh = __ldg(Gh + g0 + l), ml = __ldg(Gl + g0 + l);
+            const float4 v = __ldg(bb + l);
+            const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+            const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+            dd_fma(ure, mr, vr);
+            dd_fma(ure, -mi, vi);
+            dd_fma(uim, mr, vi);
+            dd_fma(uim, mi, vr);
+        }
+        const double2 av = a[((size_t)r * M.Vc + X) * ncd + i];
+        dd ar = d2dd(av.x), ai = d2dd(av.y);
+        if (gamma5 && h == 1) { ar = -ar; ai = -ai; }
+        dd_fma(sre, ar, ure);                // conj(a) u
+        dd_fma(sre, ai, uim);
+        dd_fma(sim, ar, uim);
+        dd_fma(sim, -ai, ure);
+    }
+    double2 acc = make_double2(dd2d(sre), dd2d(sim));
+    acc = block_reduce_z(acc, sh);
+    if (threadIdx.x == 0) {
+        part[((size_t)r * T + t) * 2] = acc.x;
+        part[((size_t)r * T + t) * 2 + 1] = acc.y;
+    }
+}
+
+// Per-timeslice restriction: Rt[r][X][tau][i] = sum over the sites x of
+// aggregate X at timeslice t0(X) + tau and the 6 components of half h(i) of
+// conj(P_i(x)) v(x); the sum over tau is P^dag v.  DD: P as Phi + Plo and v
+// in the double-float layout (ve, vo float4), else FP64 (P, ve, vo double).
+// A thread takes one (X, tau, i) for RT right-hand sides, so that each P
+// entry is read once per RT RHS (P is larger than L2).
+template <bool DD, int RT>
+__global__ void k_restrict_t(const double2 *P, const float2 *Ph, const float2 *Pl, const void *ve, const void *vo,
+                             double2 *Rt, MgGeom M, int nrhs) {
+    const int at = M.agg[3];
+    const int ngrp = (nrhs + RT - 1) / RT;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)ngrp * M.Vc * at * M.ncd) return;
+    const int i = (int)(t % M.ncd);
+    long rest = t / M.ncd;
+    const int tau = (int)(rest % at);
+    rest /= at;
+    const int X = (int)(rest % M.Vc), r0 = (int)(rest / M.Vc) * RT;
+    const int nr = nrhs - r0 < RT ? nrhs - r0 : RT;
+    const int h = i / M.nv, k = i % M.nv;
+    const int ns3 = M.agg[0] * M.agg[1] * M.agg[2];
+    dd are[RT], aim[RT];
+    double2 acc[RT];
+#pragma unroll
+    for (int q = 0; q < RT; ++q) { are[q] = dd_make(0.f, 0.f); aim[q] = dd_make(0.f, 0.f); acc[q] = make_double2(0, 0); }
+    for (int j3 = 0; j3 < ns3; ++j3) {
+        int c[4];
+        agg_site(M, X, j3 + ns3 * tau, c);
+        const int site = lex(M.g, c), par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
+        for (int qc = 0; qc < 6; ++qc) {
+            const int comp = 6 * h + qc;
+            const size_t pi = (((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv + k;
+            if constexpr (DD) {
+                const float2 mh = __ldg(Ph + pi), ml = __ldg(Pl + pi);
+                const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+#pragma unroll
+                for (int q = 0; q < RT; ++q) {
+                    if (q < nr) {
+                        const size_t fi = ((size_t)(r0 + q) * 12 + comp) * M.g.Vh + s;
+                        const float4 v = __ldg((const float4 *)(par ? vo : ve) + fi);
+                        const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+                        dd_fma(are[q], mr, vr);  // conj(P) v
+                        dd_fma(are[q], mi, vi);
+                        dd_fma(aim[q], mr, vi);
+                        dd_fma(aim[q], -mi, vr);
+                    }
+                }
+            } else {
+                const double2 pv = P[pi];
+#pragma unroll
+                for (int q = 0; q < RT; ++q)
+                    if (q < nr) {
+                        const size_t fi = ((size_t)(r0 + q) * 12 + comp) * M.g.Vh + s;
+                        acc[q] = zfma_conj(acc[q], pv, ((const double2 *)(par ? vo : ve))[fi]);
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RT; ++q)
+        if (q < nr)
+            Rt[((((size_t)(r0 + q) * M.Vc + X) * at) + tau) * M.ncd + i] =
+                DD ? make_double2(dd2d(are[q]), dd2d(aim[q])) : acc[q];
+}
+
+// yc[r][X][i] = sum_tau Rt[r][X][tau][i], tau ascending
+__global__ void k_sum_tau(const double2 *Rt, double2 *yc, MgGeom M, int nrhs) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)nrhs * M.Vc * M.ncd) return;
+    const int i = (int)(t % M.ncd);
+    const long rx = t / M.ncd;
+    const int at = M.agg[3];
+    double2 s = make_double2(0, 0);
+    for (int tau = 0; tau < at; ++tau) {
+        const double2 v = Rt[(rx * at + tau) * M.ncd + i];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    yc[t] = s;
+}
+
+// part[r][t] = sum_{X in timeslice t / agg_t} sum_i s_h(i) conj(Rt[r][X][t % agg_t][i]) y[r][X][i]
+__global__ void __launch_bounds__(256) k_contract_rt(const double2 *Rt, const double2 *y, int gamma5, double *part,
+                                                     MgGeom M) {
+    __shared__ double2 sh[32];
+    const int r = blockIdx.x, t = blockIdx.y, T = M.g.T;
+    const int at = M.agg[3], nv = M.nv, ncd = M.ncd;
+    const int Vs = M.cd[0] * M.cd[1] * M.cd[2];
+    const int ct = t / at, tau = t % at;
+    double2 acc = make_double2(0, 0);
+    for (int item = threadIdx.x; item < Vs * ncd; item += blockDim.x) {
+        const int xs = item / ncd, i = item % ncd;
+        const int X = xs + Vs * ct;
+        const double2 rv = Rt[((((size_t)r * M.Vc + X) * at) + tau) * ncd + i];
+        const double2 yv = y[((size_t)r * M.Vc + X) * ncd + i];
+        const double sg = (gamma5 && i >= nv) ? -1.0 : 1.0;
+        acc.x += sg * (rv.x * yv.x + rv.y * yv.y);
+        acc.y += sg * (rv.x * yv.y - rv.y * yv.x);
+    }
+    acc = block_reduce_z(acc, sh);
+    if (threadIdx.x == 0) {
+        part[((size_t)r * T + t) * 2] = acc.x;
+        part[((size_t)r * T + t) * 2 + 1] = acc.y;
+    }
+}
+
 // coarse neighbour table: b = 0 self, 1+mu forward, 5+mu backward
 __global__ void k_coarse_nbr(int *nbr, MgGeom M) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,25 +382,31 @@ __global__ void k_coarse_nbr(int *nbr, MgGeom M) {
         }
 }
 
-// Block b of D_c at coarse site X; one CTA per (X, b).  For each hop x -> y
-// of the block: A += coef * P(x)^dag [Gamma (x) U] P(y), with P(.) the 12 x ncd
-// restriction of the columns to one site.  Shared memory: A (ncd^2), P(x) and
-// W = [Gamma (x) U] P(y) (12 x ncd each).
+// Block b of D_c at coarse site X; one CTA per (X, b).  For each site x of
+// the aggregate: A += P(x)^dag sum_hop coef [Gamma (x) U] P(y) over the hops
+// x -> y of the block (the identity and the internal hops for b = 0), with
+// P(.) the 12 x ncd restriction of the columns to one site: one ncd x ncd
+// product per site instead of one per hop.  Shared memory: A (ncd^2), P(x),
+// W = [Gamma (x) U] P(y), T1 and the hop sum Ws (12 x ncd each).
 __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double kappa, double2 *Dc, MgGeom M) {
     extern __shared__ double2 smem[];
     const int ncd = M.ncd, nv = M.nv;
-    double2 *A = smem, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd;
+    double2 *A = smem, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd, *Ws = T1 + 12 * ncd;
     const int X = blockIdx.x / 9, b = blockIdx.x % 9;
     const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
     const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
     const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
     for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) A[e] = make_double2(0, 0);
-    __syncthreads();
-    // hop list: for b = 0 the identity (mu = -1) and internal hops; else the face hops of one direction
+    // hop list: for b = 0 the identity (mu = -1) and internal hops; else the face hops of one direction.
+    // The hops of block b that start at site x are summed into Ws = sum_hop coef [Gamma (x) U] P(y)
+    // first, then A += P(x)^dag Ws once per site.
     for (int j = 0; j < nsite; ++j) {
         int c[4];
         agg_site(M, X, j, c);
         const int xs = lex(M.g, c);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) Ws[e] = make_double2(0, 0);
+        bool any = false;
         for (int hop = -1; hop < 8; ++hop) {
             // hop -1: identity; 0..3 forward mu; 4..7 backward mu
             int mu = hop & 3, fwd = hop < 4;
@@ -274,13 +428,13 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
                 }
             }
             if (blk != b) continue;
+            any = true;
             const int ys = lex(M.g, y);
-            // P(x) and P(y) restricted to the site (12 x ncd, zero outside each column's half)
+            __syncthreads();
+            // P(y) restricted to the site (12 x ncd, zero outside each column's half)
             for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
                 const int comp = e / ncd, i = e % ncd, h = i / nv, k = i % nv;
-                const bool on = (comp / 6) == h;
-                Px[e] = on ? P[pidx(M, xs, comp, k)] : make_double2(0, 0);
-                W[e] = on ? P[pidx(M, ys, comp, k)] : make_double2(0, 0);
+                W[e] = (comp / 6) == h ? P[pidx(M, ys, comp, k)] : make_double2(0, 0);
             }
             __syncthreads();
             double coef;
@@ -313,17 +467,27 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
             } else {
                 coef = 1.0;
             }
-            // A[i][j] += coef * sum_comp conj(Px[comp][i]) W[comp][j]
-            for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
-                const int i = e / ncd, jj = e % ncd;
-                double2 acc = make_double2(0, 0);
-                for (int comp = 0; comp < 12; ++comp) acc = zfma_conj(acc, Px[comp * ncd + i], W[comp * ncd + jj]);
-                A[e].x += coef * acc.x;
-                A[e].y += coef * acc.y;
+            for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                Ws[e].x += coef * W[e].x;
+                Ws[e].y += coef * W[e].y;
             }
-            __syncthreads();
+        }
+        if (!any) continue;
+        // P(x) restricted to the site, then A[i][j] += sum_comp conj(Px[comp][i]) Ws[comp][j]
+        for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+            const int comp = e / ncd, i = e % ncd, h = i / nv, k = i % nv;
+            Px[e] = (comp / 6) == h ? P[pidx(M, xs, comp, k)] : make_double2(0, 0);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
+            const int i = e / ncd, jj = e % ncd;
+            double2 acc = make_double2(0, 0);
+            for (int comp = 0; comp < 12; ++comp) acc = zfma_conj(acc, Px[comp * ncd + i], Ws[comp * ncd + jj]);
+            A[e].x += acc.x;
+            A[e].y += acc.y;
         }
     }
+    __syncthreads();
     for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) Dc[((size_t)X * 9 + b) * ncd * ncd + e] = A[e];
 }
 
@@ -649,14 +813,63 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
     wd_mg *g = c->mg;
     if (!g || !g->Gt) { set_error("coarse contraction: no multigrid setup"); return WD_EINVAL; }
     if (nrhs <= 0) return WD_OK;
-    k_contract_coarse_t<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Gt, (const double2 *)a, (const double2 *)b, gamma5,
-                                                              part, mg_geom(c));
+    const MgGeom M = mg_geom(c);
+    if (c->outer == PDD && g->Ghi) {
+        // double-float arithmetic (the FP64 rate is a small fraction of the FP32 one)
+        void *bd;
+        const long nc = (long)nrhs * M.Vc * M.ncd;
+        WD_TRY(ws_get(c, "mg.cdd", (size_t)nc * sizeof(float4), &bd));
+        WD_CUDA(launch_to_ddl(b, bd, nc, c->st));
+        k_contract_coarse_t_dd<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Ghi, g->Glo, (const double2 *)a,
+                                                                     (const float4 *)bd, gamma5, part, M);
+        c->launches += 2;
+    } else {
+        k_contract_coarse_t<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Gt, (const double2 *)a, (const double2 *)b,
+                                                                  gamma5, part, M);
+        c->launches++;
+    }
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, double *yc, int nrhs) {
+    const MgGeom M = mg_geom(c);
+    constexpr int RT = 8;
+    const long n = (long)((nrhs + RT - 1) / RT) * M.Vc * M.agg[3] * M.ncd;
+    if (c->outer == PDD && c->mg->Phi) {
+        void *ved, *vod;
+        const long nf = 12L * M.g.Vh * nrhs;
+        WD_TRY(ws_get(c, "mg.vedd", (size_t)nf * sizeof(float4), &ved));
+        WD_TRY(ws_get(c, "mg.vodd", (size_t)nf * sizeof(float4), &vod));
+        WD_CUDA(launch_to_ddl(ve, ved, nf, c->st));
+        WD_CUDA(launch_to_ddl(vo, vod, nf, c->st));
+        k_restrict_t<true, RT><<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(nullptr, c->mg->Phi, c->mg->Plo, ved,
+                                                                               vod, (double2 *)Rt, M, nrhs);
+        c->launches += 3;
+    } else {
+        k_restrict_t<false, RT><<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->P, nullptr, nullptr, ve, vo,
+                                                                                (double2 *)Rt, M, nrhs);
+        c->launches++;
+    }
+    const long nc = (long)nrhs * M.Vc * M.ncd;
+    k_sum_tau<<<(unsigned)((nc + 255) / 256), 256, 0, c->st>>>((const double2 *)Rt, (double2 *)yc, M, nrhs);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
-int coarse_tc_apply(wd_ctx *c, const void *x_bf16, float *y, int nrhs);   // wd_coarse_tc.cu
+int mg_contract_rt(wd_ctx *c, const double *Rt, const double *y, int gamma5, int nrhs, double *part) {
+    if (nrhs <= 0) return WD_OK;
+    k_contract_rt<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>((const double2 *)Rt, (const double2 *)y, gamma5, part,
+                                                        mg_geom(c));
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// split = false: x a BF16 field; true: x an FP32 field, split into a BF16
+// pair and multiplied with the blocks as BF16 pairs (~16 significant bits)
+int coarse_tc_apply(wd_ctx *c, const void *x, float *y, int nrhs, bool split = false);   // wd_coarse_tc.cu
 int coarse_tc_check(wd_ctx *c);
 int coarse_tc_build(wd_ctx *c);
 bool coarse_tc_ok(wd_ctx *c);
@@ -667,8 +880,16 @@ static int cop64(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
 static int cop32(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
     return coarse_apply32(c, (const float *)in, (float *)out, nrhs);
 }
+// inner operators of the mixed coarse solves on the tensor cores: BF16
+// Krylov vectors and blocks (good to ~4e-3), or (split) FP32 Krylov vectors
+// and blocks both as BF16 pairs (hi + lo, ~16 significant bits), so that an
+// inner solve can go to 1e-5 and the outer loop needs two FP64 residuals
+// instead of four or five
 static int coptc(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
-    return coarse_tc_apply(c, in, (float *)out, nrhs);
+    return coarse_tc_apply(c, in, (float *)out, nrhs, false);
+}
+static int coptc_split(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
+    return coarse_tc_apply(c, in, (float *)out, nrhs, true);
 }
 // r = b - D_c x; u (nullable) points at a flag: nonzero = double-float arithmetic
 static int cres64(wd_ctx *c, const double *b, const double *x, double *r, int nrhs, void *u) {
@@ -693,13 +914,14 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
     // the tensor cores BF16 operands; FP32 mode falls back to FP32 CUDA cores
     // only when the tensor-core operand could not be built)
     const bool tc = prec != P64 && coarse_tc_ok(c);
-    P.oplo = tc ? coptc : cop32; P.ulo = nullptr;
+    const bool split = tc && c->mg->Wlo;
+    P.oplo = split ? coptc_split : tc ? coptc : cop32; P.ulo = nullptr;
     // the FP64 residuals of the mixed solves in double-float arithmetic, as on
     // the fine lattice (~2^-44 normwise), unless the tolerance asks for more
     int use_dd = prec != P64 && tol >= 1e-12 && c->outer == PDD;
     P.res64 = cres64; P.ures = &use_dd;
     P.tag = "coarse";
-    const int inner = tc ? P16 : P32;
+    const int inner = tc && !split ? P16 : P32;
     std::vector<int> iters;
     std::vector<double> last;
     int s = dc_solve(c, P, b, x, nrhs, bn2, bnorm2, tol, prec == P64 ? P64 : inner, max_iter, iters, last);
@@ -732,11 +954,14 @@ void wd_mg_free(wd_ctx *c) {
     cudaFree(g->Dc);
     cudaFree(g->nbr);
     if (g->Wtc) cudaFree(g->Wtc);
+    if (g->Wlo) cudaFree(g->Wlo);
     if (g->Dc32) cudaFree(g->Dc32);
     if (g->Dclo) cudaFree(g->Dclo);
     if (g->Phi) cudaFree(g->Phi);
     if (g->Plo) cudaFree(g->Plo);
     if (g->Gt) cudaFree(g->Gt);
+    if (g->Ghi) cudaFree(g->Ghi);
+    if (g->Glo) cudaFree(g->Glo);
     delete g;
     c->mg = nullptr;
 }
@@ -757,7 +982,7 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     }
     if (nv > 6 * nsite) { set_error("wd_mg_setup: nv > 6 * aggregate volume"); return WD_EINVAL; }
     const int ncd = 2 * nv;
-    const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 3 * 12 * ncd);
+    const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 4 * 12 * ncd);
     if (smem > 227 * 1024) { set_error("wd_mg_setup: nv too large for the block assembly"); return WD_ENOTSUP; }
     wd_mg_free(c);
     wd_mg *g = new wd_mg();
@@ -773,7 +998,9 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Dclo, nD * sizeof(float2)) != cudaSuccess || cudaMalloc(&g->Phi, nP * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Plo, nP * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&g->Gt, sizeof(double2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess) {
+        cudaMalloc(&g->Gt, sizeof(double2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess ||
+        cudaMalloc(&g->Ghi, sizeof(float2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess ||
+        cudaMalloc(&g->Glo, sizeof(float2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess) {
         cudaGetLastError();
         wd_mg_free(c);
         set_error("wd_mg_setup: allocation failed");
@@ -806,7 +1033,8 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
-    c->launches += 7;
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Gt, g->Ghi, g->Glo, (long)g->Vc * agg[3] * 2 * nv * nv);
+    c->launches += 8;
     WD_CUDA(cudaGetLastError());
     WD_TRY(coarse_tc_build(c));
     WD_CUDA(cudaStreamSynchronize(c->st));

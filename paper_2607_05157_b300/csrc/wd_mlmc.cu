@@ -71,9 +71,12 @@ __global__ void k_coarse_noise_probe(double2 *xi, unsigned long long seed, int g
     xi[i] = make_double2(v, 0.0);
 }
 
-// d = z - w on FP64 eo fields (both parities stored separately); elementwise
-__global__ void k_sub(double *z, const double *w, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] -= w[i];
+// X[(g0 + r) T + t] -= part[r][t] (complex), one RHS per sample
+__global__ void k_sub_part(double *X, const double *part, int g0, int nrhs, int T) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrhs * T) return;
+    X[((size_t)g0 * T + i) * 2] -= part[(size_t)i * 2];
+    X[((size_t)g0 * T + i) * 2 + 1] -= part[(size_t)i * 2 + 1];
 }
 
 // partial X(rhs, t) = sum_{x in t} conj(a(x)) (B b)(x) for explicit eo fields a, b
@@ -213,27 +216,30 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
     for (int s0 = 0; s0 < (level1 ? 0 : N1); s0 += B) {
         const int nb = N1 - s0 < B ? N1 - s0 : B;
         const size_t f = field_bytes(g, P64, nb);
-        double *be, *bo, *ze, *zo, *we, *wo, *bc, *yc;
+        double *be, *bo, *ze, *zo, *bc, *yc;
         WD_TRY(ws_get(c, "mlmc.be", f, (void **)&be));
         WD_TRY(ws_get(c, "mlmc.bo", f, (void **)&bo));
         WD_TRY(ws_get(c, "mlmc.ze", f, (void **)&ze));
         WD_TRY(ws_get(c, "mlmc.zo", f, (void **)&zo));
-        WD_TRY(ws_get(c, "mlmc.we", f, (void **)&we));
-        WD_TRY(ws_get(c, "mlmc.wo", f, (void **)&wo));
         WD_TRY(ws_get(c, "mlmc.bc", sizeof(double2) * ncoarse * nb, (void **)&bc));
         WD_TRY(ws_get(c, "mlmc.yc", sizeof(double2) * ncoarse * nb, (void **)&yc));
         WD_TRY(gen_noise_eo(c, seed, s0, nb, be, bo));
         int s = solve_eo(c, be, bo, ze, zo, nb, tol, prec, 100000, nullptr, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_restrict_eo(c, be, bo, bc, nb, true));
+        // P^dag eta, kept per timeslice of each aggregate (Rt) for the coarse contraction
+        double *Rt, *part;
+        WD_TRY(ws_get(c, "mlmc.rt", sizeof(double2) * ncoarse * c->mg->agg[3] * nb, (void **)&Rt));
+        WD_TRY(ws_get(c, "mlmc.part", sizeof(double) * 2 * (size_t)nb * T, (void **)&part));
+        WD_TRY(mg_restrict_t_eo(c, be, bo, Rt, bc, nb));
         s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
-        WD_TRY(mg_prolong_eo(c, yc, we, wo, nb, true));
-        const long n = (long)nb * 24 * g.Vh;
-        k_sub<<<1184, 256, 0, c->st>>>(ze, we, n);
-        k_sub<<<1184, 256, 0, c->st>>>(zo, wo, n);
-        c->launches += 2;
+        // X_1(t) = eta^dag B z - sum_{x in t} eta^dag B (P y): the first on the
+        // fine lattice, the second on the coarse one from Rt (no prolongation)
         WD_TRY(contract_noise_eo(c, seed, s0, nb, gamma5, ze, zo, X1));
+        WD_TRY(mg_contract_rt(c, Rt, yc, gamma5, nb, part));
+        k_sub_part<<<(nb * T + 127) / 128, 128, 0, c->st>>>(X1, part, s0, nb, T);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
         ns += 2 * nb;
     }
     // ---- level 2: (P xi)^dag B (P D_c^{-1} xi), xi plain coarse noise or

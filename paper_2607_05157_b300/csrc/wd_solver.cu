@@ -255,7 +255,7 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
         return status;
     }
     const int pw = P32, pp = prec == P32 ? P32 : P16;
-    const double inner_tol = prec == P32 ? 1e-5 : 1e-2;
+    const double inner_tol = P.inner_tol > 0.0 ? P.inner_tol : prec == P32 ? 1e-5 : 1e-2;
     BiVecs V;
     WD_TRY(alloc_bivecs(c, P.sp, pw, pp, nrhs, V, tag + (prec == P32 ? ".bi32" : ".bi16")));
     V.op = P.oplo;
