@@ -282,7 +282,10 @@ def probing_measure(wd, api, torch, synth):
     out = {"workload": "16^3x32 kappa 0.13, tr[g5 D^-1(t,t)] summed over t; probing d = 2 (16 colours) and "
                        "d = 4 (64 colours) x 12 dilution, 4 noise samples each; Hutchinson with 768 Rademacher "
                        "vectors; solves to 1e-10, FP32 inner, autotuned batches"}
-    api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 1, 32, d=2, seed=1, op=1, tol=TOL)    # tuning, workspaces
+    # warm-up at the measured shapes (tuning, workspaces, graphs)
+    for d in (2, 4):
+        api.trace_estimate(ctx.h, wd.WD_PROBE, 12, 4, 32, d=d, seed=1, op=1, tol=TOL)
+    api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, 768, 32, seed=1, op=1, tol=TOL)
     for d, N in ((2, 4), (4, 4)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -485,6 +488,31 @@ def small_trace_measure(wd, api, torch, synth, steps=10):
             "estimate_diff_over_eps": abs(mix['total'] - ref['total']) / eps}
 
 
+def apply_measure(wd, api, torch, synth, dims, nrhs, steps, warmup):
+    """Row a4 alone: D = 1 - kappa H applied to nrhs Gaussian spinors with
+    FP32 storage (two hops per application, each with its same-parity
+    addend), CUDA-event times per hop launch and GB/s of the algorithmic
+    bytes (96 B in + 96 B out + 96 B addend per site and RHS, 8 links of 72 B
+    per site)."""
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1003), 0.13, BC)
+    x = torch.randn(ctx.field_shape(nrhs), dtype=torch.complex64, device='cuda')
+    y = torch.empty_like(x)
+    for _ in range(warmup):
+        api.wd_apply(ctx.h, x, y, prec=wd.WD_MIXED_FP32)
+    torch.cuda.synchronize()
+    api.wd_profile(ctx.h, True)
+    for _ in range(steps):
+        api.wd_apply(ctx.h, x, y, prec=wd.WD_MIXED_FP32)
+    n, ms, b = api.wd_profile_get(ctx.h, wd.WD_K_HOP)
+    api.wd_profile(ctx.h, False)
+    ctx.close()
+    peaks = measured_peaks()
+    gbs = b / (ms * 1e-3) / 1e9 if ms else None
+    return {"lattice": "x".join(map(str, dims)), "nrhs": nrhs, "hop_launches": n, "us_per_hop": 1e3 * ms / max(n, 1),
+            "MB_per_hop": b / max(n, 1) / 1e6, "GB_s": gbs,
+            "frac_of_measured_copy": gbs / peaks['hbm_gbs'] if (peaks and gbs) else None}
+
+
 # ---- the headline ------------------------------------------------------------
 
 def main():
@@ -501,13 +529,17 @@ def main():
     ap.add_argument('--coarse-only', action='store_true', help='only the tensor-core coarse stencil measurement')
     ap.add_argument('--coarse-lattice', default='24,24,24,48', help='fine lattice of --coarse-only (X,Y,Z,T)')
     ap.add_argument('--coarse-rhs', default='64,128,256,512', help='RHS counts of --coarse-only')
+    ap.add_argument('--apply-only', action='store_true',
+                    help='only the fine stencil: D applied (FP32 storage) to --apply-rhs spinors on --apply-lattice')
+    ap.add_argument('--apply-lattice', default='24,24,24,48', help='lattice of --apply-only (X,Y,Z,T)')
+    ap.add_argument('--apply-rhs', type=int, default=64, help='RHS of --apply-only')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)
 
     rank, world, local = env_rank()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.coarse_only:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.coarse_only or args.apply_only):
         # the oracle baseline runs in spawned processes before any GPU work
         gbs, cores, busy, wall = oracle_baseline(1)
         cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -530,6 +562,12 @@ def main():
             cd = tuple(int(v) for v in args.coarse_lattice.split(','))
             cr = tuple(int(v) for v in args.coarse_rhs.split(','))
             print(json.dumps({"coarse_tc": coarse_measure(wd, api, torch, synth, cr, cd)}), flush=True)
+        return
+    if args.apply_only:
+        if rank == 0:
+            ad = tuple(int(v) for v in args.apply_lattice.split(','))
+            print(json.dumps({"fine_stencil": apply_measure(wd, api, torch, synth, ad, args.apply_rhs,
+                                                            args.steps, args.warmup)}), flush=True)
         return
 
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16

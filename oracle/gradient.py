@@ -11,7 +11,7 @@ with the per-link force matrices (3x3 colour outer products, spin summed)
     G_mu(x) = kappa b sum_s z(x+mu)_s  [(1-g_mu) w(x)]_s^dag
     H_mu(x) = kappa b sum_s [(1+g_mu) w(x+mu)]_s  z(x)_s^dag
 where b = bc[mu] on the links that wrap around the lattice and 1 elsewhere.
-For kappa: dD/dkappa = (1 - D)/kappa, so dX/dkappa = (w^dag z - X)/kappa.
+For kappa: dD/dkappa = -H = (D - 1)/kappa, so dX/dkappa = (w^dag z - X)/kappa.
 """
 import numpy as np
 
