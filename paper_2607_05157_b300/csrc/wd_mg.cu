@@ -220,44 +220,63 @@ __global__ void __launch_bounds__(256) k_contract_coarse_t(const double2 *Gt, co
 }
 
 // the same in double-float arithmetic: Gt as Ghi + Glo, b split once into the
-// double-float layout, a split on the fly
+// double-float layout, a split on the fly.  One CTA per (tile of CR RHS, t):
+// each G row is read once for the CR RHS of the tile (the timeslice's G is
+// 4 MB, read from L2 by every CTA of that timeslice).
+template <int CR>
 __global__ void __launch_bounds__(256) k_contract_coarse_t_dd(const float2 *Gh, const float2 *Gl, const double2 *a,
-                                                              const float4 *b, int gamma5, double *part, MgGeom M) {
+                                                              const float4 *b, int gamma5, double *part, MgGeom M,
+                                                              int nrhs) {
     __shared__ double2 sh[32];
-    const int r = blockIdx.x, t = blockIdx.y, T = M.g.T;
+    const int r0 = blockIdx.x * CR, t = blockIdx.y, T = M.g.T;
+    const int nr = nrhs - r0 < CR ? nrhs - r0 : CR;
     const int at = M.agg[3], nv = M.nv, ncd = M.ncd;
     const int Vs = M.cd[0] * M.cd[1] * M.cd[2];
     const int ct = t / at, tau = t % at;
-    dd sre = dd_make(0.f, 0.f), sim = dd_make(0.f, 0.f);
+    dd sre[CR], sim[CR];
+#pragma unroll
+    for (int q = 0; q < CR; ++q) { sre[q] = dd_make(0.f, 0.f); sim[q] = dd_make(0.f, 0.f); }
     for (int item = threadIdx.x; item < Vs * ncd; item += blockDim.x) {
         const int xs = item / ncd, i = item % ncd, h = i / nv, k = i % nv;
         const int X = xs + Vs * ct;
         const size_t g0 = ((((size_t)X * at + tau) * 2 + h) * nv + k) * nv;
-        const float4 *bb = b + ((size_t)r * M.Vc + X) * ncd + nv * h;
-        dd ure = dd_make(0.f, 0.f), uim = dd_make(0.f, 0.f);
+        dd ure[CR], uim[CR];
+#pragma unroll
+        for (int q = 0; q < CR; ++q) { ure[q] = dd_make(0.f, 0.f); uim[q] = dd_make(0.f, 0.f); }
         for (int l = 0; l < nv; ++l) {
             const float2 mh = __ldg(Gh + g0 + l), ml = __ldg(Gl + g0 + l);
-            const float4 v = __ldg(bb + l);
             const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
-            const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
-            dd_fma(ure, mr, vr);
-            dd_fma(ure, -mi, vi);
-            dd_fma(uim, mr, vi);
-            dd_fma(uim, mi, vr);
+#pragma unroll
+            for (int q = 0; q < CR; ++q)
+                if (q < nr) {
+                    const float4 v = __ldg(b + ((size_t)(r0 + q) * M.Vc + X) * ncd + nv * h + l);
+                    const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+                    dd_fma(ure[q], mr, vr);
+                    dd_fma(ure[q], -mi, vi);
+                    dd_fma(uim[q], mr, vi);
+                    dd_fma(uim[q], mi, vr);
+                }
         }
-        const double2 av = a[((size_t)r * M.Vc + X) * ncd + i];
-        dd ar = d2dd(av.x), ai = d2dd(av.y);
-        if (gamma5 && h == 1) { ar = -ar; ai = -ai; }
-        dd_fma(sre, ar, ure);                // conj(a) u
-        dd_fma(sre, ai, uim);
-        dd_fma(sim, ar, uim);
-        dd_fma(sim, -ai, ure);
+#pragma unroll
+        for (int q = 0; q < CR; ++q)
+            if (q < nr) {
+                const double2 av = a[((size_t)(r0 + q) * M.Vc + X) * ncd + i];
+                dd ar = d2dd(av.x), ai = d2dd(av.y);
+                if (gamma5 && h == 1) { ar = -ar; ai = -ai; }
+                dd_fma(sre[q], ar, ure[q]);      // conj(a) u
+                dd_fma(sre[q], ai, uim[q]);
+                dd_fma(sim[q], ar, uim[q]);
+                dd_fma(sim[q], -ai, ure[q]);
+            }
     }
-    double2 acc = make_double2(dd2d(sre), dd2d(sim));
-    acc = block_reduce_z(acc, sh);
-    if (threadIdx.x == 0) {
-        part[((size_t)r * T + t) * 2] = acc.x;
-        part[((size_t)r * T + t) * 2 + 1] = acc.y;
+#pragma unroll
+    for (int q = 0; q < CR; ++q) {
+        double2 acc = make_double2(dd2d(sre[q]), dd2d(sim[q]));
+        acc = block_reduce_z(acc, sh);
+        if (threadIdx.x == 0 && q < nr) {
+            part[((size_t)(r0 + q) * T + t) * 2] = acc.x;
+            part[((size_t)(r0 + q) * T + t) * 2 + 1] = acc.y;
+        }
     }
 }
 
@@ -503,21 +522,26 @@ __global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
 // as Dc32 + Dclo, x split once into the double-float layout): y = a w + beta
 // A x with the block products and the sums over j and the 9 blocks kept as
 // float pairs (exact FMA errors, TwoSum), the final a w + beta acc in FP64.
-// One CTA per (X, 8-RHS tile), threads (i, r); each of the 9 blocks is
+// One CTA per (X, 32-RHS tile), threads (i, rq); each of the 9 blocks is
 // staged in shared memory by coalesced loads, transposed (column j
 // contiguous, so the threads of a warp read consecutive words), together
-// with the 8 RHS of its neighbour.
-__global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int *nbr, const float4 *x,
-                                  double2 *y, const double2 *w, double a, double beta, int ncd, int Vc, int nrhs) {
+// with the 32 RHS of its neighbour.
+__global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int *nbr, const float4 *x, double2 *y,
+                                  const double2 *w, double a, double beta, int ncd, int Vc, int nrhs) {
+    // one CTA per (X, tile of CD_TILE = 32 RHS), threads (i, rq), rq < 8; thread (i, rq) takes
+    // the RHS rq, rq + 8, rq + 16, rq + 24 of the tile, so each staged block element read
+    // from shared memory serves four RHS (the summation order per RHS is unchanged)
+    constexpr int NQ = 4, TILE = 8 * NQ;
     extern __shared__ float4 sm[];
     const int ld = ncd + 1;                                     // padded column stride
     float2 *Ah = (float2 *)sm, *Al = Ah + ncd * ld;
-    float4 *xs = (float4 *)(Al + ncd * ld + (ncd * ld) % 2);    // [8][ncd], 16-byte aligned
-    const int X = blockIdx.x, r0 = blockIdx.y * 8;
-    const int i = threadIdx.x % ncd, rr = threadIdx.x / ncd;
-    const int r = r0 + rr;
+    float4 *xs = (float4 *)(Al + ncd * ld + (ncd * ld) % 2);    // [TILE][ncd], 16-byte aligned
+    const int X = blockIdx.x, r0 = blockIdx.y * TILE;
+    const int i = threadIdx.x % ncd, rq = threadIdx.x / ncd;
     const int nn = ncd * ncd;
-    dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
+    dd are[NQ], aim[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) { are[q] = dd_make(0.f, 0.f); aim[q] = dd_make(0.f, 0.f); }
     for (int b = 0; b < 9; ++b) {
         const int nb = nbr[X * 9 + b];
         const size_t base = ((size_t)X * 9 + b) * nn;
@@ -527,29 +551,37 @@ __global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int 
             Ah[ej * ld + ei] = __ldg(Dh + base + e);
             Al[ej * ld + ei] = __ldg(Dl + base + e);
         }
-        for (int e = threadIdx.x; e < 8 * ncd; e += blockDim.x) {
+        for (int e = threadIdx.x; e < TILE * ncd; e += blockDim.x) {
             const int er = e / ncd, ej = e - er * ncd;
             xs[e] = r0 + er < nrhs ? __ldg(x + ((size_t)(r0 + er) * Vc + nb) * ncd + ej) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
-        if (rr < 8) {
+        if (rq < 8) {
             for (int j = 0; j < ncd; ++j) {
                 const float2 mh = Ah[j * ld + i], ml = Al[j * ld + i];
-                const float4 v = xs[rr * ncd + j];
                 const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
-                const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
-                dd_fma(are, mr, vr);
-                dd_fma(are, -mi, vi);
-                dd_fma(aim, mr, vi);
-                dd_fma(aim, mi, vr);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 v = xs[(rq + 8 * q) * ncd + j];
+                    const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
+                    dd_fma(are[q], mr, vr);
+                    dd_fma(are[q], -mi, vi);
+                    dd_fma(aim[q], mr, vi);
+                    dd_fma(aim[q], mi, vr);
+                }
             }
         }
     }
-    if (rr >= 8 || r >= nrhs) return;
-    const size_t o = ((size_t)r * Vc + X) * ncd + i;
-    double ore = beta * dd2d(are), oim = beta * dd2d(aim);
-    if (w) { ore += a * w[o].x; oim += a * w[o].y; }
-    y[o] = make_double2(ore, oim);
+    if (rq >= 8) return;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int r = r0 + rq + 8 * q;
+        if (r >= nrhs) continue;
+        const size_t o = ((size_t)r * Vc + X) * ncd + i;
+        double ore = beta * dd2d(are[q]), oim = beta * dd2d(aim[q]);
+        if (w) { ore += a * w[o].x; oim += a * w[o].y; }
+        y[o] = make_double2(ore, oim);
+    }
 }
 
 // ---- coarse stencil on CUDA cores (FP64 reference path and FP32) -----------
@@ -731,9 +763,9 @@ int coarse_apply_dd(wd_ctx *c, const double *x, double *y, const double *w, doub
     void *xd;
     WD_TRY(ws_get(c, "coarse.xdd", (size_t)n * sizeof(float4), &xd));
     WD_CUDA(launch_to_ddl(x, xd, n, c->st));
-    dim3 grid(g->Vc, (nrhs + 7) / 8);
+    dim3 grid(g->Vc, (nrhs + 31) / 32);
     const size_t nld = (size_t)g->ncd * (g->ncd + 1);
-    const size_t smem = (2 * nld + nld % 2) * sizeof(float2) + (size_t)8 * g->ncd * sizeof(float4);
+    const size_t smem = (2 * nld + nld % 2) * sizeof(float2) + (size_t)32 * g->ncd * sizeof(float4);
     WD_CUDA(cudaFuncSetAttribute(k_coarse_apply_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_coarse_apply_dd<<<grid, g->ncd * 8, smem, c->st>>>(g->Dc32, g->Dclo, g->nbr, (const float4 *)xd, (double2 *)y,
                                                          (const double2 *)w, a, beta, g->ncd, g->Vc, nrhs);
@@ -820,8 +852,9 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
         const long nc = (long)nrhs * M.Vc * M.ncd;
         WD_TRY(ws_get(c, "mg.cdd", (size_t)nc * sizeof(float4), &bd));
         WD_CUDA(launch_to_ddl(b, bd, nc, c->st));
-        k_contract_coarse_t_dd<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Ghi, g->Glo, (const double2 *)a,
-                                                                     (const float4 *)bd, gamma5, part, M);
+        constexpr int CR = 8;
+        k_contract_coarse_t_dd<CR><<<dim3((nrhs + CR - 1) / CR, c->g.T), 256, 0, c->st>>>(
+            g->Ghi, g->Glo, (const double2 *)a, (const float4 *)bd, gamma5, part, M, nrhs);
         c->launches += 2;
     } else {
         k_contract_coarse_t<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Gt, (const double2 *)a, (const double2 *)b,
