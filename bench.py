@@ -204,14 +204,15 @@ def run_reference(args):
 
 def dslash_bytes(api, wd, c, ncd, Vc):
     """Fine (FP32/BF16 and FP64 / double-float) stencil bytes and coarse
-    stencil bytes (blocks as compact complex BF16, 9 * ncd^2 * 4 B per site and
-    launch, plus the BF16 input and FP32 output vectors per RHS) and event
-    times of the launches profiled on context c since wd_profile(c, 1)."""
+    stencil bytes, and event times of the launches profiled on context c since
+    wd_profile(c, 1).  The coarse launches of the solves multiply BF16 pairs:
+    blocks 9 * ncd^2 * 8 B per site and launch, input 8 B and FP32 output 8 B
+    per complex entry and RHS."""
     n32, ms32, b32 = api.wd_profile_get(c.h, wd.WD_K_HOP)
     n64, ms64, b64 = api.wd_profile_get(c.h, wd.WD_K_HOP64)
     nco, msco, flco = api.wd_profile_get(c.h, wd.WD_K_COARSE)
     rhs_sites = flco / (8.0 * ncd * ncd * 9.0) if ncd else 0.0      # sum over launches of Vc * nrhs
-    bco = nco * Vc * 9 * ncd * ncd * 4.0 + rhs_sites * ncd * (4.0 + 8.0)
+    bco = nco * Vc * 9 * ncd * ncd * 8.0 + rhs_sites * ncd * (8.0 + 8.0)
     return {"hop32": (n32, ms32, b32), "hop64": (n64, ms64, b64), "coarse": (nco, msco, bco, flco)}
 
 
@@ -222,29 +223,31 @@ def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 
     workload (4^4 aggregates, 24 test vectors -> 48x48 blocks, 2592 coarse
     sites), CUDA-event times of the kernel, algorithmic TFLOP/s (8 ncd^2 per
     block, 9 blocks per site and RHS) and GB/s of the compact algorithmic
-    bytes (blocks as complex BF16, vectors in and out)."""
+    bytes: blocks and input at 4 B (BF16) or 8 B (BF16 pairs, the operator of
+    the coarse solves) per complex entry, FP32 output 8 B."""
     ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1004), 0.13, BC)
     api.wd_mg_setup(ctx.h, None, 24, (4, 4, 4, 4), tv_iters=0, seed=3)
     Vc, ncd = (dims[0] // 4) * (dims[1] // 4) * (dims[2] // 4) * (dims[3] // 4), 48
     out = []
-    for nrhs in rhs_list:
-        x = torch.randn((nrhs, Vc, ncd), dtype=torch.complex128, device='cuda')
-        y = torch.empty_like(x)
-        for _ in range(2):
-            api.wd_coarse_apply(ctx.h, x, y, 1)
-        torch.cuda.synchronize()
-        api.wd_profile(ctx.h, True)
-        for _ in range(5):
-            api.wd_coarse_apply(ctx.h, x, y, 1)
-        n, ms, fl = api.wd_profile_get(ctx.h, wd.WD_K_COARSE)
-        api.wd_profile(ctx.h, False)
-        per = ms / n
-        alg = Vc * (9 * ncd * ncd * 4.0 + nrhs * ncd * 12.0)
-        out.append({"nrhs": nrhs, "ms_per_launch": per, "TFLOP_s": fl / n / (per * 1e-3) / 1e12,
-                    "GB_s_algorithmic": alg / (per * 1e-3) / 1e9})
+    for mode, prec, eb in (("bf16_pairs", 1, 8.0), ("bf16", 2, 4.0)):
+        for nrhs in rhs_list:
+            x = torch.randn((nrhs, Vc, ncd), dtype=torch.complex128, device='cuda')
+            y = torch.empty_like(x)
+            for _ in range(2):
+                api.wd_coarse_apply(ctx.h, x, y, prec)
+            torch.cuda.synchronize()
+            api.wd_profile(ctx.h, True)
+            for _ in range(5):
+                api.wd_coarse_apply(ctx.h, x, y, prec)
+            n, ms, fl = api.wd_profile_get(ctx.h, wd.WD_K_COARSE)
+            api.wd_profile(ctx.h, False)
+            per = ms / n
+            alg = Vc * (9 * ncd * ncd * eb + nrhs * ncd * (eb + 8.0))
+            out.append({"operands": mode, "nrhs": nrhs, "ms_per_launch": per,
+                        "TFLOP_s": fl / n / (per * 1e-3) / 1e12, "GB_s_algorithmic": alg / (per * 1e-3) / 1e9})
     ctx.close()
     peaks = measured_peaks()
-    return {"workload": "x".join(map(str, dims)) + ", 4^4 aggregates, nv=24 (48x48 blocks), BF16 tcgen05, FP32 accumulate",
+    return {"workload": "x".join(map(str, dims)) + ", 4^4 aggregates, nv=24 (48x48 blocks), tcgen05 BF16 or BF16-pair operands, FP32 accumulate",
             "bf16_peak_TFLOP_s": peaks['bf16_tflops'] if peaks else 1800.0, "points": out}
 
 

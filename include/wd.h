@@ -258,8 +258,11 @@ int wd_mg_setup(wd_ctx *ctx, const double *tv, int nv, const int agg[4], int tv_
 int wd_mg_test_vectors(wd_ctx *ctx, int nv, int iters, uint64_t seed, double *tv_out);
 
 /* y_c = D_c x_c on the coarse lattice: device complex128 [nrhs][Vc][2nv].
- * prec WD_FP64 uses FP64 blocks; WD_MIXED_FP32 / WD_MIXED_BF16 run the
- * 9-point block stencil on tensor cores with BF16 operands, FP32 accumulate. */
+ * prec WD_FP64 uses FP64 blocks.  The mixed precisions run the 9-point block
+ * stencil on the tensor cores (2nv in {48, 96}; FP32 accumulate): WD_MIXED_BF16
+ * with the blocks and x rounded to BF16 (~2^-8 per product), WD_MIXED_FP32
+ * with both as BF16 pairs hi + lo (~2^-16 per product, the operator of the
+ * mixed coarse solves).  Other shapes take the FP32 blocks on the CUDA cores. */
 int wd_coarse_apply(wd_ctx *ctx, const double *in, double *out, int nrhs, int prec);
 
 /* Restriction P^dag and prolongation P: fine device complex128

@@ -1,40 +1,52 @@
 // Coarse 9-point block stencil on the 5th-generation tensor cores (row a8).
 //
 // y(X) = sum_{b=0..8} A_b(X) x(nbr_b(X)) with ncd x ncd complex blocks is, for
-// every coarse site X, a real GEMM over the right-hand sides:
-//   out[r][n] = sum_k xin[r][k] W_X[n][k],   M = RHS (tiles of 128),
-//   N = 2 ncd (re/im interleaved outputs), K = 9 * 2 ncd (9 neighbour blocks),
-// where xin[r] concatenates the 9 neighbours' complex vectors as interleaved
-// (re, im) BF16 -- exactly the memory layout of a BF16 coarse field
-// [rhs][Vc][ncd] complex -- and W_X is the real expansion of the blocks:
-//   W[2i][2j] = Re A_ij, W[2i][2j+1] = -Im A_ij, W[2i+1][2j] = Im A_ij,
-//   W[2i+1][2j+1] = Re A_ij.
-// The output row is the FP32 coarse field [rhs][Vc][ncd] complex, directly.
+// every coarse site X, two real GEMMs over the right-hand sides that share one
+// compact block operand.  In 16-dof groups g (K = 16, one MMA deep):
+//   D1 += Re x_g . B_g^T,  D2 += Im x_g . B_g^T,
+//   B_g = [Re A_b(X)[:, g] ; Im A_b(X)[:, g]]   (N = 2 ncd rows),
+// so D1 = [Re x Re A^T | Re x Im A^T], D2 = [Im x Re A^T | Im x Im A^T] and
+//   Re y = D1[:, :ncd] - D2[:, ncd:],  Im y = D1[:, ncd:] + D2[:, :ncd].
+// Neither operand is duplicated for the complex product: the blocks stream
+// once at 4 bytes per complex entry (BF16), the input at the field's own size.
 //
-// Kernel: one CTA (4 warps) per (X, RHS tile).  TMA brings 32-wide K chunks of
-// xin (3D map over the coarse field: K, site, rhs; the neighbour index picks
-// the site coordinate) and of W_X (2D map) into 64-byte-swizzled shared
-// memory through a 4-stage mbarrier pipeline; thread 0 produces, thread 32
-// issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M=128, N=2ncd, K=16)
-// into a TMEM accumulator and releases each stage with tcgen05.commit; the 4
-// warps then read their 32 TMEM lanes with tcgen05.ld and store FP32 rows.
+// Operand layout: every MMA tile is a run of 32-byte rows (16 BF16), stored in
+// global memory as the image of its shared-memory tile under the 32-byte
+// swizzle the MMA descriptors name (16-byte unit u of row r at u ^ ((r >> 2) & 1)),
+// so that a stage is filled by plain bulk copies of whole tiles:
+//   input  P: [Vc][G][RHS tile][Re|Im][rows][16], rows = 128 except in the
+//             last tile (its RHS count rounded up to 8), so that one copy
+//             brings the Re and the Im tile of a group;
+//   blocks B: [Vc][9][G][2 ncd][16], tile (X, b, g) over the rows of B_g.
+//
+// Kernel: persistent, one CTA of 6 warps per SM, looping over the work items
+// (X, RHS tile of 128).  Warp 0 (one lane) produces: bulk copies
+// (cp.async.bulk, completion counted on the stage's mbarrier) of TC_CPS groups
+// per stage into a ring that runs on across items.  Warp 1 allocates TMEM and
+// (one lane) issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128,
+// N = 2 ncd) into one of two accumulator sets, releasing each stage with
+// tcgen05.commit and handing a finished set to the epilogue with another.
+// Warps 2-5 drain a set (tcgen05.ld of their 32 TMEM lanes each), give it back
+// and store interleaved FP32 complex rows while the next item's MMAs run.
 // Every mbarrier wait is bounded: on timeout the kernel raises an error flag,
-// skips the remaining work, lets the copies it issued land, frees its TMEM
-// and returns; a producer wait also gives up as soon as another role of the
-// CTA has failed.  The environment variable WD_TEST_TC_STALL=1 makes the MMA
-// issuer wait, with a short limit, on a barrier nothing arrives on (a test of
-// that failure path without any fault: the call returns WD_ETIMEOUT and the
-// context stays usable).
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
+// all roles stop, the copies and MMAs already issued complete, the TMEM is
+// freed and the kernel returns.  The environment variable WD_TEST_TC_STALL=1
+// makes the MMA issuer wait, with a short limit, on a barrier nothing arrives
+// on (a test of that failure path without any fault: the call returns
+// WD_ETIMEOUT and the context stays usable).
 #include "wd_internal.h"
 
 namespace wd {
 
 static constexpr int TC_M = 128;      // RHS per tile
-static constexpr int TC_KC = 32;      // K elements (bf16) per chunk = one 64-byte swizzle row
-static constexpr int TC_STAGES = 4;
+static constexpr int TC_KC = 16;      // K elements (bf16) per tile row = one 32-byte swizzle row
+static constexpr int TC_MAXSTAGES = 8;
+static constexpr int TC_THREADS = 192;   // producer warp, MMA warp, 4 epilogue warps
+static constexpr int TC_CPS = 3;         // 16-dof groups per stage (one neighbour block at ncd = 48)
+// ring depth: 165-200 KB of stages for the one CTA per SM
+__host__ __device__ constexpr int tc_stages(int NC, bool split) {
+    return NC <= 48 ? (split ? 3 : 5) : (split ? 2 : 4);
+}
 static constexpr long TC_SPIN = 1L << 24;   // bounded waits
 static constexpr long TC_SPIN_TEST = 1L << 10;   // the short limit of the stall test
 
@@ -42,6 +54,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -65,28 +80,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1) : "memory");
+// bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, counted on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// UMMA shared-memory descriptor, K-major operand with 64-byte swizzle:
+// UMMA shared-memory descriptor, K-major operand with 32-byte swizzle:
 // start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29, unused for
-// swizzled K-major), stride byte offset >> 4 (32-45: 8-row groups, 512 B apart),
-// descriptor version 1 (46-47), layout type 4 = SWIZZLE_64B (61-63).
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+// swizzled K-major), stride byte offset >> 4 (32-45: 8-row groups, 256 B apart),
+// descriptor version 1 (46-47), layout type 6 = SWIZZLE_32B (61-63).
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)(256 >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
+    d |= (uint64_t)6 << 61;
     return d;
 }
 
@@ -96,53 +107,72 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// 16 consecutive TMEM columns of this warp's 32 lanes (one 32-bit value each)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
 struct TcArgs {
+    const bf16 *P, *Plo;   // input operand (and remainder; Plo = P when not split)
+    const bf16 *B, *Blo;   // block operand (and remainder)
     const int *nbr;     // [Vc][9]
     float *y;           // FP32 coarse field [nrhs][Vc][ncd] complex
     int *err;           // set to a nonzero code on a timed-out wait
     int Vc, ncd, nrhs;
+    int nitems;         // Vc x RHS tiles, handed out round-robin over the CTAs
+    int nrhs8;          // nrhs rounded up to 8: the rows of one (site, group) of P
     int stall_test;     // 1: the MMA issuer waits (short limit) on a barrier nothing arrives on
 };
 
-// SPLIT: the blocks as two BF16 operands W + W_lo (mapw2) and the input as
-// two BF16 fields x + x_lo (mapx2), multiplied into the same accumulator as
-// W x + W_lo x + W x_lo (~16 significant bits of both operands; the product
-// of the two remainders is below that)
-template <int N, bool SPLIT>
-__global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CUtensorMap mapx,
-                                                      const __grid_constant__ CUtensorMap mapx2,
-                                                      const __grid_constant__ CUtensorMap mapw,
-                                                      const __grid_constant__ CUtensorMap mapw2, TcArgs A) {
-    constexpr int KB = N / TC_KC;              // chunks per neighbour block (N = 2 ncd)
-    constexpr int NCHUNK = 9 * KB;
-    constexpr int NB = SPLIT ? 2 : 1;          // A and B operands per chunk
-    constexpr uint32_t A1_BYTES = TC_M * TC_KC * 2, B1_BYTES = N * TC_KC * 2;
-    constexpr uint32_t A_BYTES = NB * A1_BYTES, B_BYTES = NB * B1_BYTES;
-    constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+// SPLIT: the blocks and the input as BF16 pairs (hi + lo: B, B_lo and P,
+// P_lo), multiplied into the same accumulators as B P + B_lo P + B P_lo (~16
+// significant bits of both operands; the product of the two remainders is
+// below that).  NC = ncd; the MMA's N is 2 NC.
+template <int NC, bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_coarse_tc(TcArgs A) {
+    constexpr int S = tc_stages(NC, SPLIT);
+    constexpr int G = NC / 16;                 // 16-dof groups per block
+    constexpr int NGRP = 9 * G;                // groups per item
+    constexpr int NSTEP = NGRP / TC_CPS;       // stages per item
+    constexpr int NQ = SPLIT ? 2 : 1;          // hi (, lo) tiles of each operand
+    constexpr int N = 2 * NC;
+    // a stage: input groups [NQ][TC_CPS] of GA bytes (128 Re rows, then 128
+    // Im rows of 32 bytes), then block tiles [NQ][TC_CPS]
+    constexpr uint32_t GA = 2 * TC_M * TC_KC * 2, B1_BYTES = N * TC_KC * 2;
+    constexpr uint32_t A_BYTES = NQ * TC_CPS * GA, B_BYTES = NQ * TC_CPS * B1_BYTES;
+    constexpr uint32_t DOFF = N <= 128 ? 128 : 256;   // TMEM columns of D1, then D2
+    constexpr int NSET = 4 * DOFF <= 512 ? 2 : 1;     // accumulator sets (double buffer when they fit)
+    constexpr int TMEM_COLS = 512;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned stage buffers (swizzle atoms must not straddle their base)
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
-    unsigned char *sB = sA + TC_STAGES * A_BYTES;
-    uint64_t *full = (uint64_t *)(sB + TC_STAGES * B_BYTES);
-    uint64_t *empty = full + TC_STAGES;
-    uint64_t *done = empty + TC_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    unsigned char *sB = sA + S * A_BYTES;
+    uint64_t *full = (uint64_t *)(sB + S * B_BYTES);
+    uint64_t *empty = full + S;
+    uint64_t *tfull = empty + S;               // [NSET] accumulator set ready (MMA -> epilogue)
+    uint64_t *tempty = tfull + 2;              // [NSET] accumulator set drained (epilogue -> MMA)
+    uint64_t *drain = tempty + 2;              // the MMA issuer's last commit
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile __shared__ int s_fail;
-    __shared__ int s_issued[TC_STAGES];
+    __shared__ int s_issued[TC_MAXSTAGES];
 
-    const int X = blockIdx.x / ((A.nrhs + TC_M - 1) / TC_M);
-    const int r0 = (blockIdx.x % ((A.nrhs + TC_M - 1) / TC_M)) * TC_M;
+    const int ntile = (A.nrhs + TC_M - 1) / TC_M;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(done, 1);
+        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int t = 0; t < 2; ++t) { mbar_init(&tfull[t], 1); mbar_init(&tempty[t], 4); }
+        mbar_init(drain, 1);
         s_fail = 0;
-        for (int s = 0; s < TC_STAGES; ++s) s_issued[s] = 0;
+        for (int s = 0; s < S; ++s) s_issued[s] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -153,80 +183,156 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
     const uint32_t tmem = *tmem_slot;
 
     if (threadIdx.x == 0) {
-        // producer: TMA loads of chunk kc into stage kc % S
-        for (int kc = 0; kc < NCHUNK && !s_fail; ++kc) {
-            const int s = kc % TC_STAGES;
-            if (kc >= TC_STAGES && !mbar_wait(&empty[s], ((kc / TC_STAGES) - 1) & 1, TC_SPIN, &s_fail)) {
-                if (!s_fail) s_fail = 1;
-                break;
+        // producer: bulk copies of TC_CPS groups per stage fill into stage
+        // gs % S.  An input tile holds the item's rows of RHS (fewer than 128
+        // in the last tile); the MMA still reads 128 rows: the rows past them
+        // hold stale data and give accumulator rows that are never stored.
+        // The 9 neighbour indices of the next item are loaded while this one
+        // is issued, so that no copy waits on a dependent global load.
+        uint32_t gs = 0;                       // stage fills, counted over all items
+        int nbv[9], nbn[9];
+        if (blockIdx.x < A.nitems) {
+#pragma unroll
+            for (int b = 0; b < 9; ++b) nbv[b] = A.nbr[(blockIdx.x / ntile) * 9 + b];
+        }
+        for (int it = blockIdx.x; it < A.nitems && !s_fail; it += gridDim.x) {
+            const int X = it / ntile, r0 = (it % ntile) * TC_M;
+            const int itn = it + gridDim.x;
+            if (itn < A.nitems) {
+#pragma unroll
+                for (int b = 0; b < 9; ++b) nbn[b] = A.nbr[(itn / ntile) * 9 + b];
             }
-            const int b = kc / KB, kk = (kc % KB) * TC_KC;
-            const int nb = A.nbr[X * 9 + b];
-            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_3d(sA + s * A_BYTES, &mapx, &full[s], kk, nb, r0);
-            tma_load_2d(sB + s * B_BYTES, &mapw, &full[s], kc * TC_KC, X * N);
-            if (SPLIT) {
-                tma_load_3d(sA + s * A_BYTES + A1_BYTES, &mapx2, &full[s], kk, nb, r0);
-                tma_load_2d(sB + s * B_BYTES + B1_BYTES, &mapw2, &full[s], kc * TC_KC, X * N);
+            // rows of this tile in P (a multiple of 8); its Im half follows its Re half
+            const int rows = min(TC_M, A.nrhs8 - r0);
+            const uint32_t abytes = 2u * (uint32_t)rows * TC_KC * 2;
+            const uint32_t tx = NQ * TC_CPS * (abytes + B1_BYTES);
+            const size_t bx = (size_t)X * NGRP * N * TC_KC;
+            bool stop = false;
+            for (int st = 0; st < NSTEP; ++st, ++gs) {
+                const int s = (int)(gs % S);
+                if (gs >= S && !mbar_wait(&empty[s], ((gs / S) - 1) & 1, TC_SPIN, &s_fail)) {
+                    if (!s_fail) s_fail = 1;
+                    stop = true;
+                    break;
+                }
+                unsigned char *a = sA + s * A_BYTES;
+                unsigned char *bb = sB + s * B_BYTES;
+                mbar_expect_tx(&full[s], tx);
+                // the stage's TC_CPS block tiles are consecutive in B
+                const size_t bo = bx + (size_t)st * TC_CPS * N * TC_KC;
+                bulk_load(bb, A.B + bo, TC_CPS * B1_BYTES, &full[s]);
+                if (SPLIT) bulk_load(bb + TC_CPS * B1_BYTES, A.Blo + bo, TC_CPS * B1_BYTES, &full[s]);
+#pragma unroll
+                for (int c = 0; c < TC_CPS; ++c) {
+                    const int kg = st * TC_CPS + c, b = kg / G, g = kg % G;
+                    int nb = nbv[0];
+#pragma unroll
+                    for (int q = 1; q < 9; ++q) nb = b == q ? nbv[q] : nb;
+                    const size_t ao = (((size_t)nb * G + g) * A.nrhs8 + r0) * 2 * TC_KC;
+                    bulk_load(a + c * GA, A.P + ao, abytes, &full[s]);
+                    if (SPLIT) bulk_load(a + (TC_CPS + c) * GA, A.Plo + ao, abytes, &full[s]);
+                }
+                s_issued[s] += 1;
             }
-            s_issued[s] += 1;
+            if (stop) break;
+#pragma unroll
+            for (int b = 0; b < 9; ++b) nbv[b] = nbn[b];
         }
     } else if (threadIdx.x == 32) {
-        // MMA issuer
+        // MMA issuer: per group, D1 += Re x . B^T and D2 += Im x . B^T
         constexpr uint32_t idesc = idesc_bf16_f32(TC_M, N);
-        for (int kc = 0; kc < NCHUNK; ++kc) {
-            const int s = kc % TC_STAGES;
-            const bool got = A.stall_test ? mbar_wait(done, 0, TC_SPIN_TEST) : mbar_wait(&full[s], (kc / TC_STAGES) & 1);
-            if (!got) { s_fail = 2; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
-#pragma unroll
-            for (int k16 = 0; k16 < TC_KC / 16; ++k16)
-#pragma unroll
-                for (int q = 0; q < (SPLIT ? 3 : 1); ++q) {
-                    // q = 0: W x, 1: W_lo x, 2: W x_lo
-                    const uint64_t da = desc_sw64(a0 + (q == 2 ? A1_BYTES : 0) + 32 * k16);
-                    const uint64_t db = desc_sw64(b0 + (q == 1 ? B1_BYTES : 0) + 32 * k16);
-                    const uint32_t acc = (kc > 0 || k16 > 0 || q > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
-                }
-            // release the stage when these MMAs have read it
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&empty[s])) : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(smem_u32(done)) : "memory");
-    }
-    __syncwarp();
-    // epilogue: all 4 warps wait for the accumulator, read their 32 lanes
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, A.stall_test ? TC_SPIN_TEST : TC_SPIN, &s_fail));
-    if (!ok && lane == 0) s_fail = 3;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncwarp();
-    const int r = r0 + warp * 32 + lane;
-    float *out = A.y + ((size_t)r * A.Vc + X) * N;
-    if (ok) {
-#pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r < A.nrhs) {
-                float4 *o4 = (float4 *)(out + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    o4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                        __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        // descriptors of stage 0; a stage's, and a tile's within it, differ
+        // only by a constant added to the 14-bit start-address field
+        const uint64_t dA0 = desc_sw32(smem_u32(sA)), dB0 = desc_sw32(smem_u32(sB));
+        uint32_t gs = 0;
+        int li = 0;
+        if (A.stall_test && !mbar_wait(drain, 0, TC_SPIN_TEST)) s_fail = 2;
+        for (int it = blockIdx.x; it < A.nitems && !s_fail; it += gridDim.x, ++li) {
+            const int set = li % NSET, use = li / NSET;
+            if (use > 0 && !mbar_wait(&tempty[set], (uint32_t)(use - 1) & 1, TC_SPIN, &s_fail)) {
+                if (!s_fail) s_fail = 2;
+                break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t dcol = tmem + (uint32_t)set * 2 * DOFF;
+            // the Im tile of a group starts `rows` rows after its Re tile (a
+            // multiple of 8 rows, so on a swizzle-atom boundary); the MMA reads
+            // 128 rows from either start, all inside the group's 2 x 128 rows
+            const uint32_t imoff = (uint32_t)min(TC_M, A.nrhs8 - (it % ntile) * TC_M) * TC_KC * 2;
+            bool ok = true;
+            for (int st = 0; st < NSTEP; ++st, ++gs) {
+                const int s = (int)(gs % S);
+                if (!mbar_wait(&full[s], (gs / S) & 1, TC_SPIN, &s_fail)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint64_t dA = dA0 + (uint64_t)(s * (A_BYTES >> 4)), dB = dB0 + (uint64_t)(s * (B_BYTES >> 4));
+                const uint32_t later = st > 0 ? 1u : 0u;
+#pragma unroll
+                for (int c = 0; c < TC_CPS; ++c)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int q = 0; q < (SPLIT ? 3 : 1); ++q) {
+                            // q = 0: P B, 1: P B_lo, 2: P_lo B
+                            const uint32_t ao = ((q == 2 ? TC_CPS : 0) + c) * GA + (h ? imoff : 0u);
+                            const uint32_t bo = ((q == 1 ? TC_CPS : 0) + c) * B1_BYTES;
+                            // the first MMA into each accumulator of an item overwrites it
+                            const uint32_t acc = (c > 0 || q > 0) ? 1u : later;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                ::"r"(dcol + (uint32_t)h * DOFF), "l"(dA + (ao >> 4)), "l"(dB + (bo >> 4)), "r"(idesc),
+                                  "r"(acc));
+                        }
+                // release the stage when these MMAs have read it
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&empty[s])) : "memory");
+            }
+            if (!ok) { if (!s_fail) s_fail = 2; break; }
+            // the set is complete once these MMAs are
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&tfull[set])) : "memory");
+        }
+        // every MMA issued has completed before the CTA may free TMEM or shared memory
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(drain)) : "memory");
+        if (!mbar_wait(drain, 0) && !s_fail) s_fail = 4;
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the lanes its
+        // position in the warpgroup may access), i.e. RHS rows r0 + 32 (w % 4) + lane
+        const int quarter = warp & 3;
+        int li = 0;
+        for (int it = blockIdx.x; it < A.nitems; it += gridDim.x, ++li) {
+            const int set = li % NSET, use = li / NSET;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(&tfull[set], (uint32_t)use & 1, TC_SPIN, &s_fail));
+            if (!got) { if (lane == 0 && !s_fail) s_fail = 3; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int X = it / ntile, r = (it % ntile) * TC_M + quarter * 32 + lane;
+            float *out = A.y + ((size_t)r * A.Vc + X) * 2 * NC;
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)set * 2 * DOFF;
+#pragma unroll
+            for (int c0 = 0; c0 < NC; c0 += 16) {
+                // u = Re x Re A, v = Re x Im A, w = Im x Re A, z = Im x Im A (16 columns each)
+                uint32_t u[16], v[16], w[16], z[16];
+                tmem_ld16(tbase + (uint32_t)c0, u);
+                tmem_ld16(tbase + (uint32_t)(NC + c0), v);
+                tmem_ld16(tbase + DOFF + (uint32_t)c0, w);
+                tmem_ld16(tbase + DOFF + (uint32_t)(NC + c0), z);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (r < A.nrhs) {
+                    float4 *o4 = (float4 *)(out + 2 * c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        o4[q] = make_float4(__uint_as_float(u[2 * q]) - __uint_as_float(z[2 * q]),
+                                            __uint_as_float(v[2 * q]) + __uint_as_float(w[2 * q]),
+                                            __uint_as_float(u[2 * q + 1]) - __uint_as_float(z[2 * q + 1]),
+                                            __uint_as_float(v[2 * q + 1]) + __uint_as_float(w[2 * q + 1]));
+                }
+            }
+            // hand the set back to the MMA issuer
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[set]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -234,56 +340,70 @@ __global__ void __launch_bounds__(128, 1) k_coarse_tc(const __grid_constant__ CU
     if (s_fail && threadIdx.x == 0) {
         atomicExch(A.err, s_fail);
         // let the copies this CTA issued land before its shared memory is released:
-        // the last load into stage s completes phase s_issued[s] - 1 of full[s]
-        for (int s = 0; s < TC_STAGES; ++s)
+        // the last fill of stage s completes phase s_issued[s] - 1 of full[s]
+        for (int s = 0; s < S; ++s)
             if (s_issued[s] > 0) mbar_wait(&full[s], (s_issued[s] - 1) & 1);
     }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// W_X[n][k] (bf16) from the FP64 blocks: [Vc][N = 2 ncd][K = 9 * 2 ncd], and
-// (Wlo nullable) the rounding remainder bf16(v - W)
-__global__ void k_build_w(const double2 *Dc, bf16 *W, bf16 *Wlo, int Vc, int ncd) {
-    const long N = 2L * ncd, K = 18L * ncd;
-    const long tot = (long)Vc * N * K;
+// position of entry t (0..15) of row r in a 32-byte-swizzled tile of 32-byte
+// rows: the 16-byte unit t / 8 moves to unit (t / 8) ^ ((r >> 2) & 1)
+__device__ __forceinline__ int sw32(int r, int t) { return r * 16 + ((((t >> 3) ^ (r >> 2)) & 1) << 3) + (t & 7); }
+
+// The block operand B (bf16) from the FP64 blocks: [Vc][9][G][2 ncd][16] in
+// the tile image; tile (X, b, g), row n, entry t: Re A_b[n][16 g + t] for
+// n < ncd, Im A_b[n - ncd][16 g + t] beyond; and (Blo nullable) the rounding
+// remainders bf16(v - B)
+__global__ void k_build_b(const double2 *Dc, bf16 *B, bf16 *Blo, int Vc, int ncd) {
+    const int G = ncd / 16, N = 2 * ncd;
+    const long tot = (long)Vc * 9 * G * N * 16;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
-        const long k = e % K, n = (e / K) % N, X = e / (N * K);
-        const int b = (int)(k / (2 * ncd)), j = (int)((k % (2 * ncd)) / 2), cin = (int)(k & 1);
-        const int i = (int)(n / 2), cout = (int)(n & 1);
+        const int t = (int)(e & 15);
+        const long row = e >> 4;
+        const int n = (int)(row % N);
+        const long tile = row / N;                           // (X, b, g)
+        const int g = (int)(tile % G), b = (int)((tile / G) % 9);
+        const long X = tile / (9 * G);
+        const int i = n < ncd ? n : n - ncd, j = g * 16 + t;
         const double2 a = Dc[(((size_t)X * 9 + b) * ncd + i) * ncd + j];
-        double v;
-        if (cout == 0) v = cin == 0 ? a.x : -a.y;
-        else v = cin == 0 ? a.y : a.x;
+        const double v = n < ncd ? a.x : a.y;
         const bf16 hi = __double2bfloat16(v);
-        W[e] = hi;
-        if (Wlo) Wlo[e] = __double2bfloat16(v - (double)__bfloat162float(hi));
+        const size_t o = (size_t)tile * N * 16 + sw32(n, t);
+        B[o] = hi;
+        if (Blo) Blo[o] = __double2bfloat16(v - (double)__bfloat162float(hi));
     }
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static void *fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            fn = nullptr;
+// FP32 coarse field [rhs][Vc][ncd] complex -> the input operand P (bf16) in
+// the tile image: per site and 16-dof group, per RHS tile of 128 (the last
+// one's rows rounded up to 8), the Re tile and then the Im tile of its rows;
+// and (lo nullable) the rounding remainders.  Rows past nrhs stay unwritten.
+__global__ void k_to_planar(const float2 *x, bf16 *p, bf16 *plo, int nrhs, int Vc, int ncd) {
+    const long n = (long)nrhs * Vc * ncd;
+    const int G = ncd / 16, nrhs8 = (nrhs + 7) & ~7;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ncd);
+        const long v = (e / ncd) % Vc;
+        const int r = (int)(e / ((long)ncd * Vc));
+        const int r0 = r & ~(TC_M - 1), rows = min(TC_M, nrhs8 - r0);
+        const float2 z = x[e];
+        const size_t tre = (((size_t)v * G + (j >> 4)) * nrhs8 + r0) * 2 * 16;
+        const size_t ore = tre + sw32(r - r0, j & 15), oim = ore + (size_t)rows * 16;
+        const bf16 re = __float2bfloat16(z.x), im = __float2bfloat16(z.y);
+        p[ore] = re;
+        p[oim] = im;
+        if (plo) {
+            plo[ore] = __float2bfloat16(z.x - __bfloat162float(re));
+            plo[oim] = __float2bfloat16(z.y - __bfloat162float(im));
+        }
     }
-    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
 }
 
-static size_t tc_smem(int N, bool split) {
-    return 1024 + TC_STAGES * (split ? 2 : 1) * ((size_t)TC_M * TC_KC * 2 + (size_t)N * TC_KC * 2) +
-           (2 * TC_STAGES + 1) * 8 + 16;
-}
-
-// FP32 coarse field -> BF16 pair: hi = bf16(x), lo = bf16(x - hi)
-__global__ void k_split_bf16(const float *x, bf16 *hi, bf16 *lo, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const float v = x[i];
-        const bf16 h = __float2bfloat16(v);
-        hi[i] = h;
-        lo[i] = __float2bfloat16(v - __bfloat162float(h));
-    }
+static size_t tc_smem(int NC, bool split) {
+    const size_t q = split ? 2 : 1;
+    const int S = tc_stages(NC, split);
+    return 1024 + S * q * TC_CPS * (2 * (size_t)TC_M * TC_KC * 2 + (size_t)2 * NC * TC_KC * 2) + (2 * S + 5) * 8 + 16;
 }
 
 bool coarse_tc_ok(wd_ctx *c) { return c->mg && c->mg->Wtc != nullptr; }
@@ -291,15 +411,19 @@ bool coarse_tc_ok(wd_ctx *c) { return c->mg && c->mg->Wtc != nullptr; }
 int coarse_tc_build(wd_ctx *c) {
     wd_mg *g = c->mg;
     const int ncd = g->ncd;
-    // tensor-core shapes: N = 2 ncd in {96, 192} (multiple of 32 for the 64-byte K chunks, <= 256)
-    if (!((2 * ncd) % TC_KC == 0 && (2 * ncd == 96 || 2 * ncd == 192)) || !encode_fn()) return WD_OK;
-    const size_t n = (size_t)g->Vc * 2 * ncd * 18 * ncd;
+    // tensor-core shapes: ncd in {48, 96} (16-dof groups, MMA N = 2 ncd <= 256)
+    if (!(ncd == 48 || ncd == 96)) return WD_OK;
+    const size_t n = (size_t)g->Vc * ncd * 18 * ncd;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g->tc_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g->tc_sms <= 0)
+        g->tc_sms = 148;
     if (cudaMalloc(&g->Wtc, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wtc = nullptr; return WD_OK; }
     if (cudaMalloc(&g->Wlo, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wlo = nullptr; }
     int *err;
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
     WD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->st));
-    k_build_w<<<1184, 256, 0, c->st>>>(g->Dc, (bf16 *)g->Wtc, (bf16 *)g->Wlo, g->Vc, ncd);
+    k_build_b<<<1184, 256, 0, c->st>>>(g->Dc, (bf16 *)g->Wtc, (bf16 *)g->Wlo, g->Vc, ncd);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
@@ -310,68 +434,38 @@ int coarse_tc_apply(wd_ctx *c, const void *x_in, float *y, int nrhs, bool split)
     if (!g || !g->Wtc) { set_error("tensor-core coarse stencil unavailable"); return WD_ENOTSUP; }
     if (nrhs <= 0) return WD_OK;
     if (split && !g->Wlo) { set_error("tensor-core coarse stencil: no block remainders"); return WD_ENOTSUP; }
-    const int N = 2 * g->ncd, K = 9 * N;
-    // split: x_in is an FP32 field, split here into a BF16 pair
-    const void *x_bf16 = x_in, *x_lo = x_in;
-    if (split) {
-        void *hi, *lo;
-        const long n = (long)nrhs * g->Vc * N;
-        WD_TRY(ws_get(c, "tc.xhi", (size_t)n * sizeof(bf16), &hi));
-        WD_TRY(ws_get(c, "tc.xlo", (size_t)n * sizeof(bf16), &lo));
-        k_split_bf16<<<1184, 256, 0, c->st>>>((const float *)x_in, (bf16 *)hi, (bf16 *)lo, n);
-        c->launches++;
-        x_bf16 = hi;
-        x_lo = lo;
-    }
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    CUtensorMap mx, mx2, mw, mw2;
-    for (int q = 0; q < (split ? 2 : 1); ++q) {
-        const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)g->Vc, (cuuint64_t)nrhs};
-        const cuuint64_t strides[2] = {(cuuint64_t)N * 2, (cuuint64_t)g->Vc * N * 2};
-        const cuuint32_t box[3] = {TC_KC, 1, TC_M};
-        const cuuint32_t es[3] = {1, 1, 1};
-        CUresult r = enc(q ? &mx2 : &mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)(q ? x_lo : x_bf16), dims, strides,
-                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (coarse field) failed: %d", (int)r); return WD_ECUDA; }
-    }
-    if (!split) mx2 = mx;
-    {
-        const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)g->Vc * N};
-        const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-        const cuuint32_t box[2] = {TC_KC, (cuuint32_t)N};
-        const cuuint32_t es[2] = {1, 1};
-        CUresult r = enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g->Wtc, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (blocks) failed: %d", (int)r); return WD_ECUDA; }
-        mw2 = mw;
-        if (split) {
-            r = enc(&mw2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g->Wlo, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (block remainders) failed: %d", (int)r); return WD_ECUDA; }
-        }
-    }
+    const int NC = g->ncd;
+    // the planar BF16 input (and its remainders when split)
+    void *pl[2] = {nullptr, nullptr};
+    const int nrhs8 = (nrhs + 7) & ~7;
+    const long nel = (long)nrhs8 * g->Vc * 2 * NC;
+    WD_TRY(ws_get(c, "tc.p", (size_t)nel * sizeof(bf16), &pl[0]));
+    if (split) WD_TRY(ws_get(c, "tc.plo", (size_t)nel * sizeof(bf16), &pl[1]));
+    k_to_planar<<<1184, 256, 0, c->st>>>((const float2 *)x_in, (bf16 *)pl[0], (bf16 *)pl[1], nrhs, g->Vc, NC);
+    c->launches++;
     int *err;
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
     TcArgs A;
     A.nbr = g->nbr; A.y = y; A.err = err; A.Vc = g->Vc; A.ncd = g->ncd; A.nrhs = nrhs;
+    A.P = (const bf16 *)pl[0]; A.Plo = split ? (const bf16 *)pl[1] : A.P;
+    A.B = (const bf16 *)g->Wtc; A.Blo = split ? (const bf16 *)g->Wlo : A.B;
+    A.nitems = g->Vc * ((nrhs + TC_M - 1) / TC_M);
+    A.nrhs8 = nrhs8;
     {
         const char *e = getenv("WD_TEST_TC_STALL");
         A.stall_test = e && atoi(e) == 1;
     }
-    const unsigned grid = (unsigned)g->Vc * ((nrhs + TC_M - 1) / TC_M);
-    const size_t smem = tc_smem(N, split);
+    const unsigned grid = (unsigned)std::min(A.nitems, g->tc_sms);
+    const size_t smem = tc_smem(NC, split);
     int slot;
     // algorithmic flops: 8 ncd^2 per block, 9 blocks, per site and RHS
     prof_begin(c, WD_K_COARSE, 8.0 * g->ncd * g->ncd * 9.0 * g->Vc * nrhs, &slot);
 #define WD_TC_CASE(NN, SP)                                                                                 \
-    if (N == NN && split == SP) {                                                                          \
+    if (NC == NN && split == SP) {                                                                         \
         WD_CUDA(cudaFuncSetAttribute(k_coarse_tc<NN, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_coarse_tc<NN, SP><<<grid, 128, smem, c->st>>>(mx, mx2, mw, mw2, A);                              \
+        k_coarse_tc<NN, SP><<<grid, TC_THREADS, smem, c->st>>>(A);          \
     }
-    WD_TC_CASE(96, false) WD_TC_CASE(96, true) WD_TC_CASE(192, false) WD_TC_CASE(192, true)
+    WD_TC_CASE(48, false) WD_TC_CASE(48, true) WD_TC_CASE(96, false) WD_TC_CASE(96, true)
 #undef WD_TC_CASE
     prof_end(c, slot);
     c->launches++;

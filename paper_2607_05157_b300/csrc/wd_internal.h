@@ -176,8 +176,9 @@ struct wd_mg {
     double2 *P;        // [2][Vh][12][nv]
     double2 *Dc;       // [Vc][9][ncd][ncd]
     int *nbr;          // [Vc][9]
-    void *Wtc;         // tensor-core operand (bf16), built by wd_coarse_tc.cu
+    void *Wtc;         // tensor-core block operand (bf16): [Vc][9 ncd/16][ncd][32], built by wd_coarse_tc.cu
     void *Wlo;         // its rounding remainder (bf16): Wtc + Wlo carries ~16 significant bits
+    int tc_sms;        // SMs of the device (one persistent tensor-core CTA each)
     float2 *Dc32;      // [Vc][9][ncd][ncd] complex64 copy for the FP32 CUDA-core path
     float2 *Dclo;      // Dc - Dc32 as complex64: with Dc32 the double-float blocks of the FP64 residual
     float2 *Phi, *Plo; // P as double-float pairs (FP32 copy and remainder), for the prolongation

@@ -900,8 +900,8 @@ int mg_contract_rt(wd_ctx *c, const double *Rt, const double *y, int gamma5, int
     return WD_OK;
 }
 
-// split = false: x a BF16 field; true: x an FP32 field, split into a BF16
-// pair and multiplied with the blocks as BF16 pairs (~16 significant bits)
+// x an FP32 coarse field; split = false: x and the blocks rounded to BF16;
+// true: both as BF16 pairs (hi + lo, ~16 significant bits)
 int coarse_tc_apply(wd_ctx *c, const void *x, float *y, int nrhs, bool split = false);   // wd_coarse_tc.cu
 int coarse_tc_check(wd_ctx *c);
 int coarse_tc_build(wd_ctx *c);
@@ -913,14 +913,10 @@ static int cop64(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
 static int cop32(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
     return coarse_apply32(c, (const float *)in, (float *)out, nrhs);
 }
-// inner operators of the mixed coarse solves on the tensor cores: BF16
-// Krylov vectors and blocks (good to ~4e-3), or (split) FP32 Krylov vectors
-// and blocks both as BF16 pairs (hi + lo, ~16 significant bits), so that an
-// inner solve can go to 1e-5 and the outer loop needs two FP64 residuals
-// instead of four or five
-static int coptc(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
-    return coarse_tc_apply(c, in, (float *)out, nrhs, false);
-}
+// inner operator of the mixed coarse solves on the tensor cores: FP32 Krylov
+// vectors, the vectors and the blocks both multiplied as BF16 pairs (hi + lo,
+// ~16 significant bits), so that an inner solve can go to 1e-5 and the outer
+// loop needs two FP64 residuals instead of four or five
 static int coptc_split(wd_ctx *c, const void *in, void *out, int nrhs, void *) {
     return coarse_tc_apply(c, in, (float *)out, nrhs, true);
 }
@@ -943,18 +939,16 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
     Problem P;
     P.sp = sp;
     P.op64 = cop64; P.u64 = nullptr;
-    // mixed: BF16 operands on tensor cores when available (both mixed modes feed
-    // the tensor cores BF16 operands; FP32 mode falls back to FP32 CUDA cores
-    // only when the tensor-core operand could not be built)
-    const bool tc = prec != P64 && coarse_tc_ok(c);
-    const bool split = tc && c->mg->Wlo;
-    P.oplo = split ? coptc_split : tc ? coptc : cop32; P.ulo = nullptr;
+    // mixed: BF16-pair operands on the tensor cores when available, else the
+    // FP32 blocks on the CUDA cores
+    const bool tc = prec != P64 && coarse_tc_ok(c) && c->mg->Wlo;
+    P.oplo = tc ? coptc_split : cop32; P.ulo = nullptr;
     // the FP64 residuals of the mixed solves in double-float arithmetic, as on
     // the fine lattice (~2^-44 normwise), unless the tolerance asks for more
     int use_dd = prec != P64 && tol >= 1e-12 && c->outer == PDD;
     P.res64 = cres64; P.ures = &use_dd;
     P.tag = "coarse";
-    const int inner = tc && !split ? P16 : P32;
+    const int inner = P32;
     std::vector<int> iters;
     std::vector<double> last;
     int s = dc_solve(c, P, b, x, nrhs, bn2, bnorm2, tol, prec == P64 ? P64 : inner, max_iter, iters, last);
@@ -1080,12 +1074,14 @@ extern "C" int wd_coarse_apply(wd_ctx *c, const double *in, double *out, int nrh
     if (nrhs == 0) return WD_OK;
     if (prec == P64) return coarse_apply64(c, in, out, nullptr, 0.0, 1.0, nrhs);
     const Space sp = coarse_space(c);
-    const bool tc = coarse_tc_ok(c);
+    // WD_MIXED_FP32: BF16-pair operands, WD_MIXED_BF16: BF16 operands on the
+    // tensor cores; the FP32 blocks on the CUDA cores where those are unavailable
+    const bool tc = coarse_tc_ok(c) && (prec == P16 || c->mg->Wlo);
     void *xl, *yl;
-    WD_TRY(ws_get(c, "ca.x", space_bytes(sp, tc ? P16 : P32, nrhs), &xl));
+    WD_TRY(ws_get(c, "ca.x", space_bytes(sp, P32, nrhs), &xl));
     WD_TRY(ws_get(c, "ca.y", space_bytes(sp, P32, nrhs), &yl));
-    WD_TRY(blas_copy_convert(c, sp, P64, in, tc ? P16 : P32, xl, nrhs, nullptr));
-    if (tc) WD_TRY(coarse_tc_apply(c, xl, (float *)yl, nrhs));
+    WD_TRY(blas_copy_convert(c, sp, P64, in, P32, xl, nrhs, nullptr));
+    if (tc) WD_TRY(coarse_tc_apply(c, xl, (float *)yl, nrhs, prec == P32));
     else WD_TRY(coarse_apply32(c, (const float *)xl, (float *)yl, nrhs));
     WD_TRY(blas_copy_convert(c, sp, P32, yl, P64, out, nrhs, nullptr));
     if (tc) WD_TRY(coarse_tc_check(c));

@@ -20,9 +20,10 @@ TOL = {0: 1e-13, 1: 3e-6, 2: 2e-2, 3: 1e-12}
 # computed from the same FP32 input): the FP32 copy of each link (2^-24) and
 # at most ~20 rounded operations along any product-and-sum chain of an output
 # (spin projection, SU(3) row, reconstruction, 8 directions, the final
-# a w + b H psi): 24 * 2^-24.  BF16 storage of links and input: 2^-9 each per
-# product (2 * 2^-9) plus the FP32 arithmetic.
-ELEM_U = {1: 24 * 2.0 ** -24, 2: 2 * 2.0 ** -9 + 24 * 2.0 ** -24}
+# a w + b H psi): 24 * 2^-24.  BF16 storage of links and input (8 significant
+# bits, unit roundoff 2^-8 each): 2 * 2^-8 + 2^-16 per product plus the FP32
+# arithmetic.
+ELEM_U = {1: 24 * 2.0 ** -24, 2: 2 * 2.0 ** -8 + 2.0 ** -16 + 24 * 2.0 ** -24}
 
 
 def abs_stencil_bound(U, psi, kappa):

@@ -33,11 +33,22 @@ def _coarse_shape(dims, agg, nv, nrhs):
 
 
 # Element-wise bound factor of the tensor-core coarse stencil against the FP64
-# operator: BF16 operands (blocks and input rounded to nearest, 2^-9 each, so
-# 2^-8 per product), FP32 accumulation of at most 9 blocks x 2 x 96 real
-# products (gamma_n, n <= 1728, 2^-24 each), and a factor 2 for splitting each
-# complex product into its real terms: |y - ref| <= U_TC * sum_b |A_b| |x|.
-U_TC = 2 * (2.0 ** -8 + 1728 * 2.0 ** -24)
+# operator, per output component: BF16 operands (blocks and input rounded to
+# nearest, unit roundoff u = 2^-8 each; the input first rounded to FP32), so
+# 2u + u^2 + 2^-24 <= 2^-7 + 2^-15 per real product; |Re a Re x| + |Im a Im x|
+# <= |a| |x| per complex product; FP32 accumulation of the 9 x 2 x 48 = 864
+# real products of one component, gamma_n taken twice (1728 * 2^-24) for an
+# accumulation order that is not IEEE pairwise:
+#   |y - ref| <= U_TC * sum_b |A_b| |x|.
+U_TC = 2.0 ** -7 + 2.0 ** -15 + 1728 * 2.0 ** -24
+# The same with BF16-pair operands (WD_MIXED_FP32: v = hi + lo, lo the BF16
+# rounding of v - hi, so |v - hi - lo| <= u^2 |v| = 2^-16 |v|): hi hi + lo hi +
+# hi lo misses lo lo and the two representation errors, 3 * 2^-16 + 2^-24 <=
+# 2^-14 per product, and accumulates 3 x 864 products (5184 * 2^-24 taken
+# twice).  A dropped remainder product would leave a normwise error near
+# 2^-9, far above the normwise limit REL_SPLIT.
+U_SPLIT = 2.0 ** -14 + 5184 * 2.0 ** -24
+REL_SPLIT = 5e-5
 
 
 def _coarse_nbr(cd):
@@ -115,18 +126,22 @@ def test_transfer_and_coarse_operator(dims, agg, nv):
     for r in range(3):
         assert rel(rc[r].reshape(-1), P.conj().T @ v[r].reshape(-1)) < 1e-12
         assert rel(pf[r].reshape(-1), P @ yc[r].reshape(-1)) < 1e-12
-    # coarse operator, FP64 and mixed (BF16 tensor-core or FP32 operands), the
-    # mixed one element by element against U_TC |D_c| |x|
+    # coarse operator, FP64 and mixed (tensor cores with BF16-pair or BF16
+    # operands, or FP32 blocks), the mixed ones element by element against
+    # U_SPLIT |D_c| |x| and U_TC |D_c| |x|
     y64 = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
-    ylo = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    ysp = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    ybf = wd_coarse_apply(ctx.h, to_dev(yc), torch.empty(cs, dtype=torch.complex128, device='cuda'), 2).cpu().numpy()
     Dabs = Dc.copy()
     Dabs.data = np.abs(Dabs.data)
     for r in range(3):
         ref = Dc @ yc[r].reshape(-1)
         assert rel(y64[r].reshape(-1), ref) < 1e-12
-        assert rel(ylo[r].reshape(-1), ref) < 2e-2
+        assert rel(ysp[r].reshape(-1), ref) < REL_SPLIT
+        assert rel(ybf[r].reshape(-1), ref) < 2e-2
         bound = Dabs @ np.abs(yc[r].reshape(-1))
-        assert np.all(np.abs(ylo[r].reshape(-1) - ref) <= U_TC * bound)
+        assert np.all(np.abs(ysp[r].reshape(-1) - ref) <= U_SPLIT * bound)
+        assert np.all(np.abs(ybf[r].reshape(-1) - ref) <= U_TC * bound)
     ctx.close()
 
 
@@ -259,7 +274,7 @@ def test_gpu_test_vectors_give_orthonormal_prolongator():
 
 
 def test_tensor_core_coarse_stencil_16x16x16x32():
-    """tcgen05 coarse stencil (BF16 operands, FP32 accumulate) on the 16^3 x 32
+    """tcgen05 coarse stencil (BF16 and BF16-pair operands, FP32 accumulate) on the 16^3 x 32
     lattice with 4^4 aggregates and 24 test vectors (48 x 48 blocks, 512 coarse
     sites), 130 right-hand sides (a full and a ragged 128-row tile).  Sampled
     RHS are checked against the oracle's P^dag D P x computed as restriction of
@@ -274,7 +289,8 @@ def test_tensor_core_coarse_stencil_16x16x16x32():
     cs = _coarse_shape(dims, agg, nv, 130)
     rng = np.random.default_rng(12)
     x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
-    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 2).cpu().numpy()
+    ysp = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
     y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
     P = multigrid.prolongator(tv, dims, agg)
     shape = synth.spinors(dims, 1, 0).shape[1:]
@@ -287,10 +303,12 @@ def test_tensor_core_coarse_stencil_16x16x16x32():
         # BF16 operands leave a ~1e-3 error floor: proves the tensor-core path ran
         # (the FP32 CUDA-core fallback would sit near 1e-7)
         assert 1e-5 < err < 2e-2, err
+        assert rel(ysp[r].reshape(-1), ref) < REL_SPLIT
     # every element of every RHS against the probed blocks
     for r in range(x.shape[0]):
         bound = _coarse_abs_bound(A, nbr, x[r])
         assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
+        assert np.all(np.abs(ysp[r] - y64[r]) <= U_SPLIT * bound), r
     ctx.close()
 
 
@@ -298,7 +316,8 @@ def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
     """The two-level workload's coarse lattice (24^3 x 48, 4^4 aggregates, 24
     test vectors: 2592 coarse sites of 48 x 48 blocks), 200 RHS (a full and a
     ragged 128-row tile): every element of sampled RHS against the FP64 coarse
-    operator within U_TC |A| |x|, the blocks probed from that operator."""
+    operator within U_TC |A| |x| (BF16) and U_SPLIT |A| |x| (BF16 pairs), the
+    blocks probed from that operator."""
     import torch
     from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply
     dims, agg, nv = (24, 24, 24, 48), (4, 4, 4, 4), 24
@@ -307,13 +326,16 @@ def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
     cs = _coarse_shape(dims, agg, nv, 200)
     rng = np.random.default_rng(13)
     x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
-    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 2).cpu().numpy()
+    ysp = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
     y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
     A, nbr = _coarse_blocks(ctx, [L // a for L, a in zip(dims, agg)], 2 * nv)
     for r in (0, 1, 64, 127, 128, 199):
         bound = _coarse_abs_bound(A, nbr, x[r])
         assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
         assert 1e-5 < rel(y[r], y64[r]) < 2e-2
+        assert np.all(np.abs(ysp[r] - y64[r]) <= U_SPLIT * bound), r
+        assert rel(ysp[r], y64[r]) < REL_SPLIT
     ctx.close()
 
 
