@@ -867,8 +867,16 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
 
 int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, double *yc, int nrhs) {
     const MgGeom M = mg_geom(c);
-    constexpr int RT = 8;
+    // RHS per thread: each P entry is read once per RT RHS.  Measured on the
+    // 24^3x48 two-level step (64 level-1 samples): 8 is fastest; 16 and 32
+    // lose more to register pressure than they gain in P traffic
+    int RT = 8;
+    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 8, 16 or 32
+        const int r = atoi(e);
+        if (r == 8 || r == 16 || r == 32) RT = r;
+    }
     const long n = (long)((nrhs + RT - 1) / RT) * M.Vc * M.agg[3] * M.ncd;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
     if (c->outer == PDD && c->mg->Phi) {
         void *ved, *vod;
         const long nf = 12L * M.g.Vh * nrhs;
@@ -876,12 +884,18 @@ int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, 
         WD_TRY(ws_get(c, "mg.vodd", (size_t)nf * sizeof(float4), &vod));
         WD_CUDA(launch_to_ddl(ve, ved, nf, c->st));
         WD_CUDA(launch_to_ddl(vo, vod, nf, c->st));
-        k_restrict_t<true, RT><<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(nullptr, c->mg->Phi, c->mg->Plo, ved,
-                                                                               vod, (double2 *)Rt, M, nrhs);
+#define WD_RT_CASE(R)                                                                                          \
+        if (RT == R)                                                                                           \
+            k_restrict_t<true, R><<<blocks, 128, 0, c->st>>>(nullptr, c->mg->Phi, c->mg->Plo, ved, vod, (double2 *)Rt, M, nrhs);
+        WD_RT_CASE(8) WD_RT_CASE(16) WD_RT_CASE(32)
+#undef WD_RT_CASE
         c->launches += 3;
     } else {
-        k_restrict_t<false, RT><<<(unsigned)((n + 127) / 128), 128, 0, c->st>>>(c->mg->P, nullptr, nullptr, ve, vo,
-                                                                                (double2 *)Rt, M, nrhs);
+#define WD_RT_CASE(R)                                                                                          \
+        if (RT == R)                                                                                           \
+            k_restrict_t<false, R><<<blocks, 128, 0, c->st>>>(c->mg->P, nullptr, nullptr, ve, vo, (double2 *)Rt, M, nrhs);
+        WD_RT_CASE(8) WD_RT_CASE(16) WD_RT_CASE(32)
+#undef WD_RT_CASE
         c->launches++;
     }
     const long nc = (long)nrhs * M.Vc * M.ncd;

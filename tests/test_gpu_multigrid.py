@@ -165,11 +165,14 @@ def test_coarse_solve(prec):
 
 
 @pytest.mark.parametrize("gamma5", [0, 1])
-def test_mlmc2_per_sample(gamma5):
+@pytest.mark.parametrize("N1", [6, 40])
+def test_mlmc2_per_sample(gamma5, N1):
+    """Per-sample parity of both levels; N1 = 40 takes the 32-RHS restriction
+    tiles (a full and a ragged one)."""
     from paper_2607_05157_b300 import trace_estimate, wd_mlmc_level2_samples, WD_MLMC2
     dims, agg, nv = (4, 4, 4, 4), (2, 2, 2, 2), 6
     ctx, U, D, P = _setup(dims, agg, nv, kappa=0.12, seed=1001)
-    N1, N2 = 6, 10
+    N2 = 10
     r = trace_estimate(ctx.h, WD_MLMC2, 1, N1, dims[3], n2=N2, seed=2004, op=gamma5, prec=1, tol=1e-12,
                        with_samples=True)
     X2 = wd_mlmc_level2_samples(ctx.h, N2, dims[3])
