@@ -301,48 +301,94 @@ __global__ void k_restrict_t(const double2 *P, const float2 *Ph, const float2 *P
     const int nr = nrhs - r0 < RT ? nrhs - r0 : RT;
     const int h = i / M.nv, k = i % M.nv;
     const int ns3 = M.agg[0] * M.agg[1] * M.agg[2];
-    dd are[RT], aim[RT];
-    double2 acc[RT];
+    // origin of aggregate X at its timeslice tau; the sites of the aggregate
+    // timeslice are walked with an incremental (dx, dy, dz) counter, x fastest
+    int o[4];
+    {
+        int r = X;
+        for (int m = 0; m < 4; ++m) { o[m] = (r % M.cd[m]) * M.agg[m]; r /= M.cd[m]; }
+        o[3] += tau;
+    }
+    if constexpr (DD) {
+        // software-pipelined over the (site, component) pairs: the P entry and
+        // the RT field values of pair it + 1 are loaded before the arithmetic
+        // of pair it, so every thread keeps one pair of loads in flight
+        const size_t rstride = (size_t)12 * M.g.Vh;
+        dd are[RT], aim[RT];
 #pragma unroll
-    for (int q = 0; q < RT; ++q) { are[q] = dd_make(0.f, 0.f); aim[q] = dd_make(0.f, 0.f); acc[q] = make_double2(0, 0); }
-    for (int j3 = 0; j3 < ns3; ++j3) {
-        int c[4];
-        agg_site(M, X, j3 + ns3 * tau, c);
-        const int site = lex(M.g, c), par = (c[0] + c[1] + c[2] + c[3]) & 1, s = site >> 1;
-        for (int qc = 0; qc < 6; ++qc) {
-            const int comp = 6 * h + qc;
-            const size_t pi = (((size_t)par * M.g.Vh + s) * 12 + comp) * M.nv + k;
-            if constexpr (DD) {
-                const float2 mh = __ldg(Ph + pi), ml = __ldg(Pl + pi);
-                const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+        for (int q = 0; q < RT; ++q) { are[q] = dd_make(0.f, 0.f); aim[q] = dd_make(0.f, 0.f); }
+        int dx = 0, dy = 0, dz = 0, qc = 0;
+        float2 mh, ml;
+        float4 v[RT];
+        auto load_pair = [&](int ddx, int ddy, int ddz, int qq, float2 &ph, float2 &pl, float4 (&w)[RT]) {
+            const int c0 = o[0] + ddx, c1 = o[1] + ddy, c2 = o[2] + ddz;
+            const int site = c0 + M.g.X * (c1 + M.g.Y * (c2 + M.g.Z * o[3]));
+            const int par = (c0 + c1 + c2 + o[3]) & 1, sh = site >> 1;
+            const int comp = 6 * h + qq;
+            const size_t pi = (((size_t)par * M.g.Vh + sh) * 12 + comp) * M.nv + k;
+            ph = __ldg(Ph + pi);
+            pl = __ldg(Pl + pi);
+            const float4 *base = (const float4 *)(par ? vo : ve) + ((size_t)r0 * 12 + comp) * M.g.Vh + sh;
 #pragma unroll
-                for (int q = 0; q < RT; ++q) {
-                    if (q < nr) {
-                        const size_t fi = ((size_t)(r0 + q) * 12 + comp) * M.g.Vh + s;
-                        const float4 v = __ldg((const float4 *)(par ? vo : ve) + fi);
-                        const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
-                        dd_fma(are[q], mr, vr);  // conj(P) v
-                        dd_fma(are[q], mi, vi);
-                        dd_fma(aim[q], mr, vi);
-                        dd_fma(aim[q], -mi, vr);
-                    }
+            for (int q = 0; q < RT; ++q) w[q] = q < nr ? __ldg(base + q * rstride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        load_pair(0, 0, 0, 0, mh, ml, v);
+        const int nit = ns3 * 6;
+        for (int it = 0; it < nit; ++it) {
+            float2 nmh = mh, nml = ml;
+            float4 nv[RT];
+#pragma unroll
+            for (int q = 0; q < RT; ++q) nv[q] = v[q];
+            if (it + 1 < nit) {
+                if (++qc == 6) {
+                    qc = 0;
+                    if (++dx == M.agg[0]) { dx = 0; if (++dy == M.agg[1]) { dy = 0; ++dz; } }
                 }
-            } else {
-                const double2 pv = P[pi];
+                load_pair(dx, dy, dz, qc, nmh, nml, nv);
+            }
+            const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+#pragma unroll
+            for (int q = 0; q < RT; ++q) {
+                if (q < nr) {
+                    const dd vr = dd_make(v[q].x, v[q].z), vi = dd_make(v[q].y, v[q].w);
+                    dd_fma(are[q], mr, vr);  // conj(P) v
+                    dd_fma(are[q], mi, vi);
+                    dd_fma(aim[q], mr, vi);
+                    dd_fma(aim[q], -mi, vr);
+                }
+            }
+            mh = nmh; ml = nml;
+#pragma unroll
+            for (int q = 0; q < RT; ++q) v[q] = nv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < RT; ++q)
+            if (q < nr)
+                Rt[((((size_t)(r0 + q) * M.Vc + X) * at) + tau) * M.ncd + i] = make_double2(dd2d(are[q]), dd2d(aim[q]));
+    } else {
+        double2 acc[RT];
+#pragma unroll
+        for (int q = 0; q < RT; ++q) acc[q] = make_double2(0, 0);
+        for (int j3 = 0; j3 < ns3; ++j3) {
+            const int c0 = o[0] + j3 % M.agg[0], c1 = o[1] + (j3 / M.agg[0]) % M.agg[1];
+            const int c2 = o[2] + j3 / (M.agg[0] * M.agg[1]);
+            const int site = c0 + M.g.X * (c1 + M.g.Y * (c2 + M.g.Z * o[3]));
+            const int par = (c0 + c1 + c2 + o[3]) & 1, sh = site >> 1;
+            for (int qc = 0; qc < 6; ++qc) {
+                const int comp = 6 * h + qc;
+                const double2 pv = P[(((size_t)par * M.g.Vh + sh) * 12 + comp) * M.nv + k];
 #pragma unroll
                 for (int q = 0; q < RT; ++q)
                     if (q < nr) {
-                        const size_t fi = ((size_t)(r0 + q) * 12 + comp) * M.g.Vh + s;
+                        const size_t fi = ((size_t)(r0 + q) * 12 + comp) * M.g.Vh + sh;
                         acc[q] = zfma_conj(acc[q], pv, ((const double2 *)(par ? vo : ve))[fi]);
                     }
             }
         }
-    }
 #pragma unroll
-    for (int q = 0; q < RT; ++q)
-        if (q < nr)
-            Rt[((((size_t)(r0 + q) * M.Vc + X) * at) + tau) * M.ncd + i] =
-                DD ? make_double2(dd2d(are[q]), dd2d(aim[q])) : acc[q];
+        for (int q = 0; q < RT; ++q)
+            if (q < nr) Rt[((((size_t)(r0 + q) * M.Vc + X) * at) + tau) * M.ncd + i] = acc[q];
+    }
 }
 
 // yc[r][X][i] = sum_tau Rt[r][X][tau][i], tau ascending
@@ -868,12 +914,12 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
 int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, double *yc, int nrhs) {
     const MgGeom M = mg_geom(c);
     // RHS per thread: each P entry is read once per RT RHS.  Measured on the
-    // 24^3x48 two-level step (64 level-1 samples): 8 is fastest; 16 and 32
-    // lose more to register pressure than they gain in P traffic
+    // 24^3x48 two-level step (64 level-1 samples): 8 is fastest; 16 (and 32,
+    // which spills) lose more to register pressure than they gain in P traffic
     int RT = 8;
-    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 8, 16 or 32
+    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 8 or 16
         const int r = atoi(e);
-        if (r == 8 || r == 16 || r == 32) RT = r;
+        if (r == 8 || r == 16) RT = r;
     }
     const long n = (long)((nrhs + RT - 1) / RT) * M.Vc * M.agg[3] * M.ncd;
     const unsigned blocks = (unsigned)((n + 127) / 128);
@@ -887,14 +933,14 @@ int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, 
 #define WD_RT_CASE(R)                                                                                          \
         if (RT == R)                                                                                           \
             k_restrict_t<true, R><<<blocks, 128, 0, c->st>>>(nullptr, c->mg->Phi, c->mg->Plo, ved, vod, (double2 *)Rt, M, nrhs);
-        WD_RT_CASE(8) WD_RT_CASE(16) WD_RT_CASE(32)
+        WD_RT_CASE(8) WD_RT_CASE(16)
 #undef WD_RT_CASE
         c->launches += 3;
     } else {
 #define WD_RT_CASE(R)                                                                                          \
         if (RT == R)                                                                                           \
             k_restrict_t<false, R><<<blocks, 128, 0, c->st>>>(c->mg->P, nullptr, nullptr, ve, vo, (double2 *)Rt, M, nrhs);
-        WD_RT_CASE(8) WD_RT_CASE(16) WD_RT_CASE(32)
+        WD_RT_CASE(8) WD_RT_CASE(16)
 #undef WD_RT_CASE
         c->launches++;
     }
