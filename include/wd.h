@@ -242,8 +242,9 @@ const char *wd_last_error(void);
  * agg[4]: aggregate extents (must divide dims).  Each test vector is restricted
  * to each aggregate and chirality half (spins {0,1} / {2,3}) and
  * orthonormalised by modified Gram-Schmidt in test-vector order; coarse dof
- * index = 2*nv*Xc + nv*h + k.  Requires nv <= 6 * prod(agg) and 2*nv a
- * multiple of 8. */
+ * index = 2*nv*Xc + nv*h + k.  Requires nv a positive multiple of 6 with
+ * nv <= 6 * prod(agg) (else WD_EINVAL); WD_ENOTSUP when the 2nv x 2nv blocks
+ * or an aggregate of more than 4266 sites exceed the kernels' shared memory. */
 int wd_mg_setup(wd_ctx *ctx, const double *tv, int nv, const int agg[4], int tv_iters,
                 uint64_t seed);
 

@@ -111,48 +111,55 @@ __device__ double2 block_reduce_z(double2 v, double2 *sh) {
     return a;
 }
 
-// modified Gram-Schmidt of the nv columns of one (aggregate, half) block; one CTA per block
+// modified Gram-Schmidt of the nv columns of one (aggregate, half) block; one
+// CTA per block.  Each pass over the rows subtracts q_j from v_k and, in the
+// same pass, accumulates the next dot product q_{j+1}^dag v_k (or, after the
+// last j, |v_k|^2) from the updated rows: the arithmetic of sequential MGS in
+// its order, with half the passes.  Row offsets are computed once (shared
+// memory: 6 * sites-per-aggregate offsets).
 __global__ void k_block_mgs(double2 *P, MgGeom M) {
     __shared__ double2 sh[32];
+    extern __shared__ size_t roff[];
     const int X = blockIdx.x >> 1, h = blockIdx.x & 1;
     const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
     const int m = nsite * 6;
+    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+        int c[4];
+        agg_site(M, X, row / 6, c);
+        roff[row] = pidx(M, lex(M.g, c), 6 * h + row % 6, 0);
+    }
+    __syncthreads();
     for (int k = 0; k < M.nv; ++k) {
-        for (int j = 0; j < k; ++j) {
-            double2 d = make_double2(0, 0);
-            for (int row = threadIdx.x; row < m; row += blockDim.x) {
-                int c[4];
-                agg_site(M, X, row / 6, c);
-                const int comp = 6 * h + row % 6, site = lex(M.g, c);
-                d = zfma_conj(d, P[pidx(M, site, comp, j)], P[pidx(M, site, comp, k)]);
-            }
+        double2 d = make_double2(0, 0);
+        if (k > 0) {
+            for (int row = threadIdx.x; row < m; row += blockDim.x)
+                d = zfma_conj(d, P[roff[row]], P[roff[row] + k]);
             d = block_reduce_z(d, sh);
-            for (int row = threadIdx.x; row < m; row += blockDim.x) {
-                int c[4];
-                agg_site(M, X, row / 6, c);
-                const int comp = 6 * h + row % 6, site = lex(M.g, c);
-                double2 &q = P[pidx(M, site, comp, k)];
-                const double2 qj = P[pidx(M, site, comp, j)];
-                q.x -= d.x * qj.x - d.y * qj.y;
-                q.y -= d.x * qj.y + d.y * qj.x;
-            }
-            __syncthreads();
         }
         double2 nn = make_double2(0, 0);
-        for (int row = threadIdx.x; row < m; row += blockDim.x) {
-            int c[4];
-            agg_site(M, X, row / 6, c);
-            const int comp = 6 * h + row % 6, site = lex(M.g, c);
-            const double2 q = P[pidx(M, site, comp, k)];
-            nn.x += q.x * q.x + q.y * q.y;
+        for (int j = 0; j < k; ++j) {
+            // v_k -= d_j q_j; then d_{j+1} = q_{j+1}^dag v_k, or |v_k|^2 after the last j
+            double2 dn = make_double2(0, 0);
+            for (int row = threadIdx.x; row < m; row += blockDim.x) {
+                double2 &q = P[roff[row] + k];
+                const double2 qj = P[roff[row] + j];
+                q.x -= d.x * qj.x - d.y * qj.y;
+                q.y -= d.x * qj.y + d.y * qj.x;
+                if (j + 1 < k) dn = zfma_conj(dn, P[roff[row] + j + 1], q);
+                else dn.x += q.x * q.x + q.y * q.y;
+            }
+            if (j + 1 < k) d = block_reduce_z(dn, sh);
+            else nn = dn;
         }
+        if (k == 0)
+            for (int row = threadIdx.x; row < m; row += blockDim.x) {
+                const double2 q = P[roff[row]];
+                nn.x += q.x * q.x + q.y * q.y;
+            }
         nn = block_reduce_z(nn, sh);
         const double inv = 1.0 / sqrt(nn.x);
         for (int row = threadIdx.x; row < m; row += blockDim.x) {
-            int c[4];
-            agg_site(M, X, row / 6, c);
-            const int comp = 6 * h + row % 6, site = lex(M.g, c);
-            double2 &q = P[pidx(M, site, comp, k)];
+            double2 &q = P[roff[row] + k];
             q.x *= inv;
             q.y *= inv;
         }
@@ -509,6 +516,8 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
                 for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
                     const int comp = e / ncd, i = e % ncd, s = comp / 3, a = comp % 3;
                     double2 acc = make_double2(0, 0);
+                    // W is zero on the spins outside the half of i, and so is T1 there
+                    if ((s >> 1) != i / nv) { T1[e] = acc; continue; }
                     for (int bb = 0; bb < 3; ++bb) {
                         double2 ul = fwd ? u[3 * a + bb] : make_double2(u[3 * bb + a].x, -u[3 * bb + a].y);
                         acc = zfma(acc, ul, W[(3 * s + bb) * ncd + i]);
@@ -545,9 +554,10 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
         }
         __syncthreads();
         for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
-            const int i = e / ncd, jj = e % ncd;
+            const int i = e / ncd, jj = e % ncd, c0 = 6 * (i / nv);
             double2 acc = make_double2(0, 0);
-            for (int comp = 0; comp < 12; ++comp) acc = zfma_conj(acc, Px[comp * ncd + i], Ws[comp * ncd + jj]);
+            // Px[comp][i] vanishes outside the half of i: the 6 components of that half
+            for (int comp = c0; comp < c0 + 6; ++comp) acc = zfma_conj(acc, Px[comp * ncd + i], Ws[comp * ncd + jj]);
             A[e].x += acc.x;
             A[e].y += acc.y;
         }
@@ -1071,6 +1081,9 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     const int ncd = 2 * nv;
     const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 4 * 12 * ncd);
     if (smem > 227 * 1024) { set_error("wd_mg_setup: nv too large for the block assembly"); return WD_ENOTSUP; }
+    // the block orthonormalisation keeps the row offsets of one aggregate half in shared memory
+    const size_t mgs_smem = (size_t)6 * nsite * sizeof(size_t);
+    if (mgs_smem > 200 * 1024) { set_error("wd_mg_setup: aggregate of %d sites too large", nsite); return WD_ENOTSUP; }
     wd_mg_free(c);
     wd_mg *g = new wd_mg();
     memset(g, 0, sizeof(*g));
@@ -1102,7 +1115,8 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         WD_TRY(mg_generate_tv(c, nv, tv_iters, seed, tvd));
     }
     k_tv_to_P<<<(unsigned)((nP + 255) / 256), 256, 0, c->st>>>((const double2 *)tvd, g->P, M);
-    k_block_mgs<<<2 * g->Vc, 256, 0, c->st>>>(g->P, M);
+    WD_CUDA(cudaFuncSetAttribute(k_block_mgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mgs_smem));
+    k_block_mgs<<<2 * g->Vc, 256, mgs_smem, c->st>>>(g->P, M);
     k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
     k_gram_t<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->P, g->Gt, M);
     double2 hg[4][4][4];
