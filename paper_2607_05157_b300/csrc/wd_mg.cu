@@ -566,6 +566,146 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
     for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) Dc[((size_t)X * 9 + b) * ncd * ncd + e] = A[e];
 }
 
+// The same assembly in double-float arithmetic (FP32 pairs, ~2^-44 per
+// operation; the FP64 rate is a small fraction of the FP32 one): P read as its
+// FP32 pair copy (Ph + Pl), links split once per hop, the spin factor
+// (1 -/+ gamma_mu) applied exactly (its entries are 0, +-1, +-i: sign flips and
+// swaps), products and sums as in the FP64 kernel, in the same order.
+struct cdd { dd re, im; };
+__device__ __forceinline__ cdd cdd_zero() { cdd z; z.re = dd_make(0.f, 0.f); z.im = dd_make(0.f, 0.f); return z; }
+__device__ __forceinline__ dd f64_to_dd(double x) {
+    const float h = (float)x;
+    return dd_make(h, (float)(x - (double)h));
+}
+// acc += a b (conj_a: conj(a) b)
+template <bool CONJ_A>
+__device__ __forceinline__ void cdd_fma(cdd &acc, const cdd &a, const cdd &b) {
+    if (CONJ_A) {
+        dd_fma(acc.re, a.re, b.re); dd_fma(acc.re, a.im, b.im);
+        dd_fma(acc.im, a.re, b.im); dd_fma(acc.im, -a.im, b.re);
+    } else {
+        dd_fma(acc.re, a.re, b.re); dd_fma(acc.re, -a.im, b.im);
+        dd_fma(acc.im, a.re, b.im); dd_fma(acc.im, a.im, b.re);
+    }
+}
+
+__global__ void k_assemble_dd(const float2 *Ph, const float2 *Pl, const double2 *U, int4 bc, double kappa, double2 *Dc,
+                              MgGeom M) {
+    extern __shared__ cdd csm[];
+    const int ncd = M.ncd, nv = M.nv;
+    cdd *A = csm, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd, *Ws = T1 + 12 * ncd;
+    const int X = blockIdx.x / 9, b = blockIdx.x % 9;
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
+    const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
+    auto pload = [&](int site, int comp, int k) {
+        const size_t q = pidx(M, site, comp, k);
+        const float2 h = __ldg(Ph + q), l = __ldg(Pl + q);
+        cdd r;
+        r.re = dd_make(h.x, l.x);
+        r.im = dd_make(h.y, l.y);
+        return r;
+    };
+    for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) A[e] = cdd_zero();
+    for (int j = 0; j < nsite; ++j) {
+        int c[4];
+        agg_site(M, X, j, c);
+        const int xs = lex(M.g, c);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) Ws[e] = cdd_zero();
+        bool any = false;
+        for (int hop = -1; hop < 8; ++hop) {
+            int mu = hop & 3, fwd = hop < 4;
+            int y[4] = {c[0], c[1], c[2], c[3]};
+            double sgn = 1.0;
+            int blk;
+            if (hop < 0) { blk = 0; }
+            else {
+                const int inside_f = (c[mu] % M.agg[mu]) != M.agg[mu] - 1;
+                const int inside_b = (c[mu] % M.agg[mu]) != 0;
+                if (fwd) {
+                    y[mu] = c[mu] + 1 == L[mu] ? 0 : c[mu] + 1;
+                    if (c[mu] == L[mu] - 1) sgn = bcv[mu];
+                    blk = inside_f ? 0 : 1 + mu;
+                } else {
+                    y[mu] = c[mu] == 0 ? L[mu] - 1 : c[mu] - 1;
+                    if (c[mu] == 0) sgn = bcv[mu];
+                    blk = inside_b ? 0 : 5 + mu;
+                }
+            }
+            if (blk != b) continue;
+            any = true;
+            const int ys = lex(M.g, y);
+            __syncthreads();
+            for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                const int comp = e / ncd, i = e % ncd, h = i / nv, k = i % nv;
+                W[e] = (comp / 6) == h ? pload(ys, comp, k) : cdd_zero();
+            }
+            __syncthreads();
+            if (hop >= 0) {
+                const double2 *u = U + ((size_t)mu * M.g.V + (fwd ? xs : ys)) * 9;
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    const int comp = e / ncd, i = e % ncd, s = comp / 3, a = comp % 3;
+                    cdd acc = cdd_zero();
+                    if ((s >> 1) == i / nv) {   // W vanishes on the spins outside the half of i
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const double2 uv = fwd ? u[3 * a + bb] : u[3 * bb + a];
+                            cdd ul;
+                            ul.re = f64_to_dd(uv.x);
+                            ul.im = f64_to_dd(fwd ? uv.y : -uv.y);
+                            cdd_fma<false>(acc, ul, W[(3 * s + bb) * ncd + i]);
+                        }
+                    }
+                    T1[e] = acc;
+                }
+                __syncthreads();
+                // W = (1 -/+ gamma_mu) T1: gamma entries are 0, +-1, +-i
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    const int comp = e / ncd, i = e % ncd, s = comp / 3, a = comp % 3;
+                    cdd acc = T1[e];
+                    for (int sp = 0; sp < 4; ++sp) {
+                        double2 gv = c_gamma[mu][s][sp];
+                        if (fwd) { gv.x = -gv.x; gv.y = -gv.y; }
+                        const cdd t = T1[(3 * sp + a) * ncd + i];
+                        if (gv.x > 0.5) { acc.re = acc.re + t.re; acc.im = acc.im + t.im; }
+                        else if (gv.x < -0.5) { acc.re = acc.re - t.re; acc.im = acc.im - t.im; }
+                        if (gv.y > 0.5) { acc.re = acc.re - t.im; acc.im = acc.im + t.re; }
+                        else if (gv.y < -0.5) { acc.re = acc.re + t.im; acc.im = acc.im - t.re; }
+                    }
+                    W[e] = acc;
+                }
+                __syncthreads();
+                const dd coef = f64_to_dd(-kappa * sgn);
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    dd_fma(Ws[e].re, coef, W[e].re);
+                    dd_fma(Ws[e].im, coef, W[e].im);
+                }
+            } else {
+                for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+                    Ws[e].re = Ws[e].re + W[e].re;
+                    Ws[e].im = Ws[e].im + W[e].im;
+                }
+            }
+        }
+        if (!any) continue;
+        for (int e = threadIdx.x; e < 12 * ncd; e += blockDim.x) {
+            const int comp = e / ncd, i = e % ncd, h = i / nv, k = i % nv;
+            Px[e] = (comp / 6) == h ? pload(xs, comp, k) : cdd_zero();
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x) {
+            const int i = e / ncd, jj = e % ncd, c0 = 6 * (i / nv);
+            cdd acc = cdd_zero();
+            for (int comp = c0; comp < c0 + 6; ++comp) cdd_fma<true>(acc, Px[comp * ncd + i], Ws[comp * ncd + jj]);
+            A[e].re = A[e].re + acc.re;
+            A[e].im = A[e].im + acc.im;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncd * ncd; e += blockDim.x)
+        Dc[((size_t)X * 9 + b) * ncd * ncd + e] = make_double2(dd2d(A[e].re), dd2d(A[e].im));
+}
+
 __global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const float hr = (float)Dc[i].x, hi = (float)Dc[i].y;
@@ -1129,11 +1269,17 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         if (it == c->bufs.end()) { set_error("wd_mg_setup: links not resident"); return WD_ECUDA; }
         ulex = it->second.first;
     }
-    WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int4 bc = make_int4(c->bc[0], c->bc[1], c->bc[2], c->bc[3]);
-    k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
-    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
+    if (c->outer == PDD) {
+        // double-float Galerkin assembly (FP32 pairs; ~2^-44 per operation)
+        WD_CUDA(cudaFuncSetAttribute(k_assemble_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_assemble_dd<<<9 * g->Vc, 256, smem, c->st>>>(g->Phi, g->Plo, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
+    } else {
+        WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
+    }
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Gt, g->Ghi, g->Glo, (long)g->Vc * agg[3] * 2 * nv * nv);
     c->launches += 8;
     WD_CUDA(cudaGetLastError());
