@@ -302,23 +302,39 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
     return WD_OK;
 }
 
+// Mean and unbiased variance over the N samples of each timeslice t < T and of
+// their sum over t (t = T): one warp per t, lanes over the samples (lane l
+// takes l, l + 32, ...), combined by a fixed butterfly.
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 __global__ void k_mean_var2(const double *X, int N, int T, double *out_mean, double *out_var) {
-    for (int t = threadIdx.x; t <= T; t += blockDim.x) {
-        double mr = 0, mi = 0;
-        for (int i = 0; i < N; ++i) {
-            double xr = 0, xi = 0;
-            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
-            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
-            mr += xr; mi += xi;
-        }
-        mr /= N; mi /= N;
-        double v = 0;
-        for (int i = 0; i < N; ++i) {
-            double xr = 0, xi = 0;
-            if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
-            else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
-            v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
-        }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int t = blockIdx.x * nw + (threadIdx.x >> 5);
+    if (t > T) return;
+    auto sample = [&](int i, double &xr, double &xi) {
+        xr = 0; xi = 0;
+        if (t < T) { xr = X[((size_t)i * T + t) * 2]; xi = X[((size_t)i * T + t) * 2 + 1]; }
+        else for (int u = 0; u < T; ++u) { xr += X[((size_t)i * T + u) * 2]; xi += X[((size_t)i * T + u) * 2 + 1]; }
+    };
+    double mr = 0, mi = 0;
+    for (int i = lane; i < N; i += 32) {
+        double xr, xi;
+        sample(i, xr, xi);
+        mr += xr;
+        mi += xi;
+    }
+    mr = warp_sum_d(mr) / N;
+    mi = warp_sum_d(mi) / N;
+    double v = 0;
+    for (int i = lane; i < N; i += 32) {
+        double xr, xi;
+        sample(i, xr, xi);
+        v += (xr - mr) * (xr - mr) + (xi - mi) * (xi - mi);
+    }
+    v = warp_sum_d(v);
+    if (lane == 0) {
         out_mean[2 * t] = mr;
         out_mean[2 * t + 1] = mi;
         out_var[t] = N > 1 ? v / (N - 1) : 0.0;
@@ -326,7 +342,8 @@ __global__ void k_mean_var2(const double *X, int N, int T, double *out_mean, dou
 }
 
 static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double *var) {
-    k_mean_var2<<<1, 128, 0, c->st>>>(X, N, c->g.T, mean, var);
+    const int T = c->g.T;
+    k_mean_var2<<<(T + 1 + 7) / 8, 256, 0, c->st>>>(X, N, T, mean, var);
     c->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
