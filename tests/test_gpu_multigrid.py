@@ -51,6 +51,17 @@ U_SPLIT = 2.0 ** -14 + 5184 * 2.0 ** -24
 REL_SPLIT = 5e-5
 
 
+def u_tc(ncd):
+    """U_TC for blocks of ncd coarse dofs: 18 ncd real products per output
+    component (864 at ncd = 48, where it equals U_TC)."""
+    return 2.0 ** -7 + 2.0 ** -15 + 2 * 18 * ncd * 2.0 ** -24
+
+
+def u_split(ncd):
+    """U_SPLIT for blocks of ncd coarse dofs (3 x 18 ncd products)."""
+    return 2.0 ** -14 + 2 * 3 * 18 * ncd * 2.0 ** -24
+
+
 def _coarse_nbr(cd):
     """Neighbour table of the coarse torus, lexicographic (x fastest):
     [Vc][9] with 0 the site, 1 + mu the forward and 5 + mu the backward one."""
@@ -338,6 +349,33 @@ def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
         assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
         assert 1e-5 < rel(y[r], y64[r]) < 2e-2
         assert np.all(np.abs(ysp[r] - y64[r]) <= U_SPLIT * bound), r
+        assert rel(ysp[r], y64[r]) < REL_SPLIT
+    ctx.close()
+
+
+def test_tensor_core_coarse_stencil_96_dofs():
+    """The second shape of the tensor-core stencil: 48 test vectors (96 x 96
+    blocks, MMA N = 192, one accumulator set of 512 TMEM columns) on 12^4 with
+    4^4 aggregates (3^4 coarse sites), 70 RHS (one ragged tile): every element
+    of every RHS against the FP64 coarse operator within u_tc / u_split (96),
+    the blocks probed from that operator."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply
+    dims, agg, nv = (12, 12, 12, 12), (4, 4, 4, 4), 48
+    ctx = Context(dims, synth.gauge_field(dims, 0.5, 1006), 0.13, BC)
+    wd_mg_setup(ctx.h, synth.test_vectors(dims, nv, 79), nv, agg)
+    cs = _coarse_shape(dims, agg, nv, 70)
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 2).cpu().numpy()
+    ysp = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
+    A, nbr = _coarse_blocks(ctx, [L // a for L, a in zip(dims, agg)], 2 * nv)
+    for r in range(x.shape[0]):
+        bound = _coarse_abs_bound(A, nbr, x[r])
+        assert np.all(np.abs(y[r] - y64[r]) <= u_tc(2 * nv) * bound), r
+        assert np.all(np.abs(ysp[r] - y64[r]) <= u_split(2 * nv) * bound), r
+        assert 1e-5 < rel(y[r], y64[r]) < 2e-2
         assert rel(ysp[r], y64[r]) < REL_SPLIT
     ctx.close()
 
