@@ -142,14 +142,16 @@ static int tune_hop(wd_ctx *c, int pin, int pout, const HopArgs &A, bool dag, in
     // (21, 22, 24 = timeslices staged through shared memory; block size fixed by the kernel)
     // (31, 32 / 41, 42 = next-direction prefetch into L1 / L2)
     // (51, 52 = plain, site tile fastest in the block order; 62 = two RHS with
-    // registers capped for 20 resident warps per SM)
+    // registers capped for 20 resident warps per SM; 63-65 = the same with the
+    // RHS tiles in groups of 4, 8, 16)
     // (32-thread blocks: more blocks per SM for launches with few RHS)
-    const int Rs[15] = {1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 62}, Ts[4] = {32, 64, 128, 256};
+    const int Rs[18] = {1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 62, 63, 64, 65};
+    const int Ts[4] = {32, 64, 128, 256};
     cudaEvent_t e0, e1;
     WD_CUDA(cudaEventCreate(&e0));
     WD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int i = 0; i < 15; ++i)
+    for (int i = 0; i < 18; ++i)
         for (int j = 0; j < 4; ++j) {
             if (pin == P64 && Rs[i] > 2) continue;                   // FP64: R = 1, 2 only (R = 4 spills)
             if (is_dd(pin) && Rs[i] != 1 && Rs[i] != 2 && Rs[i] != 11 && Rs[i] != 12) continue;

@@ -397,11 +397,27 @@ __global__ void __launch_bounds__(256) hop_kernel_f2(HopArgs A) {
 // MINB), so that MINB CTAs of 128 threads fit per SM (more resident warps to
 // hide the neighbour-load latency, at the price of spills if the cap is
 // below what the body needs); site tile fastest in the block order
+// A.rhs_major = 1: all site tiles of one RHS tile, then the next RHS tile;
+// A.rhs_major = GR >= 2: RHS tiles in groups of GR, and within a group the GR
+// tiles of one site tile together, then the next site tile.  Grouping bounds
+// the links' DRAM traffic (re-read once per group instead of once per RHS
+// tile when the links exceed L2) while the inputs the group's resident blocks
+// need from the neighbouring timeslices still fit in L2.
 template <typename SIn, typename SOut, typename SW, typename G, int R, bool DAG, int MINB>
 __global__ void __launch_bounds__(128, MINB) hop_kernel_f2_cap(HopArgs A) {
-    const int nsb = gridDim.x / A.nrb;
-    const int rb = blockIdx.x / nsb;
-    const int s = (blockIdx.x % nsb) * blockDim.x + threadIdx.x;
+    const int nsb = (A.g.Vh + blockDim.x - 1) / blockDim.x;
+    int rb, sb;
+    if (A.rhs_major >= 2) {
+        const int GR = A.rhs_major, per = GR * nsb;
+        const int grp = blockIdx.x / per, rem = blockIdx.x - grp * per;
+        sb = rem / GR;
+        rb = grp * GR + (rem - sb * GR);
+        if (rb >= A.nrb) return;
+    } else {
+        rb = blockIdx.x / nsb;
+        sb = blockIdx.x - rb * nsb;
+    }
+    const int s = sb * blockDim.x + threadIdx.x;
     if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, false, 0>(A, rb, s);
 }
 
@@ -688,13 +704,18 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     // timeslices staged through shared memory (FP32 arithmetic only); R = 31,
     // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2; R = 51, 52,
     // 54: plain with the site tile fastest in the block order; R = 62: two RHS,
-    // registers capped for 20 resident warps per SM
+    // registers capped for 20 resident warps per SM; R = 63, 64, 65: the same
+    // with the RHS tiles in groups of 4, 8, 16 (site tile fastest within a group)
     constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
     if (R > 20 && R < 30) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
-    if (R == 62) {   // two RHS, register cap for 5 CTAs of 128 threads per SM, site tile fastest
+    if (R >= 62 && R <= 65) {   // two RHS, register cap for 5 CTAs of 128 threads per SM
+        // 62: site tile fastest; 63, 64, 65: RHS tiles in groups of 4, 8, 16
         if (!PACKED || threads > 128) return cudaErrorNotSupported;
         A.nrb = (A.nrhs + 1) / 2;
-        const dim3 grid((unsigned)(((A.g.Vh + threads - 1) / threads) * A.nrb));
+        const int nsb = (A.g.Vh + threads - 1) / threads;
+        A.rhs_major = R == 62 ? 1 : 1 << (R - 61);
+        const int GR = A.rhs_major, ngrp = (A.nrb + GR - 1) / GR;
+        const dim3 grid((unsigned)(R == 62 ? (long)nsb * A.nrb : (long)ngrp * GR * nsb));
         if constexpr (PACKED) {
             if (dag) hop_kernel_f2_cap<SIn, SOut, SW, G, 2, true, 5><<<grid, threads, 0, st>>>(A);
             else hop_kernel_f2_cap<SIn, SOut, SW, G, 2, false, 5><<<grid, threads, 0, st>>>(A);

@@ -1,5 +1,6 @@
 """Parity of every stencil launch variant of row a4 (plain, software-pipelined,
-timeslices staged through shared memory by bulk async copies) with the oracle,
+timeslices staged through shared memory by bulk async copies, register-capped
+with grouped RHS block orders) with the oracle,
 each forced through the launch-shape override, FP32 and BF16, D and D^dag, with
 a ragged RHS count, plus a mixed-precision solve on the staged variant."""
 import os
@@ -24,7 +25,7 @@ def override():
     os.environ.pop('WD_HOP_R', None)
 
 
-@pytest.mark.parametrize("code", [1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 54, 62])
+@pytest.mark.parametrize("code", [1, 2, 4, 11, 12, 21, 22, 24, 31, 32, 41, 42, 51, 52, 54, 62, 63, 64, "65:32", "63:128"])
 @pytest.mark.parametrize("prec,tol", [(1, 3e-6), (2, 2e-2)])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_variant_parity(override, code, prec, tol, dagger):
