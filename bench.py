@@ -87,6 +87,30 @@ def measured_peaks():
         return None
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# FP32 fine stencil in this step, averaged over the 52 launches of one profiled
+# step (ncu, one pass, full size; command and numbers in
+# profiles/hop_kernel_f2_fp32_24x24x24x48_step.md).  It holds for the stencil
+# sources it was taken with: their hash is checked, and the field is null once
+# they change.
+HOP32_TRAFFIC = {"sources": ("paper_2607_05157_b300/csrc/wd_dslash.cu", "paper_2607_05157_b300/csrc/wd_common.cuh",
+                             "paper_2607_05157_b300/csrc/wd_internal.h"),
+                 "sha256_16": "aaee79dd0ed0c56c", "bytes_per_launch": 6558.1e6,
+                 "algorithmic_bytes_per_launch": 4901.3e6}
+
+
+def hop32_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in HOP32_TRAFFIC["sources"]:
+            with open(os.path.join(ROOT, f), 'rb') as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return HOP32_TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == HOP32_TRAFFIC["sha256_16"] else None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
     Q = ('clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
@@ -645,7 +669,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None,
             "frac_of_spec_8000": achieved / SPEC_HBM_GBS if achieved else None,
-            "traffic": None, "kernel": kern[dom]["kernel"], "peak_source": "measured" if peaks else "fallback",
+            "traffic": hop32_traffic() if dom == "hop32" and args.prec == 'fp32' else None,
+            "kernel": kern[dom]["kernel"], "peak_source": "measured" if peaks else "fallback",
             "region": "profiled repetition of the timed steps (same seeds; plain launches bracketed by CUDA events)",
             "kernels": kern}
 
