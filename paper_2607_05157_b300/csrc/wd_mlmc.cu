@@ -352,9 +352,12 @@ static int mean_var_dev(wd_ctx *c, const double *X, int N, double *mean, double 
 // ---- test vectors: tv_iters inverse iterations v <- D^{-1} v / |v| from Rademacher starts
 __global__ void k_scale_by(double *f, const double *n2a, const double *n2b, long per_rhs, int nrhs) {
     const long n = per_rhs * nrhs;
+    int rc = -1;
+    double sc = 0.0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const int r = (int)(i / per_rhs);
-        f[i] *= 1.0 / sqrt(n2a[r] + n2b[r]);
+        if (r != rc) { rc = r; sc = 1.0 / sqrt(n2a[r] + n2b[r]); }   // once per vector a thread enters
+        f[i] *= sc;
     }
 }
 
