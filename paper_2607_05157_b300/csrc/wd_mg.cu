@@ -196,6 +196,44 @@ __global__ void k_gram_t(const double2 *P, double2 *Gt, MgGeom M) {
     }
 }
 
+// The same Gram matrices in double-float arithmetic from the FP32 pair copy of
+// P (Ph + Pl), the sites of the aggregate timeslice walked with an incremental
+// counter (the FP64 rate is a small fraction of the FP32 one)
+__global__ void k_gram_t_dd(const float2 *Ph, const float2 *Pl, double2 *Gt, MgGeom M) {
+    const int at = M.agg[3], nv = M.nv;
+    const int b = blockIdx.x;                        // (X * at + tau) * 2 + h
+    const int h = b & 1, tau = (b >> 1) % at, X = (b >> 1) / at;
+    int o[4];
+    {
+        int r = X;
+        for (int m = 0; m < 4; ++m) { o[m] = (r % M.cd[m]) * M.agg[m]; r /= M.cd[m]; }
+        o[3] += tau;
+    }
+    for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) {
+        const int k = e / nv, l = e % nv;
+        dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
+        for (int dz = 0; dz < M.agg[2]; ++dz)
+            for (int dy = 0; dy < M.agg[1]; ++dy)
+                for (int dx = 0; dx < M.agg[0]; ++dx) {
+                    const int c0 = o[0] + dx, c1 = o[1] + dy, c2 = o[2] + dz;
+                    const int site = c0 + M.g.X * (c1 + M.g.Y * (c2 + M.g.Z * o[3]));
+                    const int par = (c0 + c1 + c2 + o[3]) & 1;
+                    const size_t row = ((size_t)par * M.g.Vh + (site >> 1)) * 12 + 6 * h;
+                    for (int r = 0; r < 6; ++r) {
+                        const size_t qk = (row + r) * nv + k, ql = (row + r) * nv + l;
+                        const float2 kh = __ldg(Ph + qk), kl = __ldg(Pl + qk), lh = __ldg(Ph + ql), ll = __ldg(Pl + ql);
+                        const dd kr = dd_make(kh.x, kl.x), ki = dd_make(kh.y, kl.y);
+                        const dd lr = dd_make(lh.x, ll.x), li = dd_make(lh.y, ll.y);
+                        dd_fma(are, kr, lr);   // conj(P_k) P_l
+                        dd_fma(are, ki, li);
+                        dd_fma(aim, kr, li);
+                        dd_fma(aim, -ki, lr);
+                    }
+                }
+        Gt[(size_t)b * nv * nv + e] = make_double2(dd2d(are), dd2d(aim));
+    }
+}
+
 // part[r][t] = sum_{X in timeslice t / agg_t} sum_h s_h a_{X,h}^dag Gt[X][t % agg_t][h] b_{X,h}
 // for coarse vectors a, b [nrhs][Vc][2 nv]; one CTA per (r, t), a fixed
 // assignment of (X, h, k) to threads and a fixed reduction order
@@ -1436,7 +1474,9 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     WD_CUDA(cudaFuncSetAttribute(k_block_mgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mgs_smem));
     k_block_mgs<<<2 * g->Vc, 256, mgs_smem, c->st>>>(g->P, M);
     k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
-    k_gram_t<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->P, g->Gt, M);
+    k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
+    if (c->outer == PDD) k_gram_t_dd<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->Phi, g->Plo, g->Gt, M);
+    else k_gram_t<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->P, g->Gt, M);
     double2 hg[4][4][4];
     host_gamma(hg);
     WD_CUDA(cudaMemcpyToSymbolAsync(c_gamma, hg, sizeof(hg), 0, cudaMemcpyHostToDevice, c->st));
@@ -1448,7 +1488,6 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         ulex = it->second.first;
     }
     const int4 bc = make_int4(c->bc[0], c->bc[1], c->bc[2], c->bc[3]);
-    k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
     if (c->outer == PDD) {
         // double-float Galerkin assembly (FP32 pairs; ~2^-44 per operation)
         if (ncd <= 48 && nsite <= 512) {
