@@ -453,6 +453,9 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     P.res_ddl = sres.pout == PDDL;
     P.x_ddl = sres.x_ddl;
     P.tag = "fine";
+    // a loose target (the multigrid setup's inverse iterations solve to 1e-6):
+    // take the FP32 inner solve deeper, so that one outer step can reach it
+    if (prec == P32 && tol >= 1e-6) P.inner_tol = 0.5 * tol;
     // the Schur operator's launches see the precisions and the odd workspace
     P.graph_ok = true;
     P.sig64[0] = s64.pin; P.sig64[1] = s64.pout; P.sig64[2] = (uintptr_t)s64.tmp;
