@@ -244,7 +244,7 @@ const char *wd_last_error(void);
  * orthonormalised by modified Gram-Schmidt in test-vector order; coarse dof
  * index = 2*nv*Xc + nv*h + k.  Requires nv a positive multiple of 6 with
  * nv <= 6 * prod(agg) (else WD_EINVAL); WD_ENOTSUP when the 2nv x 2nv blocks
- * or an aggregate of more than 4266 sites exceed the kernels' shared memory. */
+ * exceed the assembly kernel's shared memory. */
 int wd_mg_setup(wd_ctx *ctx, const double *tv, int nv, const int agg[4], int tv_iters,
                 uint64_t seed);
 

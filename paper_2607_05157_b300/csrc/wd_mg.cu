@@ -111,41 +111,56 @@ __device__ double2 block_reduce_z(double2 v, double2 *sh) {
     return a;
 }
 
-// modified Gram-Schmidt of the nv columns of one (aggregate, half) block; one
-// CTA per block.  Each pass over the rows subtracts q_j from v_k and, in the
-// same pass, accumulates the next dot product q_{j+1}^dag v_k (or, after the
-// last j, |v_k|^2) from the updated rows: the arithmetic of sequential MGS in
-// its order, with half the passes.  Row offsets are computed once (shared
-// memory: 6 * sites-per-aggregate offsets).
-__global__ void k_block_mgs(double2 *P, MgGeom M) {
-    __shared__ double2 sh[32];
-    extern __shared__ size_t roff[];
-    const int X = blockIdx.x >> 1, h = blockIdx.x & 1;
-    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
-    const int m = nsite * 6;
-    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+// Column-major copy of the (aggregate, half) blocks of P for the block MGS:
+// Pt[blk][k][row], blk = 2 X + h, row = 6 (site in aggregate) + (comp - 6 h),
+// so that every MGS pass reads whole columns with coalesced loads.  One
+// thread per (blk, row) moves the row's nv contiguous entries.
+__global__ void k_mgs_gather(const double2 *P, double2 *Pt, MgGeom M, int to_blocks) {
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3], m = nsite * 6;
+    const long n = 2L * M.Vc * m;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const int row = (int)(t % m);
+        const long blk = t / m;
+        const int X = (int)(blk >> 1), h = (int)(blk & 1);
         int c[4];
         agg_site(M, X, row / 6, c);
-        roff[row] = pidx(M, lex(M.g, c), 6 * h + row % 6, 0);
+        const size_t off = pidx(M, lex(M.g, c), 6 * h + row % 6, 0);
+        double2 *col = Pt + (size_t)blk * M.nv * m + row;
+        if (to_blocks)
+            for (int k = 0; k < M.nv; ++k) col[(size_t)k * m] = P[off + k];
+        else
+            for (int k = 0; k < M.nv; ++k) ((double2 *)P)[off + k] = col[(size_t)k * m];
     }
-    __syncthreads();
+}
+
+// Modified Gram-Schmidt of the nv columns of one (aggregate, half) block of
+// the column-major copy; one CTA per block.  Each pass over the rows
+// subtracts q_j from v_k and, in the same pass, accumulates the next dot
+// product q_{j+1}^dag v_k (or, after the last j, |v_k|^2) from the updated
+// rows: the arithmetic of sequential MGS in its order, with half the passes.
+__global__ void k_block_mgs_cm(double2 *Pt, MgGeom M) {
+    __shared__ double2 sh[32];
+    const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
+    const int m = nsite * 6;
+    double2 *B = Pt + (size_t)blockIdx.x * M.nv * m;
     for (int k = 0; k < M.nv; ++k) {
+        double2 *vk = B + (size_t)k * m;
         double2 d = make_double2(0, 0);
         if (k > 0) {
-            for (int row = threadIdx.x; row < m; row += blockDim.x)
-                d = zfma_conj(d, P[roff[row]], P[roff[row] + k]);
+            for (int row = threadIdx.x; row < m; row += blockDim.x) d = zfma_conj(d, B[row], vk[row]);
             d = block_reduce_z(d, sh);
         }
         double2 nn = make_double2(0, 0);
         for (int j = 0; j < k; ++j) {
-            // v_k -= d_j q_j; then d_{j+1} = q_{j+1}^dag v_k, or |v_k|^2 after the last j
+            const double2 *qj = B + (size_t)j * m, *qn = qj + m;
             double2 dn = make_double2(0, 0);
             for (int row = threadIdx.x; row < m; row += blockDim.x) {
-                double2 &q = P[roff[row] + k];
-                const double2 qj = P[roff[row] + j];
-                q.x -= d.x * qj.x - d.y * qj.y;
-                q.y -= d.x * qj.y + d.y * qj.x;
-                if (j + 1 < k) dn = zfma_conj(dn, P[roff[row] + j + 1], q);
+                double2 q = vk[row];
+                const double2 a = qj[row];
+                q.x -= d.x * a.x - d.y * a.y;
+                q.y -= d.x * a.y + d.y * a.x;
+                vk[row] = q;
+                if (j + 1 < k) dn = zfma_conj(dn, qn[row], q);
                 else dn.x += q.x * q.x + q.y * q.y;
             }
             if (j + 1 < k) d = block_reduce_z(dn, sh);
@@ -153,15 +168,14 @@ __global__ void k_block_mgs(double2 *P, MgGeom M) {
         }
         if (k == 0)
             for (int row = threadIdx.x; row < m; row += blockDim.x) {
-                const double2 q = P[roff[row]];
+                const double2 q = vk[row];
                 nn.x += q.x * q.x + q.y * q.y;
             }
         nn = block_reduce_z(nn, sh);
         const double inv = 1.0 / sqrt(nn.x);
         for (int row = threadIdx.x; row < m; row += blockDim.x) {
-            double2 &q = P[roff[row] + k];
-            q.x *= inv;
-            q.y *= inv;
+            vk[row].x *= inv;
+            vk[row].y *= inv;
         }
         __syncthreads();
     }
@@ -1437,9 +1451,6 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     const int ncd = 2 * nv;
     const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 4 * 12 * ncd);
     if (smem > 227 * 1024) { set_error("wd_mg_setup: nv too large for the block assembly"); return WD_ENOTSUP; }
-    // the block orthonormalisation keeps the row offsets of one aggregate half in shared memory
-    const size_t mgs_smem = (size_t)6 * nsite * sizeof(size_t);
-    if (mgs_smem > 200 * 1024) { set_error("wd_mg_setup: aggregate of %d sites too large", nsite); return WD_ENOTSUP; }
     wd_mg_free(c);
     wd_mg *g = new wd_mg();
     memset(g, 0, sizeof(*g));
@@ -1471,8 +1482,11 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         WD_TRY(mg_generate_tv(c, nv, tv_iters, seed, tvd));
     }
     k_tv_to_P<<<(unsigned)((nP + 255) / 256), 256, 0, c->st>>>((const double2 *)tvd, g->P, M);
-    WD_CUDA(cudaFuncSetAttribute(k_block_mgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mgs_smem));
-    k_block_mgs<<<2 * g->Vc, 256, mgs_smem, c->st>>>(g->P, M);
+    // block MGS on a column-major copy of the blocks (coalesced passes), kept in
+    // the test-vector workspace, which P has been built from (same size)
+    k_mgs_gather<<<1184, 256, 0, c->st>>>(g->P, (double2 *)tvd, M, 1);
+    k_block_mgs_cm<<<2 * g->Vc, 256, 0, c->st>>>((double2 *)tvd, M);
+    k_mgs_gather<<<1184, 256, 0, c->st>>>(g->P, (double2 *)tvd, M, 0);
     k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
     if (c->outer == PDD) k_gram_t_dd<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->Phi, g->Plo, g->Gt, M);
