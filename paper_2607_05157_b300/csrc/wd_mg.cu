@@ -860,6 +860,10 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
         for (int e = threadIdx.x; e < CH * NE; e += blockDim.x) Ws[e] = cdd_zero();
         __syncthreads();
         for (int hop = -1; hop < 8; ++hop) {
+            // a hop no site of the chunk takes is skipped by every thread alike
+            bool used = false;
+            for (int sl = 0; sl < CH; ++sl) used |= s_ys[sl][hop + 1] >= 0;
+            if (!used) continue;
             // stage 1: W = P(y) of every chunk site that has this hop
             for (int e = threadIdx.x; e < CH * NE; e += blockDim.x) {
                 const int sl = e / NE, r = e - sl * NE, comp = r / ncd, i = r - comp * ncd, h = i / nv, k = i - h * nv;
