@@ -778,6 +778,8 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
     __shared__ int s_n;
     __shared__ int s_ys[CH][9], s_xs[CH];       // per chunk site: neighbour of each hop (-1: none), the site
     __shared__ double s_coef[CH][9];
+    __shared__ cdd s_u[CH][8][9];               // U' of each hop (U(x), or U(y)^dag backward), double-float
+    __shared__ dd s_cd[CH][9];                  // the hop coefficients, double-float
     __shared__ int s_gp[4][4];                  // gamma partner spin and value (+-1, +-i) per (mu, s)
     __shared__ double2 s_gv[4][4];
     const int X = blockIdx.x / 9, b = blockIdx.x % 9;
@@ -859,6 +861,23 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
         }
         for (int e = threadIdx.x; e < CH * NE; e += blockDim.x) Ws[e] = cdd_zero();
         __syncthreads();
+        // the links and coefficients of the chunk's hops, split into FP32 pairs once
+        // (the FP64 rate is a small fraction of the FP32 one)
+        for (int e = threadIdx.x; e < CH * 9 * 10; e += blockDim.x) {
+            const int sl = e / 90, r = e % 90, hop = r / 10 - 1, q = r % 10;
+            const int ys = s_ys[sl][hop + 1];
+            if (ys < 0) continue;
+            if (q == 9) { s_cd[sl][hop + 1] = f64_to_dd(s_coef[sl][hop + 1]); continue; }
+            if (hop < 0) continue;
+            const int mu = hop & 3, fwd = hop < 4, a = q / 3, bb = q % 3;
+            const double2 *u = U + ((size_t)mu * M.g.V + (fwd ? s_xs[sl] : ys)) * 9;
+            const double2 uv = fwd ? u[3 * a + bb] : u[3 * bb + a];
+            cdd ul;
+            ul.re = f64_to_dd(uv.x);
+            ul.im = f64_to_dd(fwd ? uv.y : -uv.y);
+            s_u[sl][hop][q] = ul;
+        }
+        __syncthreads();
         for (int hop = -1; hop < 8; ++hop) {
             // a hop no site of the chunk takes is skipped by every thread alike
             bool used = false;
@@ -876,7 +895,7 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
                 const int sl = e / NE, r = e - sl * NE, comp = r / ncd, i = r - comp * ncd;
                 const int ys = sl < nc ? s_ys[sl][hop + 1] : -1;
                 if (ys < 0) continue;
-                const dd coef = f64_to_dd(s_coef[sl][hop + 1]);
+                const dd coef = s_cd[sl][hop + 1];
                 const cdd *w = W + sl * NE;
                 cdd out;
                 if (hop < 0) {
@@ -884,15 +903,9 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
                 } else {
                     const int mu = hop & 3, fwd = hop < 4, sg = comp / 3, a = comp % 3, h = i / nv;
                     const int sp = (sg >> 1) == h ? sg : s_gp[mu][sg];
-                    const double2 *u = U + ((size_t)mu * M.g.V + (fwd ? s_xs[sl] : ys)) * 9;
                     cdd t = cdd_zero();
-                    for (int bb = 0; bb < 3; ++bb) {
-                        const double2 uv = fwd ? u[3 * a + bb] : u[3 * bb + a];
-                        cdd ul;
-                        ul.re = f64_to_dd(uv.x);
-                        ul.im = f64_to_dd(fwd ? uv.y : -uv.y);
-                        cdd_fma<false>(t, ul, w[(3 * sp + bb) * ncd + i]);
-                    }
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) cdd_fma<false>(t, s_u[sl][hop][3 * a + bb], w[(3 * sp + bb) * ncd + i]);
                     if (sp == sg) {
                         out = t;
                     } else {   // (-/+ g) t with g in {+-1, +-i}
