@@ -95,7 +95,7 @@ def measured_peaks():
 # they change.
 HOP32_TRAFFIC = {"sources": ("paper_2607_05157_b300/csrc/wd_dslash.cu", "paper_2607_05157_b300/csrc/wd_common.cuh",
                              "paper_2607_05157_b300/csrc/wd_internal.h"),
-                 "sha256_16": "aaee79dd0ed0c56c", "bytes_per_launch": 6558.1e6,
+                 "sha256_16": "ac0db3d53c3f09b6", "bytes_per_launch": 6558.1e6,
                  "algorithmic_bytes_per_launch": 4901.3e6}
 
 
@@ -243,7 +243,7 @@ def dslash_bytes(api, wd, c, ncd, Vc):
 # ---- secondary measurements (other rows and configurations) ------------------
 
 def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 48)):
-    """Row a8: tcgen05 coarse 9-point block stencil on the 24^3x48 two-level
+    """The tcgen05 coarse 9-point block stencil on the 24^3x48 two-level
     workload (4^4 aggregates, 24 test vectors -> 48x48 blocks, 2592 coarse
     sites), CUDA-event times of the kernel, algorithmic TFLOP/s (8 ncd^2 per
     block, 9 blocks per site and RHS) and GB/s of the compact algorithmic
@@ -276,7 +276,7 @@ def coarse_measure(wd, api, torch, synth, rhs_list=(64, 512), dims=(24, 24, 24, 
 
 
 def gradient_measure(wd, api, torch, synth):
-    """Row a10: d/dkappa and the link force of the probing (d=2, full dilution)
+    """The gradient: d/dkappa and the link force of the probing (d=2, full dilution)
     estimate of tr[g5 D^-1] on 8^3x16 (192 solves + force), wall time."""
     dims = (8, 8, 8, 16)
     ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, 1005), 0.125, BC)
@@ -353,7 +353,7 @@ def probing_measure(wd, api, torch, synth):
 
 
 def mlmc_probe_measure(wd, api, torch, synth):
-    """Row f2: two-level MLMC with probing on both levels (level 1: probing
+    """Two-level MLMC with probing on both levels (level 1: probing
     d = 2 x 12 dilution; level 2: colouring of the coarse torus d = 1 x the 48
     coarse dofs of a site; GPU-built 4^4 aggregates with 24 test vectors)
     against plain probing on the same noise samples, 8^3x16: wall time, solves
@@ -386,7 +386,7 @@ def mlmc_probe_measure(wd, api, torch, synth):
 
 
 def mlmc3_measure(wd, api, torch, synth):
-    """Row f3: three-level MLMC on 16^3x32 (kappa 0.13; aggregates 4^4 then
+    """Three-level MLMC on 16^3x32 (kappa 0.13; aggregates 4^4 then
     2^4, i.e. 4^3x8 and 2^3x4, 24 test vectors per level built on the GPU):
     wall time, solves and per-sample variances of each level's total, beside
     the two-level estimator on the same fine noise."""
@@ -421,7 +421,7 @@ def mlmc3_measure(wd, api, torch, synth):
 
 
 def connected_measure(wd, api, torch, synth):
-    """Row f4: connected pseudoscalar G(t) with the two-level decomposition on
+    """The connected pseudoscalar G(t) with the two-level decomposition on
     8^3x16 (N1 = 4 level-1 samples, N2 = 32 coarse samples): wall time, solves,
     and the variance of the fine term G_11 against the plain estimator on the
     same noise (the variance reduction of Sec. 4)."""
@@ -443,7 +443,7 @@ def connected_measure(wd, api, torch, synth):
 
 
 def batched_measure(wd, torch, synth):
-    """Row a11 (and the batched part of the two-level configuration):
+    """Batched solves over uneven lattices (the batched part of the two-level configuration):
     8^3x16 (64 RHS) + 12^3x24 (32) + 16^3x32 (16) solved together (persistent
     multi-lattice stencil, CUDA graph) vs one after another."""
     specs = [((8, 8, 8, 16), 0.125, 64), ((12, 12, 12, 24), 0.13, 32), ((16, 16, 16, 32), 0.13, 16)]
@@ -516,7 +516,7 @@ def small_trace_measure(wd, api, torch, synth, steps=10):
 
 
 def apply_measure(wd, api, torch, synth, dims, nrhs, steps, warmup):
-    """Row a4 alone: D = 1 - kappa H applied to nrhs Gaussian spinors with
+    """The fine stencil alone: D = 1 - kappa H applied to nrhs Gaussian spinors with
     FP32 storage (two hops per application, each with its same-parity
     addend), CUDA-event times per hop launch and GB/s of the algorithmic
     bytes (96 B in + 96 B out + 96 B addend per site and RHS, 8 links of 72 B

@@ -83,7 +83,7 @@ enum { WD_TR_DINV = 0, WD_TR_G5_DINV = 1 };
    one timeslice (Eq. 15 with n_D = 3: c(x) = sum_{j<3} sigma_j x_j mod n_c) */
 enum { WD_DIL_TIME = 0x100, WD_COLOR_3D = 0x200 };
 
-/* Create a context: uploads the gauge field (a1), folds the boundary factors
+/* Create a context: uploads the gauge field, folds the boundary factors
  * into the wrap-around links and builds FP64/FP32/BF16 even-odd copies.
  * stream: a cudaStream_t (NULL = legacy default stream).  The context owns
  * every device buffer it allocates; `gauge` is not retained. */

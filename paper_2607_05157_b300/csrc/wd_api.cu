@@ -1,4 +1,4 @@
-// C ABI entry points of libwd: context life cycle, gauge ingest (row a1),
+// C ABI entry points of libwd: context life cycle, gauge ingest,
 // D / D^dag application and solves, workspaces, profiling.
 #include <stdarg.h>
 #include <stdlib.h>
@@ -250,7 +250,7 @@ int hop(wd_ctx *c, int pin, int pout, int p, void *out, const void *in, const vo
     return WD_OK;
 }
 
-// ---- gauge ingest (a1) ------------------------------------------------------
+// ---- gauge ingest ---------------------------------------------------------
 // From lexicographic FP64 links [4][V][3][3] to the eo doubled layout of one
 // storage type: dir mu  = U_mu(x) (x bc[mu] if x_mu = L-1),
 //               dir 4+mu = U_mu(x-mu)^dag (x bc[mu] if x_mu = 0).

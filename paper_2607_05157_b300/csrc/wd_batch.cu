@@ -1,4 +1,4 @@
-// Batched solves over lattices of different sizes (row a11).
+// Batched solves over lattices of different sizes.
 //
 // A wd_batch groups contexts (one gauge field each, any even extents) that
 // share a CUDA stream.  wd_batch_solve runs their mixed-precision solves in

@@ -1,4 +1,4 @@
-// Coarse 9-point block stencil on the 5th-generation tensor cores (row a8).
+// Coarse 9-point block stencil on the 5th-generation tensor cores.
 //
 // y(X) = sum_{b=0..8} A_b(X) x(nbr_b(X)) with ncd x ncd complex blocks is, for
 // every coarse site X, two real GEMMs over the right-hand sides that share one

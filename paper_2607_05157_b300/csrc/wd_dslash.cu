@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel_f2_cap(HopArgs A) {
     if (s < A.g.Vh && tile_rhs(A, rb, 0, R) >= 0) hop_site_f2<SIn, SOut, SW, G, R, DAG, false, 0>(A, rb, s);
 }
 
-// Persistent batched stencil over several lattices (row a11): one launch walks
+// Persistent batched stencil over several lattices: one launch walks
 // a static work list of (lattice, site tile, RHS tile) items -- the items of
 // lattice j are the blocks [base_j, base_j + blocks_j) -- with a grid sized to
 // the resident CTAs of the GPU; CTA i takes items i, i + gridDim.x, ...  No

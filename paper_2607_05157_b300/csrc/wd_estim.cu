@@ -1,4 +1,4 @@
-// Trace estimators (rows a2, a9): Hutchinson (Eq. 3) and stochastic probing
+// Trace estimators: Hutchinson (Eq. 3) and stochastic probing
 // with spin-colour / time dilution (Eqs. 13-14), estimating
 // tr[B D^{-1}(t, t)] per timeslice with B = 1 or gamma5 (Eq. 21).
 //

@@ -1,4 +1,4 @@
-// Derivatives of the trace estimates (row a10).  The paper has no gradients;
+// Derivatives of the trace estimates.  The paper has no gradients;
 // they follow from differentiating its quadratic forms X = v^dag B D^{-1} v:
 //   dX = - w^dag (dD) z,   z = D^{-1} v,   w = D^{-dag} B^dag v.
 // gamma5-hermiticity, D^{-dag} = g5 D^{-1} g5, turns the adjoint solve into an

@@ -1,4 +1,4 @@
-// Two-level aggregation multigrid for the MLMC estimator (Sec. 2, row a8).
+// Two-level aggregation multigrid for the MLMC estimator (Sec. 2).
 //
 // Transfer operators (Sec. 2: R = P^dag, P^dag P = I): the fine lattice is cut
 // into aggregates of agg[mu] sites per direction; every test vector is

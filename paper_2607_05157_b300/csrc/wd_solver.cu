@@ -2,12 +2,12 @@
 //
 // With D = [[1, -k H_eo], [-k H_oe, 1]] (even sites first), the even-site
 // Schur complement is  D_hat = 1 - k^2 H_eo H_oe,  and
-//   D_hat x_e = b_e + k H_eo b_o,   x_o = b_o + k H_oe x_e          (rows a3, a7)
+//   D_hat x_e = b_e + k H_eo b_o,   x_o = b_o + k H_oe x_e
 // solve D x = b exactly; the full residual of x equals the Schur residual on
 // the even sites.  The Krylov solver is BiCGStab with per-RHS FP64 scalars
 // (the paper names no method: Sec. 1 only needs the products D^{-1} eta).
 //
-// Mixed precision (row a6): the FP64 residual r = b_hat - D_hat x is
+// Mixed precision: the FP64 residual r = b_hat - D_hat x is
 // normalised per RHS, solved to a loose relative tolerance in FP32 (or BF16
 // storage with FP32 arithmetic), and the correction is added to x in FP64;
 // repeated until the FP64 residual meets the requested tolerance.
@@ -436,7 +436,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
         b_o = bs + f64 / sizeof(double);
     }
     WD_CUDA(cudaMemcpyAsync(bn2 + 2 * nrhs, bnorm2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->st));
-    // b_hat = b_e + k H_eo b_o                                         (a3)
+    // b_hat = b_e + k H_eo b_o
     WD_TRY(hop(c, pd, pd, 0, bhat, b_o, b_e, 1.0, k, nrhs, false, nullptr, 0.0, src_tsup));
     if (bhat_out) *bhat_out = bhat;
 
@@ -464,7 +464,7 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     std::vector<double> last_rn2;
     int status = dc_solve(c, P, bhat, x_e, nrhs, bn2 + 2 * nrhs, bnorm2, tol, prec, max_iter, iters, last_rn2);
     if (status != WD_OK && status != WD_ENOCONV && status != WD_EBREAKDOWN) return status;
-    // x_o = b_o + k H_oe x_e                                             (a7)
+    // x_o = b_o + k H_oe x_e
     if (x_o) WD_TRY(hop(c, pd, pd, 1, x_o, x_e, b_o, 1.0, k, nrhs));
     // True FP64 residual of the full system, when asked for.  Without it the
     // last FP64 Schur residual (mixed modes) or the FP64 recursion (FP64 mode)

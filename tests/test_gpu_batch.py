@@ -1,4 +1,4 @@
-"""Row a11: batched lockstep solves over lattices of different sizes (persistent
+"""Batched lockstep solves over lattices of different sizes (persistent
 multi-lattice stencil launch, optional CUDA-graph replay), checked against
 dense solves on small lattices and against the oracle's operator (true FP64
 residual) on the 8^3x16 + 12^3x24 + 16^3x32 set."""

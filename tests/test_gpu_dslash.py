@@ -1,4 +1,4 @@
-"""Parity of the fine Wilson stencil (row a4, through wd_apply) with the oracle,
+"""Parity of the fine Wilson stencil (through wd_apply) with the oracle,
 element by element, FP64 / FP32 / BF16, D and D^dag, ragged RHS counts."""
 import numpy as np
 import pytest

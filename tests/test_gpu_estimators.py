@@ -1,4 +1,4 @@
-"""Parity of trace_estimate (rows a2, a3-a7, a9) with the oracle on identical
+"""Parity of trace_estimate (noise, solves, contractions) with the oracle on identical
 seeded noise: per-sample values X_i(t) element by element.
 
 Tolerance reading: solves at 1e-12 on both sides bound the error of one

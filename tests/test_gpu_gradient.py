@@ -1,4 +1,4 @@
-"""Parity of the adjoint (row a10): the link-force kernel element by element
+"""Parity of the adjoint: the link-force kernel element by element
 against the oracle, the estimator gradient against the oracle's dense
 per-vector computation on identical noise, the autograd path against central
 finite differences (h = 1e-5, FP64) on 32 random su(3) link directions on

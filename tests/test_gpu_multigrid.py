@@ -1,4 +1,4 @@
-"""Parity of the two-level hierarchy (row a8) with the oracle: the prolongator
+"""Parity of the two-level hierarchy with the oracle: the prolongator
 built on the GPU from the same test vectors, restriction and prolongation,
 the Galerkin coarse operator D_c = P^dag D P (Eq. 7) applied to random coarse
 vectors, coarse solves, and the two-level MLMC estimator (Eqs. 9-12) per sample.

@@ -1,4 +1,4 @@
-"""Parity of the solver path (rows a3-a7): x = D^{-1} b from wd_solve against
+"""Parity of the solver path: x = D^{-1} b from wd_solve against
 dense LU (4^4 and a ragged small lattice) and, at larger size, against the
 oracle's own operator on the returned x (true FP64 residual)."""
 import numpy as np

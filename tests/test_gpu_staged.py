@@ -1,4 +1,4 @@
-"""Parity of every stencil launch variant of row a4 (plain, software-pipelined,
+"""Parity of every stencil launch variant of the fine stencil (plain, software-pipelined,
 timeslices staged through shared memory by bulk async copies, register-capped
 with grouped RHS block orders) with the oracle,
 each forced through the launch-shape override, FP32 and BF16, D and D^dag, with
