@@ -353,6 +353,32 @@ def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
     ctx.close()
 
 
+@pytest.mark.parametrize("nrhs", [1, 9, 129, 257])
+def test_tensor_core_coarse_stencil_rhs_counts(nrhs):
+    """RHS counts at the edges of the tiling: one row, counts that are not a
+    multiple of 8 (the input rows are padded to 8), a last tile of one RHS,
+    three tiles.  Every element against the FP64 coarse operator within
+    U_TC (BF16) and U_SPLIT (BF16 pairs), on 12^4 with 4^4 aggregates."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply
+    dims, agg, nv = (12, 12, 12, 12), (4, 4, 4, 4), 24
+    ctx = Context(dims, synth.gauge_field(dims, 0.5, 1007), 0.13, BC)
+    wd_mg_setup(ctx.h, synth.test_vectors(dims, nv, 80), nv, agg)
+    cs = _coarse_shape(dims, agg, nv, nrhs)
+    rng = np.random.default_rng(15 + nrhs)
+    x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 2).cpu().numpy()
+    ysp = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+    y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
+    A, nbr = _coarse_blocks(ctx, [L // a for L, a in zip(dims, agg)], 2 * nv)
+    for r in sorted({0, nrhs // 2, nrhs - 1, min(nrhs - 1, 128)}):
+        bound = _coarse_abs_bound(A, nbr, x[r])
+        assert np.all(np.abs(y[r] - y64[r]) <= U_TC * bound), r
+        assert np.all(np.abs(ysp[r] - y64[r]) <= U_SPLIT * bound), r
+        assert rel(ysp[r], y64[r]) < REL_SPLIT
+    ctx.close()
+
+
 def test_tensor_core_coarse_stencil_96_dofs():
     """The second shape of the tensor-core stencil: 48 test vectors (96 x 96
     blocks, MMA N = 192, one accumulator set of 512 TMEM columns) on 12^4 with
