@@ -325,6 +325,16 @@ struct Problem {
     bool graph_ok = false;      // operators capturable in a graph (sig64 / siglo: their keys)
     uintptr_t sig64[3] = {0, 0, 0}, siglo[3] = {0, 0, 0};
     double inner_tol = 0.0;     // tolerance of the inner solves (0: by inner precision)
+    // Recursive residual update r <- r - |r| opupd(e), e the inner solution of
+    // the normalised residual (inner precision in and out, FP64 sum), in place
+    // of res64 once the residual is small: the update adds at most
+    // upd_err |r| to r (upd_err: a bound on the normwise error of opupd
+    // relative to |r|), so it is taken while upd_err |r| <= tol |b| / 4, and
+    // each RHS counts as converged only when its residual plus the sum of
+    // these bounds is <= tol |b|.  The residual may be FP64 or the
+    // double-float layout (res_ddl).
+    OpFn opupd = nullptr; void *uupd = nullptr;
+    double upd_err = 0.0;
 };
 // restriction P^dag v and prolongation P y between eo FP64 fine fields and
 // coarse FP64 vectors (wd_mg.cu); dd_ok: double-float arithmetic allowed

@@ -1027,6 +1027,58 @@ __global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int 
     }
 }
 
+// FP32 coarse stencil y = A x for many RHS, tiled like k_coarse_apply_dd: one
+// CTA per (X, 32-RHS tile), threads (i, rq), rq < 8, thread (i, rq) taking
+// the RHS rq, rq + 8, rq + 16, rq + 24; each of the 9 blocks staged
+// transposed in shared memory with the neighbour's 32 RHS.  The products and
+// sums per output run in the order of k_coarse_apply<float2, float> (blocks
+// b = 0..8, columns j = 0..ncd-1, the same four FMAs), so the two give the
+// same bits.
+__global__ void k_coarse_apply32t(const float2 *Dh, const int *nbr, const float2 *x, float2 *y, int ncd, int Vc,
+                                  int nrhs) {
+    constexpr int NQ = 4, TILE = 8 * NQ;
+    extern __shared__ float2 sm2[];
+    const int ld = ncd + 1;
+    float2 *As = sm2, *xs = sm2 + ncd * ld;                     // [ncd][ld], [TILE][ncd]
+    const int X = blockIdx.x, r0 = blockIdx.y * TILE;
+    const int i = threadIdx.x % ncd, rq = threadIdx.x / ncd;
+    const int nn = ncd * ncd;
+    float are[NQ], aim[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) { are[q] = 0.f; aim[q] = 0.f; }
+    for (int b = 0; b < 9; ++b) {
+        const int nb = nbr[X * 9 + b];
+        const size_t base = ((size_t)X * 9 + b) * nn;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int ei = e / ncd, ej = e - ei * ncd;
+            As[ej * ld + ei] = __ldg(Dh + base + e);
+        }
+        for (int e = threadIdx.x; e < TILE * ncd; e += blockDim.x) {
+            const int er = e / ncd, ej = e - er * ncd;
+            xs[e] = r0 + er < nrhs ? __ldg(x + ((size_t)(r0 + er) * Vc + nb) * ncd + ej) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (rq < 8) {
+            for (int j = 0; j < ncd; ++j) {
+                const float2 m = As[j * ld + i];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float2 v = xs[(rq + 8 * q) * ncd + j];
+                    are[q] = fmaf(m.x, v.x, are[q]); are[q] = fmaf(-m.y, v.y, are[q]);
+                    aim[q] = fmaf(m.x, v.y, aim[q]); aim[q] = fmaf(m.y, v.x, aim[q]);
+                }
+            }
+        }
+    }
+    if (rq >= 8) return;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int r = r0 + rq + 8 * q;
+        if (r < nrhs) y[((size_t)r * Vc + X) * ncd + i] = make_float2(are[q], aim[q]);
+    }
+}
+
 // ---- coarse stencil on CUDA cores (FP64 reference path and FP32) -----------
 // y[rhs][X][i] = a*w[rhs][X][i] + beta * sum_b sum_j A_b(X)[i][j] x[rhs][nbr_b(X)][j]
 // One CTA per (X, tile of 8 RHS), threads (i, r).
@@ -1231,11 +1283,19 @@ int block_stencil_apply64(wd_ctx *c, const double2 *A, const int *nbr, int n, in
 
 int coarse_apply32(wd_ctx *c, const float *x, float *y, int nrhs) {
     wd_mg *g = c->mg;
-    dim3 grid(g->Vc, (nrhs + 7) / 8);
     int slot;
     prof_begin(c, WD_K_COARSE, 8.0 * g->ncd * g->ncd * 9.0 * g->Vc * nrhs, &slot);
-    k_coarse_apply<float2, float><<<grid, g->ncd * 8, 0, c->st>>>(g->Dc32, g->nbr, (const float2 *)x, (float2 *)y,
-                                                                  nullptr, 0.0, 1.0, g->ncd, g->Vc, nrhs);
+    if (nrhs >= 16) {
+        dim3 grid(g->Vc, (nrhs + 31) / 32);
+        const size_t smem = ((size_t)g->ncd * (g->ncd + 1) + 32 * (size_t)g->ncd) * sizeof(float2);
+        WD_CUDA(cudaFuncSetAttribute(k_coarse_apply32t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_coarse_apply32t<<<grid, g->ncd * 8, smem, c->st>>>(g->Dc32, g->nbr, (const float2 *)x, (float2 *)y, g->ncd,
+                                                            g->Vc, nrhs);
+    } else {
+        dim3 grid(g->Vc, (nrhs + 7) / 8);
+        k_coarse_apply<float2, float><<<grid, g->ncd * 8, 0, c->st>>>(g->Dc32, g->nbr, (const float2 *)x, (float2 *)y,
+                                                                      nullptr, 0.0, 1.0, g->ncd, g->Vc, nrhs);
+    }
     prof_end(c, slot);
     c->launches++;
     WD_CUDA(cudaGetLastError());
@@ -1400,6 +1460,11 @@ int coarse_solve(wd_ctx *c, const double *b, double *x, int nrhs, double tol, in
     // FP32 blocks on the CUDA cores
     const bool tc = prec != P64 && coarse_tc_ok(c) && c->mg->Wlo;
     P.oplo = tc ? coptc_split : cop32; P.ulo = nullptr;
+    // once the residual is small, r <- r - D_c e with the FP32 blocks on the
+    // CUDA cores instead of a double-float residual: the FP32 product is off by
+    // a few 1e-8 of |D_c| |e| (rounded blocks, FP32 sums of 9 x ncd terms);
+    // 1e-6 of |r| bounds it with the norm of D_c^{-1} folded in
+    if (prec != P64) { P.opupd = cop32; P.upd_err = 1e-6; }
     // the FP64 residuals of the mixed solves in double-float arithmetic, as on
     // the fine lattice (~2^-44 normwise), unless the tolerance asks for more
     int use_dd = prec != P64 && tol >= 1e-12 && c->outer == PDD;
@@ -1563,7 +1628,9 @@ extern "C" int wd_coarse_apply(wd_ctx *c, const double *in, double *out, int nrh
     const Space sp = coarse_space(c);
     // WD_MIXED_FP32: BF16-pair operands, WD_MIXED_BF16: BF16 operands on the
     // tensor cores; the FP32 blocks on the CUDA cores where those are unavailable
-    const bool tc = coarse_tc_ok(c) && (prec == P16 || c->mg->Wlo);
+    // (WD_COARSE_FP32=1 forces the FP32 CUDA-core blocks, for tests)
+    const char *f32 = getenv("WD_COARSE_FP32");
+    const bool tc = coarse_tc_ok(c) && (prec == P16 || c->mg->Wlo) && !(f32 && atoi(f32) > 0);
     void *xl, *yl;
     WD_TRY(ws_get(c, "ca.x", space_bytes(sp, P32, nrhs), &xl));
     WD_TRY(ws_get(c, "ca.y", space_bytes(sp, P32, nrhs), &yl));

@@ -17,6 +17,7 @@
 #include <string.h>
 #include <functional>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "wd_internal.h"
@@ -265,9 +266,11 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
     double *r64, *scale_d, *rn2_d, *blo, *hsc;
     WD_TRY(ws_get(c, (tag + ".r64").c_str(), f64, (void **)&r64));
     WD_TRY(ws_get(c, (tag + ".blo").c_str(), space_bytes(P.sp, pw, nrhs), (void **)&blo));
-    WD_TRY(ws_get(c, (tag + ".scale").c_str(), sizeof(double) * 2 * nrhs, (void **)&scale_d));
+    WD_TRY(ws_get(c, (tag + ".scale").c_str(), sizeof(double) * 3 * nrhs, (void **)&scale_d));
     WD_TRY(ws_get(c, (tag + ".rn2").c_str(), sizeof(double) * nrhs, (void **)&rn2_d));
-    WD_TRY(hws_get(c, (tag + ".hscale").c_str(), sizeof(double) * 2 * nrhs, (void **)&hsc));
+    WD_TRY(hws_get(c, (tag + ".hscale").c_str(), sizeof(double) * 3 * nrhs, (void **)&hsc));
+    const bool can_update = P.opupd != nullptr;
+    std::vector<double> upd_acc(nrhs, 0.0);    // sum of the update error bounds, per RHS
     // the solution: FP64, or (x_ddl) a double-float layout copy updated in
     // double-float arithmetic and assembled into FP64 once at the end
     void *xd = nullptr;
@@ -293,13 +296,19 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
         WD_CUDA(cudaMemcpyAsync(rn2.data(), rn2_d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
         WD_CUDA(cudaStreamSynchronize(c->st));
         int open = 0;
+        double worst_rel = 0.0;
         for (int r = 0; r < nrhs; ++r) {
-            const bool done = !(rn2[r] > tol * tol * bnorm2[r]) || bnorm2[r] == 0.0;
+            const double rn = sqrt(rn2[r]) + upd_acc[r];
+            const bool done = !(rn > tol * sqrt(bnorm2[r])) || bnorm2[r] == 0.0;
             if (!isfinite(rn2[r])) status = WD_EBREAKDOWN;
             hsc[r] = done || !isfinite(rn2[r]) ? 0.0 : 1.0 / sqrt(rn2[r]);
             hsc[nrhs + r] = done || !isfinite(rn2[r]) ? 0.0 : sqrt(rn2[r]);
+            hsc[2 * nrhs + r] = -hsc[nrhs + r];
             open += hsc[r] != 0.0;
+            if (hsc[r] != 0.0) worst_rel = fmax(worst_rel, sqrt(rn2[r] / bnorm2[r]));
         }
+        // this step's residual by the recursive update (Problem::opupd)
+        const bool recursive = can_update && isfinite(worst_rel) && P.upd_err * worst_rel <= 0.25 * tol;
         last_rn2 = rn2;
         if (verbose) {
             double worst = 0;
@@ -309,7 +318,7 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
                     P.tag, outer, worst, open, used);
         }
         if (open == 0 || used >= max_iter) break;
-        WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, c->st));
+        WD_CUDA(cudaMemcpyAsync(scale_d, hsc, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, c->st));
         // b_lo = r / |r|   (zero for converged RHS, which then stay inactive)
         WD_TRY(blas_copy_convert(c, P.sp, rp, r64, pw, blo, nrhs, scale_d));
         WD_TRY(bicg_init(c, pw, pp, V, blo, nrhs, inner_tol, nullptr));
@@ -325,13 +334,22 @@ int dc_solve(wd_ctx *c, const Problem &P, const double *b, double *x, int nrhs, 
             fprintf(stderr, "[wd]   inner: ran %d, max iters %d, breakdowns %d\n", ran, mx, flags);
         }
         // x += |r| e  (FP64 or double-float), then the FP64 residual r = b - A x
-        if (P.x_ddl) {
-            WD_TRY(blas_axpy_ddl(c, P.sp, xd, V.x, scale_d + nrhs, nrhs));
-            WD_TRY(P.res64(c, b, (const double *)xd, r64, nrhs, P.ures));
+        if (P.x_ddl) WD_TRY(blas_axpy_ddl(c, P.sp, xd, V.x, scale_d + nrhs, nrhs));
+        else WD_TRY(blas_axpy_mixed(c, P.sp, x, pw, V.x, scale_d + nrhs, nrhs));
+        if (recursive) {
+            // r -= |r| A e: A e is close to r / |r|, so an operator error of
+            // upd_err relative to |r| is all the update adds
+            void *y;
+            WD_TRY(ws_get(c, (tag + ".upd").c_str(), space_bytes(P.sp, pw, nrhs), &y));
+            WD_TRY(P.opupd(c, V.x, y, nrhs, P.uupd));
+            if (P.res_ddl) WD_TRY(blas_axpy_ddl(c, P.sp, r64, y, scale_d + 2 * nrhs, nrhs));
+            else WD_TRY(blas_axpy_mixed(c, P.sp, r64, pw, y, scale_d + 2 * nrhs, nrhs));
+            for (int r = 0; r < nrhs; ++r) upd_acc[r] += P.upd_err * hsc[nrhs + r];
         } else {
-            WD_TRY(blas_axpy_mixed(c, P.sp, x, pw, V.x, scale_d + nrhs, nrhs));
-            WD_TRY(P.res64(c, b, x, r64, nrhs, P.ures));
+            WD_TRY(P.res64(c, b, P.x_ddl ? (const double *)xd : x, r64, nrhs, P.ures));
+            std::fill(upd_acc.begin(), upd_acc.end(), 0.0);
         }
+        if (verbose) fprintf(stderr, "[wd]   residual by %s\n", recursive ? "recursive update" : "res64");
     }
     if (P.x_ddl) WD_TRY(blas_ddl_to_f64(c, P.sp, xd, x, nrhs));
     if (status == WD_OK)
@@ -456,6 +474,11 @@ int solve_eo(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, doubl
     // a loose target (the multigrid setup's inverse iterations solve to 1e-6):
     // take the FP32 inner solve deeper, so that one outer step can reach it
     if (prec == P32 && tol >= 1e-6) P.inner_tol = 0.5 * tol;
+    // once the residual is small, r <- r - D_hat e with the FP32 operator of
+    // the inner solves instead of a double-float residual (two FP32 hops in
+    // place of two double-float ones): its normwise error, a few 1e-7 of |e|
+    // at the masses of interest, stays below 1.5e-6 of |r|
+    if (prec == P32) { P.opupd = schur_op; P.uupd = &slo; P.upd_err = 1.5e-6; }
     // the Schur operator's launches see the precisions and the odd workspace
     P.graph_ok = true;
     P.sig64[0] = s64.pin; P.sig64[1] = s64.pout; P.sig64[2] = (uintptr_t)s64.tmp;
