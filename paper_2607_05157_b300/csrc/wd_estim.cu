@@ -471,6 +471,39 @@ int gen_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, double *be, do
     return WD_OK;
 }
 
+// Sign words of the plain Rademacher noise gen_noise_eo writes:
+// bits[(p Vh + s) 12 + k] has bit r set where entry k of half-site s of parity
+// p is -1 in sample sample0 + r (r < nrhs <= 64).  The same hash as
+// site_noise, so the words describe exactly the fields of gen_noise_eo.
+__global__ void k_noise_signs(EstParams P, Geom g, unsigned long long *bits) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)g.V * 12) return;
+    const int k = (int)(i % 12);
+    const long eo = i / 12;
+    const int p = (int)(eo / g.Vh), s = (int)(eo - (long)p * g.Vh);
+    int x, y, z, t;
+    eo_coords(g, p, s, x, y, z, t);
+    const unsigned long long site = (unsigned long long)(x + g.X * (y + g.Y * (z + (long)g.Z * t)));
+    unsigned long long w = 0;
+    for (int r = 0; r < P.nrhs; ++r) {
+        const RhsDesc d = describe(P, P.g0 + r);
+        if (rademacher(P.seed, (unsigned long long)(d.sample | P.stream_hi), 12ULL * site + k) < 0.0) w |= 1ULL << r;
+    }
+    bits[i] = w;
+}
+
+int gen_noise_signs(wd_ctx *c, uint64_t seed, int sample0, int nrhs, unsigned long long *bits) {
+    if (nrhs < 1 || nrhs > 64) { set_error("noise signs: 1..64 samples per word"); return WD_EINVAL; }
+    EstParams P;
+    memset(&P, 0, sizeof(P));
+    P.seed = seed; P.m = 1; P.nc = 1; P.dil = 1; P.TT = 1; P.g0 = sample0; P.nrhs = nrhs;
+    const long n = (long)c->g.V * 12;
+    k_noise_signs<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(P, c->g, bits);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
 // X[sample0 + r][t] += sum_{x in t} conj(eta_r(x)) (B y_r)(x) for unmasked
 // Rademacher noise of samples sample0 + r (r < nrhs); X is [N][T][2]
 int contract_noise_eo(wd_ctx *c, uint64_t seed, int sample0, int nrhs, int gamma5, const double *ye,

@@ -348,6 +348,11 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
 // per-timeslice restriction Rt[r][X][tau][i] (complex FP64, tau the timeslice
 // inside aggregate X) of eo FP64 fields, and yc = sum_tau Rt = P^dag v
 int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, double *yc, int nrhs);
+// the same for the plain Rademacher noise of samples sample0 .. sample0 +
+// nrhs - 1 of seed (the fields gen_noise_eo writes, passed as ve, vo for the
+// FP64 path): in double-float arithmetic from the noise's sign words
+int mg_restrict_t_noise(wd_ctx *c, uint64_t seed, int sample0, const double *ve, const double *vo, double *Rt,
+                        double *yc, int nrhs);
 // part[r][t] = sum_{x in t} v_r(x)^dag B (P y_r)(x) from the per-timeslice
 // restriction Rt of v (B = 1 or g5); part: device complex [nrhs][T]
 int mg_contract_rt(wd_ctx *c, const double *Rt, const double *y, int gamma5, int nrhs, double *part);

@@ -450,6 +450,75 @@ __global__ void k_restrict_t(const double2 *P, const float2 *Ph, const float2 *P
     }
 }
 
+// The same restriction for Rademacher noise (every entry +1 or -1, given as
+// sign words: bit r of bits[(p Vh + s) 12 + comp] set where sample r0w + r is
+// -1), with P as Phi + Plo: conj(P) eta is +/- conj(P), so each term is a
+// double-float addition (TwoSum on the high parts, the low parts and the
+// TwoSum errors summed in FP32 and folded into the pair once per site)
+// instead of a double-float multiply-add, and the noise field is not read.
+// A thread takes one (X, tau, i) for RT of the word's samples.
+template <int RT>
+__global__ void k_restrict_t_sign(const float2 *Ph, const float2 *Pl, const unsigned long long *bits, double2 *Rt,
+                                  MgGeom M, int nw, int r0w, int nrhs) {
+    const int at = M.agg[3];
+    const int ngrp = (nw + RT - 1) / RT;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)ngrp * M.Vc * at * M.ncd) return;
+    const int i = (int)(t % M.ncd);
+    long rest = t / M.ncd;
+    const int tau = (int)(rest % at);
+    rest /= at;
+    const int X = (int)(rest % M.Vc), rg = (int)(rest / M.Vc) * RT;
+    const int nr = nw - rg < RT ? nw - rg : RT;
+    const int h = i / M.nv, k = i % M.nv;
+    int o[4];
+    {
+        int r = X;
+        for (int m = 0; m < 4; ++m) { o[m] = (r % M.cd[m]) * M.agg[m]; r /= M.cd[m]; }
+        o[3] += tau;
+    }
+    float reh[RT], rel[RT], imh[RT], iml[RT];
+#pragma unroll
+    for (int q = 0; q < RT; ++q) { reh[q] = 0.f; rel[q] = 0.f; imh[q] = 0.f; iml[q] = 0.f; }
+    for (int dz = 0; dz < M.agg[2]; ++dz)
+        for (int dy = 0; dy < M.agg[1]; ++dy)
+            for (int dx = 0; dx < M.agg[0]; ++dx) {
+                const int c0 = o[0] + dx, c1 = o[1] + dy, c2 = o[2] + dz;
+                const int site = c0 + M.g.X * (c1 + M.g.Y * (c2 + M.g.Z * o[3]));
+                const int par = (c0 + c1 + c2 + o[3]) & 1, sh = site >> 1;
+                const size_t eo = ((size_t)par * M.g.Vh + sh) * 12 + 6 * h;
+#pragma unroll 2
+                for (int qc = 0; qc < 6; ++qc) {
+                    const size_t pi = (eo + qc) * M.nv + k;
+                    const float2 mh = __ldg(Ph + pi), ml = __ldg(Pl + pi);
+                    const unsigned long long w = __ldg(bits + eo + qc) >> rg;
+#pragma unroll
+                    for (int q = 0; q < RT; ++q) {
+                        // conj(P) eta: (Pr, -Pi) times +1 or -1
+                        const float sr = ((w >> q) & 1) ? -1.f : 1.f;
+                        float sv, e;
+                        two_sum(reh[q], sr * mh.x, sv, e);
+                        reh[q] = sv;
+                        rel[q] = __fadd_rn(rel[q], __fadd_rn(e, sr * ml.x));
+                        two_sum(imh[q], -sr * mh.y, sv, e);
+                        imh[q] = sv;
+                        iml[q] = __fadd_rn(iml[q], __fadd_rn(e, -sr * ml.y));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < RT; ++q) {
+                    float sv, e;
+                    two_sum(reh[q], rel[q], sv, e); reh[q] = sv; rel[q] = e;
+                    two_sum(imh[q], iml[q], sv, e); imh[q] = sv; iml[q] = e;
+                }
+            }
+#pragma unroll
+    for (int q = 0; q < RT; ++q)
+        if (q < nr)
+            Rt[((((size_t)(r0w + rg + q) * M.Vc + X) * at) + tau) * M.ncd + i] =
+                make_double2(__dadd_rn((double)reh[q], (double)rel[q]), __dadd_rn((double)imh[q], (double)iml[q]));
+}
+
 // yc[r][X][i] = sum_tau Rt[r][X][tau][i], tau ascending
 __global__ void k_sum_tau(const double2 *Rt, double2 *yc, MgGeom M, int nrhs) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -1400,6 +1469,37 @@ int mg_restrict_t_eo(wd_ctx *c, const double *ve, const double *vo, double *Rt, 
         WD_RT_CASE(8) WD_RT_CASE(16)
 #undef WD_RT_CASE
         c->launches++;
+    }
+    const long nc = (long)nrhs * M.Vc * M.ncd;
+    k_sum_tau<<<(unsigned)((nc + 255) / 256), 256, 0, c->st>>>((const double2 *)Rt, (double2 *)yc, M, nrhs);
+    c->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int gen_noise_signs(wd_ctx *c, uint64_t seed, int sample0, int nrhs, unsigned long long *bits);   // wd_estim.cu
+
+int mg_restrict_t_noise(wd_ctx *c, uint64_t seed, int sample0, const double *ve, const double *vo, double *Rt,
+                        double *yc, int nrhs) {
+    if (!(c->outer == PDD && c->mg->Phi)) return mg_restrict_t_eo(c, ve, vo, Rt, yc, nrhs);
+    const MgGeom M = mg_geom(c);
+    // samples per thread: each P entry is read once per RT samples
+    int RT = 16;
+    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 16 or 32
+        const int r = atoi(e);
+        if (r == 16 || r == 32) RT = r;
+    }
+    unsigned long long *bits;
+    WD_TRY(ws_get(c, "mg.signs", sizeof(unsigned long long) * 12 * (size_t)M.g.V, (void **)&bits));
+    for (int w0 = 0; w0 < nrhs; w0 += 64) {
+        const int nw = nrhs - w0 < 64 ? nrhs - w0 : 64;
+        WD_TRY(gen_noise_signs(c, seed, sample0 + w0, nw, bits));
+        const long n = (long)((nw + RT - 1) / RT) * M.Vc * M.agg[3] * M.ncd;
+        const unsigned blocks = (unsigned)((n + 127) / 128);
+        if (RT == 32) k_restrict_t_sign<32><<<blocks, 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, bits, (double2 *)Rt, M, nw, w0, nrhs);
+        else k_restrict_t_sign<16><<<blocks, 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, bits, (double2 *)Rt, M, nw, w0, nrhs);
+        c->launches++;
+        WD_CUDA(cudaGetLastError());
     }
     const long nc = (long)nrhs * M.Vc * M.ncd;
     k_sum_tau<<<(unsigned)((nc + 255) / 256), 256, 0, c->st>>>((const double2 *)Rt, (double2 *)yc, M, nrhs);

@@ -230,7 +230,7 @@ int mlmc2_estimate(wd_ctx *c, int N1, int N2, uint64_t seed, int gamma5, int pre
         double *Rt, *part;
         WD_TRY(ws_get(c, "mlmc.rt", sizeof(double2) * ncoarse * c->mg->agg[3] * nb, (void **)&Rt));
         WD_TRY(ws_get(c, "mlmc.part", sizeof(double) * 2 * (size_t)nb * T, (void **)&part));
-        WD_TRY(mg_restrict_t_eo(c, be, bo, Rt, bc, nb));
+        WD_TRY(mg_restrict_t_noise(c, seed, s0, be, bo, Rt, bc, nb));
         s = coarse_solve(c, bc, yc, nb, tol, prec, 100000, nullptr);
         if (s != WD_OK) return s;
         // X_1(t) = eta^dag B z - sum_{x in t} eta^dag B (P y): the first on the

@@ -182,10 +182,12 @@ def test_coarse_solve(prec, case):
 
 
 @pytest.mark.parametrize("gamma5", [0, 1])
-@pytest.mark.parametrize("N1", [6, 40])
+@pytest.mark.parametrize("N1", [6, 40, 70])
 def test_mlmc2_per_sample(gamma5, N1):
-    """Per-sample parity of both levels; N1 = 40 takes the 32-RHS restriction
-    tiles (a full and a ragged one)."""
+    """Per-sample parity of both levels.  The level-1 restriction of the noise
+    works on sign words of 64 samples in tiles of 16 samples per thread:
+    N1 = 40 takes full tiles and a ragged one, N1 = 70 a full word and a
+    second one of 6 samples."""
     from paper_2607_05157_b300 import trace_estimate, wd_mlmc_level2_samples, WD_MLMC2
     dims, agg, nv = (4, 4, 4, 4), (2, 2, 2, 2), 6
     ctx, U, D, P = _setup(dims, agg, nv, kappa=0.12, seed=1001)
