@@ -649,6 +649,240 @@ __global__ void __launch_bounds__(256, 1) hop_staged_f2(HopArgs A, int tlen) {
     }
 }
 
+// ---- plane-walk variant: persistent CTAs walk z through a timeslice --------
+// A unit is (RHS tile of 2, timeslice t); a CTA takes units u = blockIdx.x,
+// blockIdx.x + gridDim.x, ... and walks z = 0 .. Z-1 through each.  A ring of
+// 4 shared-memory slots holds the tile's input (other parity) x-y planes
+// z-1, z, z+1 and the next plane in flight, each a set of 1D cp.async.bulk
+// copies (one per RHS and 16-byte channel; a plane is contiguous in every
+// channel) completing on the slot's mbarrier; all waits are bounded.  The
+// x, y and z neighbours of a site come from shared memory, so every input
+// spinor crosses L2 once for them; the t neighbours, the links and the
+// addends are plain loads.  One thread per (plane site, RHS of the tile).
+// Units go in bands of W timeslices with all RHS tiles of a band together:
+// the tiles running at one time share the band's links in L2, and the t
+// neighbours of a unit are planes that the units at t - 1 and t + 1 stage
+// at about the same time.
+static constexpr int PW_SLOTS = 4;
+
+__device__ __forceinline__ void pw_unit(const HopArgs &A, int W, int ntiles, int u, int &rb, int &t) {
+    const int per = ntiles * W, band = u / per, rem = u - band * per;
+    rb = rem / W;
+    t = band * W + (rem - rb * W);
+}
+
+// plane j (-1 .. Z) of unit u into slot n & 3 (thread 0 only)
+__device__ __forceinline__ void pw_issue(const HopArgs &A, unsigned char *smem, size_t slot_bytes, uint64_t *full,
+                                        int *loads, int S, int W, int ntiles, int u, int j, int n) {
+    int rb, t;
+    pw_unit(A, W, ntiles, u, rb, t);
+    const int Z = A.g.Z, z = (j + Z) % Z, q = n & (PW_SLOTS - 1);
+    const long Vh = A.g.Vh;
+    const size_t off = ((size_t)t * Z + z) * S;
+    int nr = 0;
+    for (int r = 0; r < 2; ++r) nr += tile_rhs(A, rb, r, 2) >= 0;
+    const uint32_t bytes = (uint32_t)nr * 6 * S * 16;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(st_u32(&full[q])), "r"(bytes) : "memory");
+    for (int r = 0; r < 2; ++r) {
+        const int rhs = tile_rhs(A, rb, r, 2);
+        if (rhs < 0) continue;
+        for (int k = 0; k < 6; ++k) {
+            unsigned char *dst = smem + q * slot_bytes + (size_t)(r * 6 + k) * S * 16;
+            const uint4 *src = (const uint4 *)A.in + ((size_t)rhs * 6 + k) * Vh + off;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(st_u32(dst)), "l"((uint64_t)src), "r"((uint32_t)S * 16), "r"(st_u32(&full[q]))
+                         : "memory");
+        }
+    }
+    loads[q] += 1;
+}
+
+// one hop term: acc += (1 -/+ g_mu) U psi for the link u (split as the f32x2
+// multiplier pairs ur, ui) and the neighbour spinor psi
+template <int MU, int SIGN>
+__device__ __forceinline__ void pw_term(const float2 ur[9], const float2 ui[9], const float2 psi[12],
+                                        float2 acc[12]) {
+    float2 h[6], hs[6], uh[6];
+    proj_f2<MU, SIGN>(psi, h);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = sw(h[k]);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float2 a = __fmul2_rn(ur[3 * i], h[3 * sp]);
+            a = __ffma2_rn(ui[3 * i], hs[3 * sp], a);
+#pragma unroll
+            for (int j = 1; j < 3; ++j) {
+                a = __ffma2_rn(ur[3 * i + j], h[3 * sp + j], a);
+                a = __ffma2_rn(ui[3 * i + j], hs[3 * sp + j], a);
+            }
+            uh[3 * sp + i] = a;
+        }
+    recon_f2<MU, SIGN>(acc, uh);
+}
+
+template <int D, bool DAG>
+__device__ __forceinline__ void pw_dir(const HopArgs &A, long s, const float2 psi[12], float2 acc[12]) {
+    constexpr int MU = D & 3;
+    constexpr int SIGN = ((D < 4) != DAG) ? -1 : +1;
+    const long Vh = A.g.Vh;
+    cx<float> u[9];
+    LIO<float>::load((const char *)A.gauge + (size_t)D * 9 * Vh * LIO<float>::ELEM, Vh, s, u);
+    float2 ur[9], ui[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { ur[k] = f2(u[k].re, u[k].re); ui[k] = f2(-u[k].im, u[k].im); }
+    pw_term<MU, SIGN>(ur, ui, psi, acc);
+}
+
+template <bool DAG>
+__global__ void __launch_bounds__(576, 1) hop_plane_f2(HopArgs A, int W) {
+    const Geom &g = A.g;
+    const long Vh = g.Vh;
+    const int Z = g.Z, T = g.T, S = (int)(Vh / ((long)Z * T));
+    const size_t slot_bytes = (size_t)2 * 6 * S * 16;
+    extern __shared__ __align__(128) unsigned char pw_smem[];
+    uint64_t *full = (uint64_t *)(pw_smem + PW_SLOTS * slot_bytes);
+    __shared__ int s_fail;
+    __shared__ int s_loads[PW_SLOTS];
+    const int nact = A.alist ? __ldg(A.acount) : A.nrhs;
+    const int ntiles = (nact + 1) / 2, nunits = ntiles * T;
+    if ((int)blockIdx.x >= nunits) return;                 // uniform in the CTA, before any barrier
+    const int my_units = (nunits - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+    const int nitems = my_units * (Z + 2);
+    const int tid = threadIdx.x, rs = tid / S, so = tid - rs * S;
+    int issued = 0;                                        // thread 0's count of plane copies issued
+    if (tid == 0) {
+        for (int q = 0; q < PW_SLOTS; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(st_u32(&full[q])));
+            s_loads[q] = 0;
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (; issued < nitems && issued < PW_SLOTS; ++issued)
+            pw_issue(A, pw_smem, slot_bytes, full, s_loads, S, W, ntiles, blockIdx.x + (issued / (Z + 2)) * gridDim.x,
+                     issued % (Z + 2) - 1, issued);
+    const float2 a2 = f2((float)A.a, (float)A.a), b2 = f2((float)A.b, (float)A.b), c2 = f2((float)A.c, (float)A.c);
+    for (int k = 0; k < my_units && !s_fail; ++k) {
+        int rb, t;
+        pw_unit(A, W, ntiles, blockIdx.x + k * gridDim.x, rb, t);
+        const int rhs = rs < 2 ? tile_rhs(A, rb, rs, 2) : -1;
+        const int tp = t + 1 == T ? 0 : t + 1, tm = t == 0 ? T - 1 : t - 1;
+        for (int z = 0; z < Z; ++z) {
+            const int n0 = k * (Z + 2) + z;                // item of plane z - 1
+            bool ok = true;
+            for (int m = 0; m < 3; ++m) ok = ok && st_wait(&full[(n0 + m) & (PW_SLOTS - 1)], ((n0 + m) >> 2) & 1);
+            if (!ok) s_fail = 1;
+            __syncthreads();
+            if (s_fail) break;
+            if (rhs >= 0) {
+                const unsigned char *pm = pw_smem + ((n0) & (PW_SLOTS - 1)) * slot_bytes + (size_t)rs * 6 * S * 16;
+                const unsigned char *p0 = pw_smem + ((n0 + 1) & (PW_SLOTS - 1)) * slot_bytes + (size_t)rs * 6 * S * 16;
+                const unsigned char *pp = pw_smem + ((n0 + 2) & (PW_SLOTS - 1)) * slot_bytes + (size_t)rs * 6 * S * 16;
+                const int xh = so % g.Xh, y = so / g.Xh;
+                const int x = 2 * xh + ((A.p + y + z + t) & 1);
+                const int xp = x + 1 == g.X ? 0 : x + 1, xm = x == 0 ? g.X - 1 : x - 1;
+                const int yp = y + 1 == g.Y ? 0 : y + 1, ym = y == 0 ? g.Y - 1 : y - 1;
+                const long s = ((long)t * Z + z) * S + so;
+                const uint4 *in = (const uint4 *)A.in + (size_t)rhs * 6 * Vh;
+                float2 acc[12];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) acc[q] = f2(0.f, 0.f);
+                float2 psi[12];
+                load_f2<float>(in, Vh, ((long)tp * Z + z) * S + so, psi);
+                pw_dir<3, DAG>(A, s, psi, acc);
+                load_f2<float>(in, Vh, ((long)tm * Z + z) * S + so, psi);
+                pw_dir<7, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(p0, S, y * g.Xh + (xp >> 1), psi);
+                pw_dir<0, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(p0, S, y * g.Xh + (xm >> 1), psi);
+                pw_dir<4, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(p0, S, yp * g.Xh + xh, psi);
+                pw_dir<1, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(p0, S, ym * g.Xh + xh, psi);
+                pw_dir<5, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(pp, S, so, psi);
+                pw_dir<2, DAG>(A, s, psi, acc);
+                load_smem_f2<float>(pm, S, so, psi);
+                pw_dir<6, DAG>(A, s, psi, acc);
+                float2 o[12];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) o[q] = __fmul2_rn(b2, acc[q]);
+                if (A.w) {
+                    float2 wv[12];
+                    load_f2<float>((const uint4 *)A.w + (size_t)rhs * 6 * Vh, Vh, s, wv);
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) o[q] = __ffma2_rn(a2, wv[q], o[q]);
+                }
+                if (A.w2) {
+                    float2 wv[12];
+                    load_f2<float>((const uint4 *)A.w2 + (size_t)rhs * 6 * Vh, Vh, s, wv);
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) o[q] = __ffma2_rn(c2, wv[q], o[q]);
+                }
+                cx<float> oc[12];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) oc[q] = cmake(o[q].x, o[q].y);
+                SIO<float>::store((uint4 *)A.out + (size_t)rhs * 6 * Vh, Vh, s, oc);
+            }
+            // every thread is done with plane z - 1: order its reads before the
+            // async refill, then top the ring up from the first item still needed
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const int need = z + 1 < Z ? n0 + 1 : n0 + 3;
+                for (; issued < nitems && issued < need + PW_SLOTS; ++issued)
+                    pw_issue(A, pw_smem, slot_bytes, full, s_loads, S, W, ntiles,
+                             blockIdx.x + (issued / (Z + 2)) * gridDim.x, issued % (Z + 2) - 1, issued);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_fail) {
+        if (A.err) atomicExch(A.err, 1);
+        // copies already issued must land before the shared memory is released
+        for (int q = 0; q < PW_SLOTS; ++q)
+            if (s_loads[q] > 0) st_wait(&full[q], (s_loads[q] - 1) & 1);
+    }
+}
+
+size_t hop_plane_smem(const Geom &g) {
+    return (size_t)PW_SLOTS * 2 * 6 * (g.Vh / ((long)g.Z * g.T)) * 16 + PW_SLOTS * 8;
+}
+
+template <typename SIn, typename SOut, typename SW, typename G>
+cudaError_t launch_hop_plane(const HopArgs &A0, bool dag, cudaStream_t st) {
+    if constexpr (!(std::is_same<SIn, float>::value && std::is_same<SOut, float>::value &&
+                    std::is_same<SW, float>::value && std::is_same<G, float>::value)) {
+        return cudaErrorNotSupported;
+    } else {
+        HopArgs A = A0;
+        if (A.nrhs <= 0) return cudaSuccess;
+        const int S = (int)(A.g.Vh / ((long)A.g.Z * A.g.T));
+        const size_t smem = hop_plane_smem(A.g);
+        const int th = 2 * S;
+        if (th > 576 || A.g.Z < 3 || smem > 227 * 1024) return cudaErrorNotSupported;
+        int W = 1;                                           // the largest divisor of T up to 12
+        for (int w = 1; w <= 12 && w <= A.g.T; ++w)
+            if (A.g.T % w == 0) W = w;
+        int dev = 0, sms = 148, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int ntiles = (A.nrhs + 1) / 2;
+        auto kern = dag ? hop_plane_f2<true> : hop_plane_f2<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, th, smem);
+        if (per < 1) return cudaErrorNotSupported;
+        long grid = (long)sms * per;
+        if (grid > (long)ntiles * A.g.T) grid = (long)ntiles * A.g.T;
+        kern<<<(unsigned)grid, th, smem, st>>>(A, W);
+        return cudaGetLastError();
+    }
+}
+
 size_t hop_staged_smem(const HopArgs &A, int R, int nch) {
     if (A.g.Vh % A.g.T) return 0;
     return (size_t)ST_SLOTS * R * nch * (A.g.Vh / A.g.T) * 16 + ST_SLOTS * 8;
@@ -705,9 +939,11 @@ cudaError_t launch_hop(const HopArgs &A0, int R, bool dag, int threads, cudaStre
     // 32, 34 / 41, 42, 44: next-direction prefetch into L1 / L2; R = 51, 52,
     // 54: plain with the site tile fastest in the block order; R = 62: two RHS,
     // registers capped for 20 resident warps per SM; R = 63, 64, 65: the same
-    // with the RHS tiles in groups of 4, 8, 16 (site tile fastest within a group)
+    // with the RHS tiles in groups of 4, 8, 16 (site tile fastest within a group);
+    // R = 71: persistent plane walk with x-y planes staged in shared memory
     constexpr bool PACKED = !std::is_same<typename RealOf<SIn>::type, double>::value;
     if (R > 20 && R < 30) return launch_hop_staged<SIn, SOut, SW, G>(A, R - 20, dag, st);
+    if (R == 71) return launch_hop_plane<SIn, SOut, SW, G>(A, dag, st);
     if (R >= 62 && R <= 65) {   // two RHS, register cap for 5 CTAs of 128 threads per SM
         // 62: site tile fastest; 63, 64, 65: RHS tiles in groups of 4, 8, 16
         if (!PACKED || threads > 128) return cudaErrorNotSupported;
