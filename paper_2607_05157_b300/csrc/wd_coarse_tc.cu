@@ -418,8 +418,9 @@ int coarse_tc_build(wd_ctx *c) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&g->tc_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g->tc_sms <= 0)
         g->tc_sms = 148;
-    if (cudaMalloc(&g->Wtc, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wtc = nullptr; return WD_OK; }
-    if (cudaMalloc(&g->Wlo, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wlo = nullptr; }
+    // (kept from a previous setup of the same geometry, else allocated)
+    if (!g->Wtc && cudaMalloc(&g->Wtc, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wtc = nullptr; return WD_OK; }
+    if (!g->Wlo && cudaMalloc(&g->Wlo, n * sizeof(bf16)) != cudaSuccess) { cudaGetLastError(); g->Wlo = nullptr; }
     int *err;
     WD_TRY(ws_get(c, "tc.err", sizeof(int), (void **)&err));
     WD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->st));

@@ -23,6 +23,8 @@
 
 #include <vector>
 
+#include <chrono>
+
 #include "wd_internal.h"
 #include "wd_dd.cuh"
 
@@ -1633,9 +1635,16 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     const int ncd = 2 * nv;
     const size_t smem = sizeof(double2) * ((size_t)ncd * ncd + 4 * 12 * ncd);
     if (smem > 227 * 1024) { set_error("wd_mg_setup: nv too large for the block assembly"); return WD_ENOTSUP; }
-    wd_mg_free(c);
-    wd_mg *g = new wd_mg();
-    memset(g, 0, sizeof(*g));
+    // A new setup with the geometry of the current one (the same N_v and
+    // aggregates, e.g. the next gauge configuration) overwrites its buffers in
+    // place: ~8 GB at 24^3x48 that need not be freed and mapped again.  The
+    // third level, built on the old operator, goes.
+    const bool reuse = c->mg && c->mg->nv == nv && c->mg->agg[0] == agg[0] && c->mg->agg[1] == agg[1] &&
+                       c->mg->agg[2] == agg[2] && c->mg->agg[3] == agg[3];
+    if (reuse) wd_mg3_free(c);
+    else wd_mg_free(c);
+    wd_mg *g = reuse ? c->mg : new wd_mg();
+    if (!reuse) memset(g, 0, sizeof(*g));
     c->mg = g;
     g->nv = nv;
     g->ncd = ncd;
@@ -1643,19 +1652,32 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     for (int m = 0; m < 4; ++m) { g->agg[m] = agg[m]; g->cd[m] = c->dims[m] / agg[m]; g->Vc *= g->cd[m]; }
     const size_t nP = (size_t)c->g.V * 12 * nv;
     const size_t nD = (size_t)g->Vc * 9 * ncd * ncd;
-    if (cudaMalloc(&g->P, nP * sizeof(double2)) != cudaSuccess || cudaMalloc(&g->Dc, nD * sizeof(double2)) != cudaSuccess ||
+    if (!reuse && (cudaMalloc(&g->P, nP * sizeof(double2)) != cudaSuccess || cudaMalloc(&g->Dc, nD * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&g->nbr, sizeof(int) * 9 * g->Vc) != cudaSuccess || cudaMalloc(&g->Dc32, nD * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Dclo, nD * sizeof(float2)) != cudaSuccess || cudaMalloc(&g->Phi, nP * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Plo, nP * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->Gt, sizeof(double2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess ||
         cudaMalloc(&g->Ghi, sizeof(float2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess ||
-        cudaMalloc(&g->Glo, sizeof(float2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess) {
+        cudaMalloc(&g->Glo, sizeof(float2) * (size_t)g->Vc * agg[3] * 2 * nv * nv) != cudaSuccess)) {
         cudaGetLastError();
         wd_mg_free(c);
         set_error("wd_mg_setup: allocation failed");
         return WD_ENOMEM;
     }
     MgGeom M = mg_geom(c);
+    // WD_VERBOSE: the wall time of each phase (the stream synchronised at the
+    // phase ends, so only then)
+    const bool verbose = getenv("WD_VERBOSE") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto phase = [&](const char *name) {
+        if (!verbose) return;
+        cudaStreamSynchronize(c->st);
+        const auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[wd] setup %-24s %8.2f ms\n", name,
+                std::chrono::duration<double, std::milli>(now - t_last).count());
+        t_last = now;
+    };
+    phase("allocation");
     double *tvd;
     WD_TRY(ws_get(c, "mg.tv", nP * sizeof(double2), (void **)&tvd));
     if (tv) {
@@ -1663,16 +1685,19 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
     } else {
         WD_TRY(mg_generate_tv(c, nv, tv_iters, seed, tvd));
     }
+    phase("test vectors");
     k_tv_to_P<<<(unsigned)((nP + 255) / 256), 256, 0, c->st>>>((const double2 *)tvd, g->P, M);
     // block MGS on a column-major copy of the blocks (coalesced passes), kept in
     // the test-vector workspace, which P has been built from (same size)
     k_mgs_gather<<<1184, 256, 0, c->st>>>(g->P, (double2 *)tvd, M, 1);
     k_block_mgs_cm<<<2 * g->Vc, 256, 0, c->st>>>((double2 *)tvd, M);
     k_mgs_gather<<<1184, 256, 0, c->st>>>(g->P, (double2 *)tvd, M, 0);
+    phase("block MGS");
     k_coarse_nbr<<<(g->Vc + 127) / 128, 128, 0, c->st>>>(g->nbr, M);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->P, g->Phi, g->Plo, (long)nP);
     if (c->outer == PDD) k_gram_t_dd<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->Phi, g->Plo, g->Gt, M);
     else k_gram_t<<<g->Vc * agg[3] * 2, 256, 0, c->st>>>(g->P, g->Gt, M);
+    phase("P pairs, Gram matrices");
     double2 hg[4][4][4];
     host_gamma(hg);
     WD_CUDA(cudaMemcpyToSymbolAsync(c_gamma, hg, sizeof(hg), 0, cudaMemcpyHostToDevice, c->st));
@@ -1711,12 +1736,14 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
         WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
     }
+    phase("Galerkin assembly");
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Gt, g->Ghi, g->Glo, (long)g->Vc * agg[3] * 2 * nv * nv);
     c->launches += 8;
     WD_CUDA(cudaGetLastError());
     WD_TRY(coarse_tc_build(c));
     WD_CUDA(cudaStreamSynchronize(c->st));
+    phase("coarse copies, TC operand");
     return WD_OK;
 }
 

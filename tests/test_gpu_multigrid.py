@@ -527,3 +527,36 @@ def test_fp32_coarse_stencil_tiled(monkeypatch):
         ref = (Dc @ x[r].reshape(-1)).reshape(Vc, ncd)
         assert np.all(np.abs(y[r] - ref) <= u * _coarse_abs_bound(A, nbr, x[r])), r
     ctx.close()
+
+
+def test_setup_again_after_new_links():
+    """The path of the end-to-end loop: wd_update_gauge (new links, new kappa)
+    and a second wd_mg_setup of the same geometry on the same context, which
+    overwrites the multigrid buffers in place.  The coarse operator is then
+    the oracle's P^dag D P of the new links (FP64 to 1e-12, the tensor-core
+    BF16-pair path element by element); a third setup of another N_v
+    allocates afresh and is right as well."""
+    import torch
+    from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply, wd_update_gauge
+    dims, agg = (8, 8, 8, 8), (2, 2, 2, 2)
+    ctx = Context(dims, synth.gauge_field(dims, 0.5, 1010), 0.13, BC)
+    wd_mg_setup(ctx.h, synth.test_vectors(dims, 24, 80), 24, agg)
+    U2 = synth.gauge_field(dims, 0.5, 1011)
+    wd_update_gauge(ctx.h, U2, 0.12)
+    D2 = wilson.sparse_matrix(U2, 0.12, BC)
+    rng = np.random.default_rng(17)
+    for nv, seed in ((24, 81), (12, 82)):
+        tv = synth.test_vectors(dims, nv, seed)
+        wd_mg_setup(ctx.h, tv, nv, agg)
+        Dc = multigrid.coarse_operator(D2, multigrid.prolongator(tv, dims, agg))
+        Dabs = Dc.copy()
+        Dabs.data = np.abs(Dabs.data)
+        cs = _coarse_shape(dims, agg, nv, 3)
+        x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+        y64 = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
+        ysp = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 1).cpu().numpy()
+        for r in range(3):
+            ref = Dc @ x[r].reshape(-1)
+            assert rel(y64[r].reshape(-1), ref) < 1e-12, (nv, r)
+            assert np.all(np.abs(ysp[r].reshape(-1) - ref) <= u_split(2 * nv) * (Dabs @ np.abs(x[r].reshape(-1)))), (nv, r)
+    ctx.close()
