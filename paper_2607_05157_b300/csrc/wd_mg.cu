@@ -460,7 +460,8 @@ __global__ void k_restrict_t(const double2 *P, const float2 *Ph, const float2 *P
 // instead of a double-float multiply-add, and the noise field is not read.
 // A thread takes one (X, tau, i) for RT of the word's samples.
 template <int RT>
-__global__ void k_restrict_t_sign(const float2 *Ph, const float2 *Pl, const unsigned long long *bits, double2 *Rt,
+__global__ void __launch_bounds__(128, RT <= 8 ? 6 : 4) k_restrict_t_sign(const float2 *Ph, const float2 *Pl,
+                                                                          const unsigned long long *bits, double2 *Rt,
                                   MgGeom M, int nw, int r0w, int nrhs) {
     const int at = M.agg[3];
     const int ngrp = (nw + RT - 1) / RT;
@@ -1487,9 +1488,9 @@ int mg_restrict_t_noise(wd_ctx *c, uint64_t seed, int sample0, const double *ve,
     const MgGeom M = mg_geom(c);
     // samples per thread: each P entry is read once per RT samples
     int RT = 16;
-    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 16 or 32
+    if (const char *e = getenv("WD_RESTRICT_RT")) {   // tuning override: 8, 16 or 32
         const int r = atoi(e);
-        if (r == 16 || r == 32) RT = r;
+        if (r == 8 || r == 16 || r == 32) RT = r;
     }
     unsigned long long *bits;
     WD_TRY(ws_get(c, "mg.signs", sizeof(unsigned long long) * 12 * (size_t)M.g.V, (void **)&bits));
@@ -1499,6 +1500,7 @@ int mg_restrict_t_noise(wd_ctx *c, uint64_t seed, int sample0, const double *ve,
         const long n = (long)((nw + RT - 1) / RT) * M.Vc * M.agg[3] * M.ncd;
         const unsigned blocks = (unsigned)((n + 127) / 128);
         if (RT == 32) k_restrict_t_sign<32><<<blocks, 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, bits, (double2 *)Rt, M, nw, w0, nrhs);
+        else if (RT == 8) k_restrict_t_sign<8><<<blocks, 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, bits, (double2 *)Rt, M, nw, w0, nrhs);
         else k_restrict_t_sign<16><<<blocks, 128, 0, c->st>>>(c->mg->Phi, c->mg->Plo, bits, (double2 *)Rt, M, nw, w0, nrhs);
         c->launches++;
         WD_CUDA(cudaGetLastError());
