@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_contract_coarse_t(const double2 *Gt, co
 // each G row is read once for the CR RHS of the tile (the timeslice's G is
 // 4 MB, read from L2 by every CTA of that timeslice).
 template <int CR>
-__global__ void __launch_bounds__(256) k_contract_coarse_t_dd(const float2 *Gh, const float2 *Gl, const double2 *a,
+__global__ void __launch_bounds__(256, CR <= 4 ? 3 : 2) k_contract_coarse_t_dd(const float2 *Gh, const float2 *Gl, const double2 *a,
                                                               const float4 *b, int gamma5, double *part, MgGeom M,
                                                               int nrhs) {
     __shared__ double2 sh[32];
@@ -1427,9 +1427,19 @@ int mg_contract_coarse_t(wd_ctx *c, const double *a, const double *b, int gamma5
         const long nc = (long)nrhs * M.Vc * M.ncd;
         WD_TRY(ws_get(c, "mg.cdd", (size_t)nc * sizeof(float4), &bd));
         WD_CUDA(launch_to_ddl(b, bd, nc, c->st));
-        constexpr int CR = 8;
-        k_contract_coarse_t_dd<CR><<<dim3((nrhs + CR - 1) / CR, c->g.T), 256, 0, c->st>>>(
-            g->Ghi, g->Glo, (const double2 *)a, (const float4 *)bd, gamma5, part, M, nrhs);
+        // RHS per CTA tile: 4 (79 registers, three CTAs of 256 threads per SM)
+        // beats 8 (125 registers, two CTAs): the kernel is bound by the latency
+        // of its loads (ncu: issue 52 %, long-scoreboard stalls), not by the G
+        // rows it reads once per tile.  Two-level step on 24^3x48: 0.366 ->
+        // 0.361 s.  WD_CONTRACT_CR = 8 restores the larger tile.
+        int cr = 4;
+        if (const char *e = getenv("WD_CONTRACT_CR")) cr = atoi(e) == 8 ? 8 : 4;
+        if (cr == 4)
+            k_contract_coarse_t_dd<4><<<dim3((nrhs + 3) / 4, c->g.T), 256, 0, c->st>>>(
+                g->Ghi, g->Glo, (const double2 *)a, (const float4 *)bd, gamma5, part, M, nrhs);
+        else
+            k_contract_coarse_t_dd<8><<<dim3((nrhs + 7) / 8, c->g.T), 256, 0, c->st>>>(
+                g->Ghi, g->Glo, (const double2 *)a, (const float4 *)bd, gamma5, part, M, nrhs);
         c->launches += 2;
     } else {
         k_contract_coarse_t<<<dim3(nrhs, c->g.T), 256, 0, c->st>>>(g->Gt, (const double2 *)a, (const double2 *)b,
