@@ -657,7 +657,8 @@ def main():
     kern = {}
     for name, label in (("hop32", f"hop_kernel ({args.prec} storage, fine stencil)"),
                         ("hop64", "hop_kernel_dd (double-float FP64 steps, fine stencil)"),
-                        ("coarse", "k_coarse_tc (tcgen05 coarse 9-point stencil)")):
+                        ("coarse", "coarse 9-point stencil: k_coarse_tc (tcgen05, inner solves) and "
+                                   "k_coarse_apply32t (FP32 CUDA cores, recursive residual updates)")):
         n, t_ms, b = prof[name][0], prof[name][1], prof[name][2]
         kern[name] = {"kernel": label, "launches_per_step": n / max(args.steps, 1),
                       "GB_s": b / (t_ms * 1e-3) / 1e9 if t_ms else None,
@@ -738,6 +739,21 @@ def main():
                                                   f"x{N1 // sub1} to the step's {N1} + {N2}",
                               "max_sample_diff_over_eps": dmax / eps, "std_error_eps": eps}
     if rank == 0 and not args.no_secondary:
+        # the same 64 fine noise samples through plain Hutchinson (Eq. 3) on the
+        # same context: the cost of the two-level split against the estimator
+        # it refines (one warm-up, then the mean of three)
+        api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, N1, T, seed=seed0 + 1000, op=1, prec=prec, tol=TOL)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record()
+        for _ in range(3):
+            hut = api.trace_estimate(ctx.h, wd.WD_HUTCH, 1, N1, T, seed=seed0 + 1000, op=1, prec=prec, tol=TOL)
+        h1.record()
+        torch.cuda.synchronize()
+        ms_h = h0.elapsed_time(h1) / 3
+        line["mlmc2_vs_hutchinson"] = {
+            "workload": f"{WORKLOAD.split(':')[0]}; Hutchinson with the {N1} level-1 noise samples, same solver",
+            "hutchinson_ms": ms_h, "mlmc2_ms": ms / args.steps, "mlmc2_over_hutchinson": (ms / args.steps) / ms_h,
+            "hutchinson_var_total": hut["var_total"], "mlmc2_var_total": results[0]["var_total"]}
         sec = {}
         for name, fn in (("trace_8x8x8x16", lambda: small_trace_measure(wd, api, torch, synth)),
                          ("probing_16x16x16x32", lambda: probing_measure(wd, api, torch, synth)),
