@@ -641,7 +641,8 @@ __global__ void k_coarse_nbr(int *nbr, MgGeom M) {
         }
 }
 
-// Block b of D_c at coarse site X; one CTA per (X, b).  For each site x of
+// Block b of D_c at coarse site X (b = 0 .. 4: the site block and the forward
+// ones; k_dc_backward derives the rest); one CTA per (X, b).  For each site x of
 // the aggregate: A += P(x)^dag sum_hop coef [Gamma (x) U] P(y) over the hops
 // x -> y of the block (the identity and the internal hops for b = 0), with
 // P(.) the 12 x ncd restriction of the columns to one site: one ncd x ncd
@@ -651,7 +652,7 @@ __global__ void k_assemble(const double2 *P, const double2 *U, int4 bc, double k
     extern __shared__ double2 smem[];
     const int ncd = M.ncd, nv = M.nv;
     double2 *A = smem, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd, *Ws = T1 + 12 * ncd;
-    const int X = blockIdx.x / 9, b = blockIdx.x % 9;
+    const int X = blockIdx.x / 5, b = blockIdx.x % 5;   // the site block and the 4 forward ones
     const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
     const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
     const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
@@ -781,7 +782,7 @@ __global__ void k_assemble_dd(const float2 *Ph, const float2 *Pl, const double2 
     extern __shared__ cdd csm[];
     const int ncd = M.ncd, nv = M.nv;
     cdd *A = csm, *Px = A + ncd * ncd, *W = Px + 12 * ncd, *T1 = W + 12 * ncd, *Ws = T1 + 12 * ncd;
-    const int X = blockIdx.x / 9, b = blockIdx.x % 9;
+    const int X = blockIdx.x / 5, b = blockIdx.x % 5;   // the site block and the 4 forward ones
     const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
     const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
     const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
@@ -917,7 +918,7 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
     __shared__ dd s_cd[CH][9];                  // the hop coefficients, double-float
     __shared__ int s_gp[4][4];                  // gamma partner spin and value (+-1, +-i) per (mu, s)
     __shared__ double2 s_gv[4][4];
-    const int X = blockIdx.x / 9, b = blockIdx.x % 9;
+    const int X = blockIdx.x / 5, b = blockIdx.x % 5;   // the site block and the 4 forward ones
     const int nsite = M.agg[0] * M.agg[1] * M.agg[2] * M.agg[3];
     const int L[4] = {M.g.X, M.g.Y, M.g.Z, M.g.T};
     const int bcv[4] = {bc.x, bc.y, bc.z, bc.w};
@@ -1086,6 +1087,29 @@ __global__ void __launch_bounds__(256) k_assemble_dd2(const float2 *Ph, const fl
             for (int v = 0; v < 3; ++v)
                 Dc[((size_t)X * 9 + b) * ncd * ncd + (size_t)(i0 + u) * ncd + j0 + v] =
                     make_double2(dd2d(acc[u][v].re), dd2d(acc[u][v].im));
+}
+
+// The backward blocks of D_c from the forward ones.  D is gamma5-hermitian
+// and P keeps the two chirality halves apart (P gamma5c = gamma5 P, gamma5c =
+// +1 on the first N_v coarse dofs of a site and -1 on the rest), so D_c =
+// P^dag D P satisfies D_c^dag = gamma5c D_c gamma5c.  Block 5 + mu of X
+// couples X to Y = X - mu, and Y's forward block 1 + mu couples Y to X, face
+// by face (also when the coarse extent is 1 or 2), so
+//   A_{5+mu}(X)[i][j] = s_i s_j conj(A_{1+mu}(Y)[j][i]).
+// The assembly computes blocks 0 .. 4 only.
+__global__ void k_dc_backward(double2 *Dc, const int *nbr, int Vc, int ncd, int nv) {
+    const long n = (long)Vc * 4 * ncd * ncd;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ncd);
+        long r = e / ncd;
+        const int i = (int)(r % ncd);
+        r /= ncd;
+        const int mu = (int)(r % 4), X = (int)(r / 4);
+        const int Y = nbr[X * 9 + 5 + mu];
+        const double2 a = Dc[(((size_t)Y * 9 + 1 + mu) * ncd + j) * ncd + i];
+        const double sg = ((i < nv) == (j < nv)) ? 1.0 : -1.0;
+        Dc[(((size_t)X * 9 + 5 + mu) * ncd + i) * ncd + j] = make_double2(sg * a.x, -sg * a.y);
+    }
 }
 
 __global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
@@ -1804,24 +1828,25 @@ extern "C" int wd_mg_setup(wd_ctx *c, const double *tv, int nv, const int agg[4]
                 const size_t smem2 = sizeof(cdd) * 3 * CH * 12 * (size_t)ncd;                                     \
                 WD_CUDA(cudaFuncSetAttribute(k_assemble_dd2<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem2));                                                        \
-                k_assemble_dd2<CH><<<9 * g->Vc, 256, smem2, c->st>>>(g->Phi, g->Plo, (const double2 *)ulex, bc,   \
+                k_assemble_dd2<CH><<<5 * g->Vc, 256, smem2, c->st>>>(g->Phi, g->Plo, (const double2 *)ulex, bc,   \
                                                                      c->kappa, g->Dc, M);                         \
             }
             WD_ASM_CASE(1) WD_ASM_CASE(2) WD_ASM_CASE(4) WD_ASM_CASE(8)
 #undef WD_ASM_CASE
         } else {
             WD_CUDA(cudaFuncSetAttribute(k_assemble_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_assemble_dd<<<9 * g->Vc, 256, smem, c->st>>>(g->Phi, g->Plo, (const double2 *)ulex, bc, c->kappa, g->Dc,
+            k_assemble_dd<<<5 * g->Vc, 256, smem, c->st>>>(g->Phi, g->Plo, (const double2 *)ulex, bc, c->kappa, g->Dc,
                                                            M);
         }
     } else {
         WD_CUDA(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_assemble<<<9 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
+        k_assemble<<<5 * g->Vc, 256, smem, c->st>>>(g->P, (const double2 *)ulex, bc, c->kappa, g->Dc, M);
     }
+    k_dc_backward<<<1184, 256, 0, c->st>>>(g->Dc, g->nbr, g->Vc, ncd, nv);
     phase("Galerkin assembly");
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Dc, g->Dc32, g->Dclo, (long)nD);
     k_dc_to32<<<1184, 256, 0, c->st>>>(g->Gt, g->Ghi, g->Glo, (long)g->Vc * agg[3] * 2 * nv * nv);
-    c->launches += 8;
+    c->launches += 9;
     WD_CUDA(cudaGetLastError());
     WD_TRY(coarse_tc_build(c));
     WD_CUDA(cudaStreamSynchronize(c->st));

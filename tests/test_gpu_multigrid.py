@@ -560,3 +560,25 @@ def test_setup_again_after_new_links():
             assert rel(y64[r].reshape(-1), ref) < 1e-12, (nv, r)
             assert np.all(np.abs(ysp[r].reshape(-1) - ref) <= u_split(2 * nv) * (Dabs @ np.abs(x[r].reshape(-1)))), (nv, r)
     ctx.close()
+
+
+@pytest.mark.parametrize("dims,agg,nv", [CASES[0], CASES[2]])
+def test_coarse_operator_fp64_assembly(monkeypatch, dims, agg, nv):
+    """With WD_DD=0 the setup assembles D_c in FP64 arithmetic (k_assemble):
+    the site block and the forward blocks, the backward ones derived from the
+    gamma5c-hermiticity of D_c.  The coarse operator matches the oracle's
+    P^dag D P to 1e-12 on coarse extents 2 and 1 (where forward and backward
+    neighbours coincide)."""
+    import torch
+    from paper_2607_05157_b300 import wd_coarse_apply
+    monkeypatch.setenv('WD_DD', '0')
+    ctx, U, D, P = _setup(dims, agg, nv)
+    Dc = multigrid.coarse_operator(D, P)
+    cs = _coarse_shape(dims, agg, nv, 3)
+    rng = np.random.default_rng(23)
+    x = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    y = wd_coarse_apply(ctx.h, to_dev(x), torch.empty(cs, dtype=torch.complex128, device='cuda'), 0).cpu().numpy()
+    for r in range(3):
+        ref = Dc @ x[r].reshape(-1)
+        assert np.abs(y[r].reshape(-1) - ref).max() <= 1e-12 * np.abs(ref).max(), r
+    ctx.close()
