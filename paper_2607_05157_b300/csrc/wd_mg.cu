@@ -288,8 +288,13 @@ __global__ void k_gram_t_dd(const float2 *Ph, const float2 *Pl, double2 *Gt, MgG
         for (int m = 0; m < 4; ++m) { o[m] = (r % M.cd[m]) * M.agg[m]; r /= M.cd[m]; }
         o[3] += tau;
     }
-    for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) {
-        const int k = e / nv, l = e % nv;
+    // G is hermitian: the entries k <= l, each written to (k, l) and its
+    // conjugate to (l, k)
+    const int npair = nv * (nv + 1) / 2;
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        int k = 0, rem = e;
+        while (rem >= nv - k) { rem -= nv - k; ++k; }
+        const int l = k + rem;
         dd are = dd_make(0.f, 0.f), aim = dd_make(0.f, 0.f);
         for (int dz = 0; dz < M.agg[2]; ++dz)
             for (int dy = 0; dy < M.agg[1]; ++dy)
@@ -309,7 +314,9 @@ __global__ void k_gram_t_dd(const float2 *Ph, const float2 *Pl, double2 *Gt, MgG
                         dd_fma(aim, -ki, lr);
                     }
                 }
-        Gt[(size_t)b * nv * nv + e] = make_double2(dd2d(are), dd2d(aim));
+        const double gr = dd2d(are), gi = dd2d(aim);
+        Gt[(size_t)b * nv * nv + (size_t)k * nv + l] = make_double2(gr, gi);
+        if (l != k) Gt[(size_t)b * nv * nv + (size_t)l * nv + k] = make_double2(gr, -gi);
     }
 }
 
