@@ -252,6 +252,8 @@ int eo_to_user(wd_ctx *c, const void *even, const void *odd, int prec, void *use
 // (-1: anywhere).  x_odd nullable: no odd-site reconstruction (then
 // resid_out must be null); bhat_out: the Schur source b_e + k H_eo b_o
 // (a workspace of the context, valid until the next solve).
+// the same entirely in FP32 for tol >= 1e-6 (no FP64 certification)
+int solve_eo_fp32(wd_ctx *c, const double *b_e, const double *b_o, double *x_e, double *x_o, int nrhs, double tol);
 int solve_eo(wd_ctx *c, const double *b_even, const double *b_odd, double *x_even, double *x_odd, int nrhs,
              double tol, int prec, int max_iter, int *iters_out, double *resid_out, const int *src_tsup = nullptr,
              const double **bhat_out = nullptr);
