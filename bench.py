@@ -753,7 +753,11 @@ def main():
         line["mlmc2_vs_hutchinson"] = {
             "workload": f"{WORKLOAD.split(':')[0]}; Hutchinson with the {N1} level-1 noise samples, same solver",
             "hutchinson_ms": ms_h, "mlmc2_ms": ms / args.steps, "mlmc2_over_hutchinson": (ms / args.steps) / ms_h,
-            "hutchinson_var_total": hut["var_total"], "mlmc2_var_total": results[0]["var_total"]}
+            # variances of the two estimates of the total (trace_estimate reports the
+            # per-sample variance for Hutchinson, the estimate's for MLMC2)
+            "hutchinson_var_of_estimate": hut["var_total"] / N1, "mlmc2_var_of_estimate": results[0]["var_total"],
+            "cost_x_variance_mlmc2_over_hutchinson":
+                (ms / args.steps) * results[0]["var_total"] / (ms_h * hut["var_total"] / N1)}
         sec = {}
         for name, fn in (("trace_8x8x8x16", lambda: small_trace_measure(wd, api, torch, synth)),
                          ("probing_16x16x16x32", lambda: probing_measure(wd, api, torch, synth)),
