@@ -361,12 +361,14 @@ def test_tensor_core_coarse_stencil_24x24x24x48_sampled():
     ctx.close()
 
 
-@pytest.mark.parametrize("nrhs", [1, 9, 129, 257])
+@pytest.mark.parametrize("nrhs", [1, 9, 40, 64, 129, 257])
 def test_tensor_core_coarse_stencil_rhs_counts(nrhs):
     """RHS counts at the edges of the tiling: one row, counts that are not a
     multiple of 8 (the input rows are padded to 8), a last tile of one RHS,
-    three tiles.  Every element against the FP64 coarse operator within
-    U_TC (BF16) and U_SPLIT (BF16 pairs), on 12^4 with 4^4 aggregates."""
+    three tiles; with BF16 pairs, tiles of at most 64 RHS stack their Re and
+    Im rows into one MMA (40: the Im rows straddle two lane quarters, 64: they
+    fill the upper two).  Every element against the FP64 coarse operator
+    within U_TC (BF16) and U_SPLIT (BF16 pairs), on 12^4 with 4^4 aggregates."""
     import torch
     from paper_2607_05157_b300 import Context, wd_mg_setup, wd_coarse_apply
     dims, agg, nv = (12, 12, 12, 12), (4, 4, 4, 4), 24
