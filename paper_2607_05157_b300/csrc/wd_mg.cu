@@ -1131,26 +1131,33 @@ __global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
 // as Dc32 + Dclo, x split once into the double-float layout): y = a w + beta
 // A x with the block products and the sums over j and the 9 blocks kept as
 // float pairs (exact FMA errors, TwoSum), the final a w + beta acc in FP64.
+// Each complex product m v = (a + ib)(c + id) takes three real products
+// (Gauss): K1 += (a + b) c, K2 += a (d - c), K3 += b (c + d), and the
+// outputs are Re = K1 - K3, Im = K1 + K2, so 36 instead of 48 FP32
+// operations per term, the pipe this kernel is bound by.  d - c and c + d
+// are formed once per staged RHS element, a + b once per thread and j.
 // One CTA per (X, 32-RHS tile), threads (i, rq); each of the 9 blocks is
 // staged in shared memory by coalesced loads, transposed (column j
 // contiguous, so the threads of a warp read consecutive words), together
 // with the 32 RHS of its neighbour.
-__global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int *nbr, const float4 *x, double2 *y,
-                                  const double2 *w, double a, double beta, int ncd, int Vc, int nrhs) {
-    // one CTA per (X, tile of CD_TILE = 32 RHS), threads (i, rq), rq < 8; thread (i, rq) takes
-    // the RHS rq, rq + 8, rq + 16, rq + 24 of the tile, so each staged block element read
-    // from shared memory serves four RHS (the summation order per RHS is unchanged)
+__global__ void __maxnreg__(56) k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int *nbr,
+                                                  const float4 *x, double2 *y, const double2 *w, double a,
+                                                  double beta, int ncd, int Vc, int nrhs) {
+    // one CTA per (X, tile of 32 RHS), threads (i, rq), rq < 8; thread (i, rq) takes the RHS
+    // rq, rq + 8, rq + 16, rq + 24 of the tile, so each staged block element read from shared
+    // memory (and its a + b) serves four RHS
     constexpr int NQ = 4, TILE = 8 * NQ;
     extern __shared__ float4 sm[];
     const int ld = ncd + 1;                                     // padded column stride
     float2 *Ah = (float2 *)sm, *Al = Ah + ncd * ld;
-    float4 *xs = (float4 *)(Al + ncd * ld + (ncd * ld) % 2);    // [TILE][ncd], 16-byte aligned
+    float4 *xs4 = (float4 *)(Al + ncd * ld);                    // [TILE][ncd] (c.h, c.l, (d-c).h, (d-c).l)
+    float2 *xs2 = (float2 *)(xs4 + TILE * ncd);                 // [TILE][ncd] ((c+d).h, (c+d).l)
     const int X = blockIdx.x, r0 = blockIdx.y * TILE;
     const int i = threadIdx.x % ncd, rq = threadIdx.x / ncd;
     const int nn = ncd * ncd;
-    dd are[NQ], aim[NQ];
+    dd k1[NQ], k2[NQ], k3[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) { are[q] = dd_make(0.f, 0.f); aim[q] = dd_make(0.f, 0.f); }
+    for (int q = 0; q < NQ; ++q) { k1[q] = dd_make(0.f, 0.f); k2[q] = k1[q]; k3[q] = k1[q]; }
     for (int b = 0; b < 9; ++b) {
         const int nb = nbr[X * 9 + b];
         const size_t base = ((size_t)X * 9 + b) * nn;
@@ -1162,21 +1169,25 @@ __global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int 
         }
         for (int e = threadIdx.x; e < TILE * ncd; e += blockDim.x) {
             const int er = e / ncd, ej = e - er * ncd;
-            xs[e] = r0 + er < nrhs ? __ldg(x + ((size_t)(r0 + er) * Vc + nb) * ncd + ej) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v = r0 + er < nrhs ? __ldg(x + ((size_t)(r0 + er) * Vc + nb) * ncd + ej)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            const dd c = dd_make(v.x, v.z), d = dd_make(v.y, v.w);
+            const dd dmc = d - c, cpd = c + d;
+            xs4[e] = make_float4(c.h, c.l, dmc.h, dmc.l);
+            xs2[e] = make_float2(cpd.h, cpd.l);
         }
         __syncthreads();
         if (rq < 8) {
             for (int j = 0; j < ncd; ++j) {
                 const float2 mh = Ah[j * ld + i], ml = Al[j * ld + i];
-                const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y);
+                const dd mr = dd_make(mh.x, ml.x), mi = dd_make(mh.y, ml.y), ms = mr + mi;
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    const float4 v = xs[(rq + 8 * q) * ncd + j];
-                    const dd vr = dd_make(v.x, v.z), vi = dd_make(v.y, v.w);
-                    dd_fma(are[q], mr, vr);
-                    dd_fma(are[q], -mi, vi);
-                    dd_fma(aim[q], mr, vi);
-                    dd_fma(aim[q], mi, vr);
+                    const float4 v = xs4[(rq + 8 * q) * ncd + j];
+                    const float2 u = xs2[(rq + 8 * q) * ncd + j];
+                    dd_fma(k1[q], ms, dd_make(v.x, v.y));
+                    dd_fma(k2[q], mr, dd_make(v.z, v.w));
+                    dd_fma(k3[q], mi, dd_make(u.x, u.y));
                 }
             }
         }
@@ -1187,7 +1198,8 @@ __global__ void k_coarse_apply_dd(const float2 *Dh, const float2 *Dl, const int 
         const int r = r0 + rq + 8 * q;
         if (r >= nrhs) continue;
         const size_t o = ((size_t)r * Vc + X) * ncd + i;
-        double ore = beta * dd2d(are[q]), oim = beta * dd2d(aim[q]);
+        const double s1 = dd2d(k1[q]);
+        double ore = beta * (s1 - dd2d(k3[q])), oim = beta * (s1 + dd2d(k2[q]));
         if (w) { ore += a * w[o].x; oim += a * w[o].y; }
         y[o] = make_double2(ore, oim);
     }
@@ -1426,8 +1438,11 @@ int coarse_apply_dd(wd_ctx *c, const double *x, double *y, const double *w, doub
     WD_CUDA(launch_to_ddl(x, xd, n, c->st));
     dim3 grid(g->Vc, (nrhs + 31) / 32);
     const size_t nld = (size_t)g->ncd * (g->ncd + 1);
-    const size_t smem = (2 * nld + nld % 2) * sizeof(float2) + (size_t)32 * g->ncd * sizeof(float4);
+    const size_t smem = 2 * nld * sizeof(float2) + (size_t)32 * g->ncd * (sizeof(float4) + sizeof(float2));
     WD_CUDA(cudaFuncSetAttribute(k_coarse_apply_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // three 74.5 KB CTAs per SM (2N_v = 48) fit only in the largest shared-memory carveout
+    WD_CUDA(cudaFuncSetAttribute(k_coarse_apply_dd, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
     k_coarse_apply_dd<<<grid, g->ncd * 8, smem, c->st>>>(g->Dc32, g->Dclo, g->nbr, (const float4 *)xd, (double2 *)y,
                                                          (const double2 *)w, a, beta, g->ncd, g->Vc, nrhs);
     c->launches += 2;
