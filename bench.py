@@ -540,6 +540,39 @@ def apply_measure(wd, api, torch, synth, dims, nrhs, steps, warmup):
             "frac_of_measured_copy": gbs / peaks['hbm_gbs'] if (peaks and gbs) else None}
 
 
+def step_measure(wd, api, torch, synth, dims, steps, warmup):
+    """The headline step (two-level MGMLMC, 64 level-1 + 512 level-2 samples,
+    solves to 1e-10, FP32 inner) on another lattice, the other parameters the
+    headline's: a small case of the same kernels for profiling.  Returns the
+    setup time and the CUDA-event time per step."""
+    ctx = wd.Context(dims, synth.gauge_field(dims, SPREAD, GAUGE_SEED), KAPPA, BC)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.wd_mg_setup(ctx.h, None, NV, AGG, tv_iters=TV_ITERS, seed=TV_SEED)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def step(i):
+        return api.trace_estimate(ctx.h, wd.WD_MLMC2, 1, N1, dims[3], n2=N2, seed=rank_seed(0) + i, op=1,
+                                  prec=wd.WD_MIXED_FP32, tol=TOL)
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    l0 = api.wd_launch_count(ctx.h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(steps):
+        res = step(1000 + i)
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = api.wd_launch_count(ctx.h) - l0
+    ctx.close()
+    return {"lattice": "x".join(map(str, dims)), "samples": {"level1": N1, "level2": N2}, "setup_s": setup_s,
+            "ms_per_step": ev0.elapsed_time(ev1) / max(steps, 1), "launches_per_step": launches / max(steps, 1),
+            "n_solves": res["n_solves"] if steps else None}
+
+
 # ---- the headline ------------------------------------------------------------
 
 def main():
@@ -560,13 +593,16 @@ def main():
                     help='only the fine stencil: D applied (FP32 storage) to --apply-rhs spinors on --apply-lattice')
     ap.add_argument('--apply-lattice', default='24,24,24,48', help='lattice of --apply-only (X,Y,Z,T)')
     ap.add_argument('--apply-rhs', type=int, default=64, help='RHS of --apply-only')
+    ap.add_argument('--step-only', action='store_true',
+                    help='only the headline step (setup, then --warmup and --steps steps) on --step-lattice')
+    ap.add_argument('--step-lattice', default='16,16,16,32', help='lattice of --step-only (X,Y,Z,T)')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)
 
     rank, world, local = env_rank()
     cpu = None
-    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.coarse_only or args.apply_only):
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.coarse_only or args.apply_only or args.step_only):
         # the oracle baseline runs in spawned processes before any GPU work
         gbs, cores, busy, wall = oracle_baseline(1)
         cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -595,6 +631,12 @@ def main():
             ad = tuple(int(v) for v in args.apply_lattice.split(','))
             print(json.dumps({"fine_stencil": apply_measure(wd, api, torch, synth, ad, args.apply_rhs,
                                                             args.steps, args.warmup)}), flush=True)
+        return
+    if args.step_only:
+        if rank == 0:
+            sd = tuple(int(v) for v in args.step_lattice.split(','))
+            print(json.dumps({"mlmc2_step": step_measure(wd, api, torch, synth, sd, args.steps, args.warmup)}),
+                  flush=True)
         return
 
     prec = wd.WD_MIXED_FP32 if args.prec == 'fp32' else wd.WD_MIXED_BF16
