@@ -156,17 +156,20 @@ def test_transfer_and_coarse_operator(dims, agg, nv):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", [((4, 4, 4, 4), 2), ((8, 8, 8, 8), 24)])
+@pytest.mark.parametrize("case", [((4, 4, 4, 4), 2, 6), ((8, 8, 8, 8), 24, 6), ((4, 4, 4, 4), 40, 24),
+                                  ((4, 4, 4, 4), 33, 48)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_coarse_solve(prec, case):
     """True FP64 residual of the coarse solves against the oracle's D_c.  The
     mixed solves (prec 1, 2) take their residual by the recursive FP32 update
     r - D_c e once it is small; the reported residual still matches the true
-    one to 1e-11 of |b|."""
+    one to 1e-11 of |b|.  N_v = 24 and 48 give the double-float residual its
+    48x48 and 96x96 blocks (the largest that fit its shared memory), with a
+    ragged last tile of 32 RHS (40 = 32 + 8, 33 = 32 + 1)."""
     from paper_2607_05157_b300 import wd_coarse_solve
     import torch
-    dims, nrhs = case
-    agg, nv = (2, 2, 2, 2), 6
+    dims, nrhs, nv = case
+    agg = (2, 2, 2, 2)
     ctx, U, D, P = _setup(dims, agg, nv)
     Dc = multigrid.coarse_operator(D, P).toarray()
     cs = _coarse_shape(dims, agg, nv, nrhs)
