@@ -1134,8 +1134,8 @@ __global__ void k_dc_to32(const double2 *Dc, float2 *D32, float2 *Dlo, long n) {
 // Each complex product m v = (a + ib)(c + id) takes three real products
 // (Gauss): K1 += (a + b) c, K2 += a (d - c), K3 += b (c + d), and the
 // outputs are Re = K1 - K3, Im = K1 + K2, so 36 instead of 48 FP32
-// operations per term, the pipe this kernel is bound by.  d - c and c + d
-// are formed once per staged RHS element, a + b once per thread and j.
+// operations per term (the kernel is bound by instruction issue).  d - c and
+// c + d are formed once per staged RHS element, a + b once per thread and j.
 // One CTA per (X, 32-RHS tile), threads (i, rq); each of the 9 blocks is
 // staged in shared memory by coalesced loads, transposed (column j
 // contiguous, so the threads of a warp read consecutive words), together
